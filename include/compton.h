@@ -1,0 +1,203 @@
+/*
+ * compton.h -- C ABI of the GB300 Compton pair-scatter library (libcompton.so).
+ *
+ * The library implements the data-parallel hot path of the Monte-Carlo
+ * Compton-scattering step of a particle-in-cell code (arXiv 2206.02937,
+ * Sec. 3.1 and Sec. 3.2): electron and photon macro-particles are binned by
+ * collision cell and paired at random inside each cell, every pair gets its
+ * probability of interaction from the Klein-Nishina cross section evaluated in
+ * the electron rest frame, a Bernoulli trial decides the collision, and the
+ * momenta of accepted pairs are updated.  A small fully connected network can
+ * replace the probability evaluation (Sec. 2, Sec. 3.2).
+ *
+ * Units (Sec. 3.2): momenta in m_e c (electron u, photon k; photon energy
+ * eps = |k| in m_e c^2), cross sections in units of sigma_T, densities in
+ * 1/(sigma_T c t_unit), so that n * sigma * c * dt is dimensionless.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a compton_status; nothing aborts or exits.
+ *   - Pointers named *_dev are device pointers owned by the caller; the
+ *     library never frees them.  Host pointers are named *_host.
+ *   - Calls are asynchronous on the stream they are given (NULL = legacy
+ *     default stream) unless stated otherwise.  One context per host thread,
+ *     except compton_submit / compton_poll, which are thread-safe.
+ *   - Errors found by a kernel (a cell index out of range, ...) are recorded
+ *     in a device word of the context; compton_check() synchronises the stream
+ *     and reports them.
+ *   - All library-owned device memory is allocated in compton_init, within
+ *     compton_config.mem_budget_bytes; no entry point allocates afterwards.
+ */
+#ifndef COMPTON_H
+#define COMPTON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; declared here so this header needs no CUDA. */
+typedef struct CUstream_st* compton_stream_t;
+
+typedef enum compton_status {
+    COMPTON_OK = 0,
+    COMPTON_EINVAL = 1,    /* bad argument (null pointer, size, mode, ...)          */
+    COMPTON_ENOMEM = 2,    /* device allocation failed or exceeds the budget        */
+    COMPTON_EBUSY = 3,     /* serving: no slot or budget free now; retry later      */
+    COMPTON_ETIMEOUT = 4,  /* a bounded device wait gave up                         */
+    COMPTON_ERANGE = 5,    /* input out of range (cell index, size beyond capacity) */
+    COMPTON_ENOTREADY = 6, /* serving: the request has not finished                 */
+    COMPTON_ECUDA = 7,     /* a CUDA call failed; compton_last_error() has the text */
+    COMPTON_ENOMODEL = 8   /* surrogate mode requested but no network is loaded     */
+} compton_status;
+
+typedef enum compton_mode {
+    COMPTON_MODE_PLAIN = 0,    /* analytic probability (Klein-Nishina)      */
+    COMPTON_MODE_MLP_FP32 = 1, /* surrogate network, FP32 operands          */
+    COMPTON_MODE_MLP_BF16 = 2, /* surrogate network, BF16 operands          */
+    COMPTON_MODE_MLP_FP8 = 3   /* surrogate network, FP8 E4M3 operands      */
+} compton_mode;
+
+typedef struct compton_config {
+    int64_t n_cells;             /* number of collision cells C (> 0)                          */
+    int64_t max_particles;       /* capacity per species (sizes the sort scratch)              */
+    double w_over_v;             /* macro-particle weight / cell volume: the density one
+                                    macro-particle adds to its cell                            */
+    double dt;                   /* time step                                                  */
+    uint64_t seed;               /* Philox key of the whole run                                */
+    int32_t device;              /* CUDA device ordinal                                        */
+    float gamma_fp64_threshold;  /* electrons with gamma above this get the pair invariants
+                                    recomputed in FP64 (0 = always, inf = never)               */
+    uint64_t mem_budget_bytes;   /* cap on library-owned device memory (0 = no cap)            */
+} compton_config;
+
+/* One species in structure-of-arrays form (all device pointers, length n).
+ * For photons u* hold the momentum k.  id is a per-particle identifier,
+ * unique within the species; it orders particles whose random keys tie. */
+typedef struct compton_species {
+    float* ux_dev;
+    float* uy_dev;
+    float* uz_dev;
+    int32_t* cell_dev;  /* collision cell in [0, n_cells) */
+    uint32_t* id_dev;
+    int64_t n;
+} compton_species;
+
+/* Pair list of one step, produced by compton_bin_pairs.  Its pointers refer to
+ * context memory and stay valid until the next compton_bin_pairs on the same
+ * context.  Pairs of cell c are the ranks 0..M_c-1 of both species in that
+ * cell, M_c = min(N_e,c, N_g,c); pair p has counter id p. */
+typedef struct compton_pairs {
+    const int32_t* off_e_dev;     /* [n_cells+1] first sorted electron of each cell */
+    const int32_t* off_g_dev;     /* [n_cells+1] first sorted photon of each cell   */
+    const void* cell_info_dev;    /* [n_cells] per-cell pair offset, starts, density */
+    const int32_t* tile_cell_dev; /* per tile of pairs: the cell of its first pair  */
+    const int64_t* n_pairs_dev;   /* total pair count (device scalar)               */
+    int64_t max_pairs;            /* host-side bound: min(n_e, n_g)                  */
+    int64_t n_cells;
+} compton_pairs;
+
+/* Counters accumulated by the kernels since the last reset. */
+typedef struct compton_stats {
+    uint64_t pairs_tested;   /* pairs whose probability was evaluated           */
+    uint64_t scatters;       /* pairs that collided                             */
+    uint64_t mlp_fallbacks;  /* surrogate pairs outside its range (analytic P)  */
+    uint64_t error_flags;    /* bit 0: cell out of range; bit 1: capacity       */
+} compton_stats;
+
+/* ---------------------------------------------------------------------- */
+/* Context                                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Create a context on cfg->device: allocates the scratch for binning
+ * (about 24 bytes per particle of capacity and 40 bytes per cell), the
+ * network buffers and the stats, all within cfg->mem_budget_bytes.
+ * Synchronous.  EINVAL on bad sizes, ENOMEM if the budget or the device
+ * cannot hold it. */
+compton_status compton_init(const compton_config* cfg, struct compton_ctx** out);
+
+/* Free everything compton_init allocated.  Synchronous.  NULL is allowed. */
+compton_status compton_destroy(struct compton_ctx* ctx);
+
+/* Text of the last CUDA error seen by this context ("" if none). */
+const char* compton_last_error(const struct compton_ctx* ctx);
+const char* compton_strerror(compton_status s);
+
+/* Synchronise `stream` and report errors recorded by kernels since the last
+ * check (ERANGE for a cell index outside [0, n_cells)); clears them. */
+compton_status compton_check(struct compton_ctx* ctx, compton_stream_t stream);
+
+/* Synchronise `stream`, copy the counters to *out_host and, if reset != 0,
+ * zero them. */
+compton_status compton_get_stats(struct compton_ctx* ctx, compton_stats* out_host, int reset,
+                                 compton_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Step 1: binning and random in-cell pairing (Sec. 3.1, first step)       */
+/* ---------------------------------------------------------------------- */
+
+/* Bin both species by cell and order each cell at random: particles of a cell
+ * are sorted by (key, id) with key = word 0 of Philox4x32-10 under key
+ * (seed lo, seed hi) at counter (id, step lo, stream, step hi), stream 1 for
+ * electrons and 2 for photons.  The order depends only on the set of
+ * (cell, id) values, never on the input order or on thread timing.
+ *
+ * e_in/g_in are read; e_out/g_out (same n, distinct memory) receive the
+ * sorted copies of all five arrays.  Fills *pairs_out (see compton_pairs).
+ * EINVAL for null pointers, aliasing in/out, n > max_particles; a cell index
+ * outside [0, n_cells) is reported by compton_check (ERANGE) and that
+ * particle is left out of every cell. */
+compton_status compton_bin_pairs(struct compton_ctx* ctx, const compton_species* e_in,
+                                 const compton_species* g_in, compton_species* e_out,
+                                 compton_species* g_out, uint64_t step,
+                                 compton_pairs* pairs_out, compton_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Steps 2-3: probability, Bernoulli trial, collision (Sec. 3.1, 3.2)      */
+/* ---------------------------------------------------------------------- */
+
+/* Resolve every pair of `pairs` in place on the sorted species e, g (the
+ * e_out/g_out of the compton_bin_pairs call that produced `pairs`).
+ * Per pair p (cell c, density n_c = max(N_e,c, N_g,c) * w_over_v):
+ *   x = gamma eps - u.k, v = 1 - beta cos(psi) (rest-frame photon energy and
+ *   flux factor), s = sigma_KN(x)/sigma_T, P = 1 - exp(-n_c dt s v);
+ *   (r0, r1, r2, r3) = Philox4x32-10 at counter (p, step lo, 3, step hi);
+ *   collide iff (r0 >> 8) 2^-24 < P; then t = 1 - cos(theta') from the
+ *   Klein-Nishina angular distribution at u1 = ((r1 >> 8) + 1/2) 2^-24,
+ *   phi = 2 pi (r2 >> 8) 2^-24, and the photon/electron momenta are replaced
+ *   so that energy and momentum are conserved (update in FP64).
+ * mode selects the analytic probability or the surrogate network.
+ * prob_out_dev (nullable, float[max_pairs]) receives P per pair;
+ * flag_out_dev (nullable, uint8[max_pairs]) receives the decision.
+ * Adds to the context stats.  ENOMODEL if a network mode has no weights. */
+compton_status compton_scatter_step(struct compton_ctx* ctx, compton_species* e, compton_species* g,
+                                    const compton_pairs* pairs, compton_mode mode, uint64_t step,
+                                    float* prob_out_dev, uint8_t* flag_out_dev,
+                                    compton_stream_t stream);
+
+/* The same resolution on an explicit pair list (no binning): pair i is
+ * (u[i], k[i]) with density n_dens_dev[i], counter id i under Philox key
+ * (seed lo, seed hi).  u and k (3 SoA arrays each, length n) are updated in
+ * place.  Used for pre-paired batches (serving) and for producing the
+ * network's training targets. */
+compton_status compton_scatter_pairs(struct compton_ctx* ctx, float* ux_dev, float* uy_dev,
+                                     float* uz_dev, float* kx_dev, float* ky_dev, float* kz_dev,
+                                     const float* n_dens_dev, int64_t n, uint64_t seed,
+                                     uint64_t step, compton_mode mode, float* prob_out_dev,
+                                     uint8_t* flag_out_dev, compton_stream_t stream);
+
+/* Analytic target of the surrogate: r = s(x) (1 - beta cos psi) / 2 in [0, 1]
+ * per pair, the probability normalised by its per-cell maximum
+ * P_max = 2 sigma_T c dt max w (Sec. 3.2) in the small-probability limit.
+ * Inputs u, k as in compton_scatter_pairs (read only); r_out_dev float[n]. */
+compton_status compton_kn_ratio(struct compton_ctx* ctx, const float* ux_dev, const float* uy_dev,
+                                const float* uz_dev, const float* kx_dev, const float* ky_dev,
+                                const float* kz_dev, int64_t n, float* r_out_dev,
+                                compton_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COMPTON_H */

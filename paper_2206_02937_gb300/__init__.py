@@ -1,0 +1,196 @@
+"""GB300 Compton pair-scatter library: thin Python binding of libcompton.so.
+
+Every function below marshals arguments to the C ABI declared in
+``include/compton.h`` (same names) and does nothing else: every step of the
+path runs in the library's CUDA kernels.  Device buffers are torch CUDA
+tensors, passed by ``data_ptr()``; streams are ``torch.cuda.Stream`` objects
+(or None for the current stream).  The library must be built first
+(``paper_2206_02937_gb300.buildlib.build()``); importing the binding without it
+raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from .buildlib import LIB, build  # noqa: F401
+
+c_i32, c_i64, c_u32, c_u64, c_f32, c_f64, c_p = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                                 ctypes.c_uint64, ctypes.c_float, ctypes.c_double,
+                                                 ctypes.c_void_p)
+
+COMPTON_OK, COMPTON_EINVAL, COMPTON_ENOMEM, COMPTON_EBUSY, COMPTON_ETIMEOUT, COMPTON_ERANGE, \
+    COMPTON_ENOTREADY, COMPTON_ECUDA, COMPTON_ENOMODEL = range(9)
+MODE_PLAIN, MODE_MLP_FP32, MODE_MLP_BF16, MODE_MLP_FP8 = range(4)
+
+
+class compton_config(ctypes.Structure):
+    _fields_ = [("n_cells", c_i64), ("max_particles", c_i64), ("w_over_v", c_f64), ("dt", c_f64),
+                ("seed", c_u64), ("device", c_i32), ("gamma_fp64_threshold", c_f32),
+                ("mem_budget_bytes", c_u64)]
+
+
+class compton_species(ctypes.Structure):
+    _fields_ = [("ux_dev", c_p), ("uy_dev", c_p), ("uz_dev", c_p), ("cell_dev", c_p), ("id_dev", c_p),
+                ("n", c_i64)]
+
+
+class compton_pairs(ctypes.Structure):
+    _fields_ = [("off_e_dev", c_p), ("off_g_dev", c_p), ("cell_info_dev", c_p), ("tile_cell_dev", c_p),
+                ("n_pairs_dev", c_p), ("max_pairs", c_i64), ("n_cells", c_i64)]
+
+
+class compton_stats(ctypes.Structure):
+    _fields_ = [("pairs_tested", c_u64), ("scatters", c_u64), ("mlp_fallbacks", c_u64),
+                ("error_flags", c_u64)]
+
+
+class ComptonError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: status {status} ({strerror(status)})")
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported symbol; the CPU tests check
+# that the built library exports each one.
+SIGNATURES = {
+    "compton_init": (c_i32, [ctypes.POINTER(compton_config), ctypes.POINTER(c_p)]),
+    "compton_destroy": (c_i32, [c_p]),
+    "compton_last_error": (ctypes.c_char_p, [c_p]),
+    "compton_strerror": (ctypes.c_char_p, [c_i32]),
+    "compton_check": (c_i32, [c_p, c_p]),
+    "compton_get_stats": (c_i32, [c_p, ctypes.POINTER(compton_stats), c_i32, c_p]),
+    "compton_bin_pairs": (c_i32, [c_p, ctypes.POINTER(compton_species), ctypes.POINTER(compton_species),
+                                  ctypes.POINTER(compton_species), ctypes.POINTER(compton_species), c_u64,
+                                  ctypes.POINTER(compton_pairs), c_p]),
+    "compton_scatter_step": (c_i32, [c_p, ctypes.POINTER(compton_species), ctypes.POINTER(compton_species),
+                                     ctypes.POINTER(compton_pairs), c_i32, c_u64, c_p, c_p, c_p]),
+    "compton_scatter_pairs": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_i64, c_u64, c_u64, c_i32,
+                                      c_p, c_p, c_p]),
+    "compton_kn_ratio": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_i64, c_p, c_p]),
+}
+
+
+def lib():
+    """Load libcompton.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise ImportError(f"libcompton.so is not built ({LIB}); run paper_2206_02937_gb300.buildlib.build()")
+        L = ctypes.CDLL(LIB)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().compton_strerror(int(status)).decode()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return c_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return c_p(0) if t is None else c_p(t.data_ptr())
+
+
+def _check(st: int, what: str, ctx=None):
+    if st != COMPTON_OK:
+        err = ComptonError(st, what)
+        if ctx is not None and st == COMPTON_ECUDA:
+            err.args = (err.args[0] + ": " + lib().compton_last_error(ctx).decode(),)
+        raise err
+
+
+@dataclass
+class Species:
+    """One species as five torch CUDA tensors of equal length."""
+    ux: "object"
+    uy: "object"
+    uz: "object"
+    cell: "object"
+    id: "object"
+
+    @property
+    def n(self) -> int:
+        return int(self.ux.shape[0])
+
+    def c(self) -> compton_species:
+        return compton_species(self.ux.data_ptr(), self.uy.data_ptr(), self.uz.data_ptr(),
+                               self.cell.data_ptr(), self.id.data_ptr(), self.n)
+
+    @staticmethod
+    def empty_like(s: "Species") -> "Species":
+        import torch
+        return Species(torch.empty_like(s.ux), torch.empty_like(s.uy), torch.empty_like(s.uz),
+                       torch.empty_like(s.cell), torch.empty_like(s.id))
+
+
+def compton_init(n_cells: int, max_particles: int, w_over_v: float, dt: float, seed: int, device: int = 0,
+                 gamma_fp64_threshold: float = 1.0e3, mem_budget_bytes: int = 0) -> int:
+    cfg = compton_config(n_cells, max_particles, w_over_v, dt, seed, device, gamma_fp64_threshold,
+                         mem_budget_bytes)
+    out = c_p()
+    _check(lib().compton_init(ctypes.byref(cfg), ctypes.byref(out)), "compton_init")
+    return out.value
+
+
+def compton_destroy(ctx: int) -> None:
+    _check(lib().compton_destroy(c_p(ctx)), "compton_destroy")
+
+
+def compton_check(ctx: int, stream=None) -> int:
+    """Returns the status (does not raise on ERANGE)."""
+    return lib().compton_check(c_p(ctx), _stream_ptr(stream))
+
+
+def compton_get_stats(ctx: int, reset: bool = False, stream=None) -> dict:
+    s = compton_stats()
+    _check(lib().compton_get_stats(c_p(ctx), ctypes.byref(s), int(reset), _stream_ptr(stream)),
+           "compton_get_stats", ctx)
+    return dict(pairs_tested=s.pairs_tested, scatters=s.scatters, mlp_fallbacks=s.mlp_fallbacks,
+                error_flags=s.error_flags)
+
+
+def compton_bin_pairs(ctx: int, e_in: Species, g_in: Species, e_out: Species, g_out: Species, step: int,
+                      stream=None) -> compton_pairs:
+    pairs = compton_pairs()
+    ei, gi, eo, go = e_in.c(), g_in.c(), e_out.c(), g_out.c()
+    _check(lib().compton_bin_pairs(c_p(ctx), ctypes.byref(ei), ctypes.byref(gi), ctypes.byref(eo),
+                                   ctypes.byref(go), int(step), ctypes.byref(pairs), _stream_ptr(stream)),
+           "compton_bin_pairs", ctx)
+    return pairs
+
+
+def compton_scatter_step(ctx: int, e: Species, g: Species, pairs: compton_pairs, mode: int, step: int,
+                         prob_out=None, flag_out=None, stream=None) -> None:
+    ec, gc = e.c(), g.c()
+    _check(lib().compton_scatter_step(c_p(ctx), ctypes.byref(ec), ctypes.byref(gc), ctypes.byref(pairs),
+                                      int(mode), int(step), _ptr(prob_out), _ptr(flag_out),
+                                      _stream_ptr(stream)), "compton_scatter_step", ctx)
+
+
+def compton_scatter_pairs(ctx: int, u, k, n_dens, seed: int, step: int, mode: int = MODE_PLAIN,
+                          prob_out=None, flag_out=None, stream=None) -> None:
+    """u, k: (3, n) float32 CUDA tensors (rows contiguous), updated in place."""
+    n = int(u.shape[1])
+    _check(lib().compton_scatter_pairs(c_p(ctx), _ptr(u[0]), _ptr(u[1]), _ptr(u[2]), _ptr(k[0]), _ptr(k[1]),
+                                       _ptr(k[2]), _ptr(n_dens), n, int(seed), int(step), int(mode),
+                                       _ptr(prob_out), _ptr(flag_out), _stream_ptr(stream)),
+           "compton_scatter_pairs", ctx)
+
+
+def compton_kn_ratio(ctx: int, u, k, r_out, stream=None) -> None:
+    n = int(u.shape[1])
+    _check(lib().compton_kn_ratio(c_p(ctx), _ptr(u[0]), _ptr(u[1]), _ptr(u[2]), _ptr(k[0]), _ptr(k[1]),
+                                  _ptr(k[2]), n, _ptr(r_out), _stream_ptr(stream)), "compton_kn_ratio", ctx)
