@@ -1,0 +1,164 @@
+"""FP64 oracle of the surrogate network (arXiv 2206.02937, Sec. 2 and 3.2).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py): only the tests, the smoke
+check and the CPU-baseline leg of the benchmark use it.
+
+The paper's network maps the photon and lepton momenta (units of m_e c) to a
+probability y' in [0, 1] with fully connected layers, hidden activations and a
+sigmoid output (Sec. 3.2); it is trained with the mean absolute error and the
+Adam optimizer at learning rate 1e-3 (Sec. 3.2, Kingma and Ba 2014).  The
+configuration built here is 4 hidden layers of 64 SiLU units (the paper's own
+9-12-9 ReLU network is a later variant), inputs
+
+    f = [sgnlog(u_i / s_u) / n_u, sgnlog(k_i / s_k) / n_k],  i = x, y, z,
+    sgnlog(z) = sign(z) log(1 + |z|),
+
+target r = sigma_KN v / (2 sigma_T) (the probability normalised by the cell
+maximum P_max = 2 sigma_T c dt max w of Sec. 3.2).
+
+Parameter vector layout (float64, length 12993), layer by layer:
+    W0 (64 x 6), b0 (64), W1 (64 x 64), b1, W2, b2, W3, b3, W4 (1 x 64), b4 (1)
+with W stored (out, in), row-major.  The library uses the same vector.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+N_IN, WIDTH, DEPTH = 6, 64, 4
+FEATURE_SCALES = dict(s_u=1.0, n_u=7.0, s_k=1e-4, n_k=10.0)
+
+
+def layer_shapes():
+    shapes = [(WIDTH, N_IN)] + [(WIDTH, WIDTH)] * (DEPTH - 1) + [(1, WIDTH)]
+    return shapes
+
+
+def n_params() -> int:
+    return sum(o * i + o for o, i in layer_shapes())
+
+
+def unpack(theta: np.ndarray):
+    """[(W, b), ...] views into the flat parameter vector."""
+    out, at = [], 0
+    for o, i in layer_shapes():
+        W = theta[at:at + o * i].reshape(o, i)
+        at += o * i
+        b = theta[at:at + o]
+        at += o
+        out.append((W, b))
+    assert at == theta.shape[0]
+    return out
+
+
+def init_params(seed: int) -> np.ndarray:
+    """Glorot-uniform weights, zero biases (Keras' default initialisation)."""
+    rng = np.random.default_rng(seed)
+    theta = np.zeros(n_params())
+    for W, b in unpack(theta):
+        lim = np.sqrt(6.0 / (W.shape[0] + W.shape[1]))
+        W[...] = rng.uniform(-lim, lim, W.shape)
+    return theta
+
+
+def sgnlog(z):
+    return np.sign(z) * np.log1p(np.abs(z))
+
+
+def features(u: np.ndarray, k: np.ndarray, scales=FEATURE_SCALES) -> np.ndarray:
+    """(6, n) network inputs from (3, n) momenta."""
+    u = np.asarray(u, dtype=np.float64)
+    k = np.asarray(k, dtype=np.float64)
+    return np.concatenate([sgnlog(u / scales["s_u"]) / scales["n_u"],
+                           sgnlog(k / scales["s_k"]) / scales["n_k"]])
+
+
+def silu(z):
+    return z / (1.0 + np.exp(-z))
+
+
+def sigmoid(z):
+    return 1.0 / (1.0 + np.exp(-z))
+
+
+def forward(theta: np.ndarray, f: np.ndarray):
+    """y' for (6, n) inputs f; returns (y', cache of pre-activations and activations)."""
+    layers = unpack(theta)
+    h = np.asarray(f, dtype=np.float64)
+    cache = [h]
+    for W, b in layers[:-1]:
+        z = W @ h + b[:, None]
+        h = silu(z)
+        cache += [z, h]
+    W, b = layers[-1]
+    z = W @ h + b[:, None]
+    y = sigmoid(z)[0]
+    cache.append(z)
+    return y, cache
+
+
+def mae_loss(y_pred, y, w=None) -> float:
+    """Weighted mean absolute error sum w |y' - y| / sum w (Sec. 3.2, MAE)."""
+    w = np.ones_like(y) if w is None else w
+    return float(np.sum(w * np.abs(y_pred - y)) / np.sum(w))
+
+
+def backward(theta: np.ndarray, f: np.ndarray, y: np.ndarray, w=None):
+    """Loss and its gradient w.r.t. theta (same layout).  The MAE subgradient
+    at y' = y is taken as 0."""
+    y_pred, cache = forward(theta, f)
+    n = y.shape[0]
+    w = np.ones(n) if w is None else np.asarray(w, dtype=np.float64)
+    loss = float(np.sum(w * np.abs(y_pred - y)) / np.sum(w))
+    grad = np.zeros_like(theta)
+    gl = unpack(grad)
+    layers = unpack(theta)
+    # d loss / d y'
+    dy = w * np.sign(y_pred - y) / np.sum(w)
+    # sigmoid output
+    s = y_pred
+    dz = (dy * s * (1.0 - s))[None, :]
+    h_prev = cache[-2]
+    gl[-1][0][...] = dz @ h_prev.T
+    gl[-1][1][...] = dz.sum(axis=1)
+    dh = layers[-1][0].T @ dz
+    for li in range(DEPTH - 1, -1, -1):
+        z = cache[1 + 2 * li]
+        sg = sigmoid(z)
+        dsilu = sg * (1.0 + z * (1.0 - sg))
+        dz = dh * dsilu
+        h_in = cache[2 * li]
+        gl[li][0][...] = dz @ h_in.T
+        gl[li][1][...] = dz.sum(axis=1)
+        dh = layers[li][0].T @ dz
+    return loss, grad
+
+
+class Adam:
+    """Adam as published (Kingma and Ba 2014, Algorithm 1): bias-corrected
+    first and second moments, update lr m_hat / (sqrt(v_hat) + eps)."""
+
+    def __init__(self, n, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-7):
+        self.m = np.zeros(n)
+        self.v = np.zeros(n)
+        self.t = 0
+        self.lr, self.b1, self.b2, self.eps = lr, beta1, beta2, eps
+
+    def step(self, theta, grad):
+        self.t += 1
+        self.m = self.b1 * self.m + (1 - self.b1) * grad
+        self.v = self.b2 * self.v + (1 - self.b2) * grad * grad
+        mh = self.m / (1 - self.b1 ** self.t)
+        vh = self.v / (1 - self.b2 ** self.t)
+        return theta - self.lr * mh / (np.sqrt(vh) + self.eps)
+
+
+def balance_weights(r: np.ndarray, n_bins: int = 32, lo: float = 1e-8, hi: float = 1.0) -> np.ndarray:
+    """Per-sample weights that make every probability decade range count
+    equally (the data balancing of Sec. 3.2): histogram log10 r in n_bins
+    equal bins on [lo, hi], weight 1/count of the sample's bin, normalised
+    to mean 1."""
+    x = np.clip(np.log10(np.maximum(r, lo)), np.log10(lo), np.log10(hi))
+    b = np.minimum(((x - np.log10(lo)) / (np.log10(hi) - np.log10(lo)) * n_bins).astype(np.int64), n_bins - 1)
+    cnt = np.bincount(b, minlength=n_bins).astype(np.float64)
+    wt = 1.0 / cnt[b]
+    return wt * (wt.shape[0] / wt.sum())
