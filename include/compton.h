@@ -196,6 +196,17 @@ compton_status compton_kn_ratio(struct compton_ctx* ctx, const float* ux_dev, co
                                 const float* kz_dev, int64_t n, float* r_out_dev,
                                 compton_stream_t stream);
 
+/* The scattering-angle sampler of compton_scatter_step on its own, for
+ * validation (the paper resolves each collision by sampling the scattered
+ * photon, Sec. 3.1).  For each i: x_dev[i] is the rest-frame photon energy,
+ * r_dev[i] a raw 32-bit random word (its top 24 bits give
+ * u1 = ((r >> 8) + 1/2) 2^-24); the outputs are cos(theta'), sin(theta') of
+ * the inverse of the Klein-Nishina angular cumulative at u1, and the Compton
+ * energy ratio 1/(1 + x (1 - cos theta')).  All arrays length n, device. */
+compton_status compton_kn_sample_angle(struct compton_ctx* ctx, const float* x_dev, const uint32_t* r_dev,
+                                       int64_t n, float* cth_out_dev, float* sth_out_dev,
+                                       float* ratio_out_dev, compton_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

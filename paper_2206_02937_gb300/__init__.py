@@ -71,6 +71,7 @@ SIGNATURES = {
     "compton_scatter_pairs": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_i64, c_u64, c_u64, c_i32,
                                       c_p, c_p, c_p]),
     "compton_kn_ratio": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_i64, c_p, c_p]),
+    "compton_kn_sample_angle": (c_i32, [c_p, c_p, c_p, c_i64, c_p, c_p, c_p, c_p]),
 }
 
 
@@ -194,3 +195,9 @@ def compton_kn_ratio(ctx: int, u, k, r_out, stream=None) -> None:
     n = int(u.shape[1])
     _check(lib().compton_kn_ratio(c_p(ctx), _ptr(u[0]), _ptr(u[1]), _ptr(u[2]), _ptr(k[0]), _ptr(k[1]),
                                   _ptr(k[2]), n, _ptr(r_out), _stream_ptr(stream)), "compton_kn_ratio", ctx)
+
+
+def compton_kn_sample_angle(ctx: int, x, r, cth_out, sth_out, ratio_out, stream=None) -> None:
+    n = int(x.shape[0])
+    _check(lib().compton_kn_sample_angle(c_p(ctx), _ptr(x), _ptr(r), n, _ptr(cth_out), _ptr(sth_out),
+                                         _ptr(ratio_out), _stream_ptr(stream)), "compton_kn_sample_angle", ctx)

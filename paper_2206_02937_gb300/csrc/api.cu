@@ -235,4 +235,13 @@ compton_status compton_kn_ratio(compton_ctx* ctx, const float* ux, const float* 
     return compton::launch_kn_ratio(ctx, ux, uy, uz, kx, ky, kz, n, r_out, stream);
 }
 
+compton_status compton_kn_sample_angle(compton_ctx* ctx, const float* x, const uint32_t* r, int64_t n,
+                                       float* cth_out, float* sth_out, float* ratio_out, compton_stream_t stream)
+{
+    if (!ctx || n < 0) return COMPTON_EINVAL;
+    if (n == 0) return COMPTON_OK;
+    if (!x || !r || !cth_out || !sth_out || !ratio_out) return COMPTON_EINVAL;
+    return compton::launch_sample_angle(ctx, x, r, n, cth_out, sth_out, ratio_out, stream);
+}
+
 }  // extern "C"

@@ -89,5 +89,7 @@ compton_status launch_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, floa
 compton_status launch_kn_ratio(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                const float* kx, const float* ky, const float* kz, int64_t n, float* r_out,
                                cudaStream_t stream);
+compton_status launch_sample_angle(compton_ctx* ctx, const float* x, const uint32_t* r, int64_t n, float* cth,
+                                   float* sth, float* ratio, cudaStream_t stream);
 
 }  // namespace compton

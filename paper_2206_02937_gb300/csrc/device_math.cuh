@@ -58,8 +58,8 @@ __device__ __forceinline__ Philox4 draw(uint64_t seed, uint64_t step, uint32_t s
 
 enum : uint32_t { kStreamPairE = 1u, kStreamPairG = 2u, kStreamScatter = 3u };
 
+// Uniform on [0, 1) from the top 24 bits of a word (exact in FP32).
 __device__ __forceinline__ float u24_closed0(uint32_t r) { return (float)(r >> 8) * 0x1.0p-24f; }
-__device__ __forceinline__ float u24_open(uint32_t r) { return ((float)(r >> 8) + 0.5f) * 0x1.0p-24f; }
 
 // ---------------------------------------------------------------------------
 // a*b - c*d with one rounding error at most 1.5 ulp: Kahan's algorithm with a
@@ -96,18 +96,18 @@ __device__ __forceinline__ Invariants invariants_f32(float ux, float uy, float u
     r.eps = sqrtf(fmaf(kx, kx, fmaf(ky, ky, kz * kz)));
     float v = 1.0f;
     if (un > 0.0f && r.eps > 0.0f) {
-        const float beta = un / r.gamma;
-        const float omb = 1.0f / (r.gamma * (r.gamma + un));
+        const float beta = __fdividef(un, r.gamma);
+        const float omb = __fdividef(1.0f, r.gamma * (r.gamma + un));
         const float uk = fmaf(ux, kx, fmaf(uy, ky, uz * kz));
         const float ue = un * r.eps;
-        const float cosp = uk / ue;
+        const float cosp = __fdividef(uk, ue);
         float omc;
         if (cosp > 0.0f) {
             const float cx = diff_of_products(uy, kz, uz, ky);
             const float cy = diff_of_products(uz, kx, ux, kz);
             const float cz = diff_of_products(ux, ky, uy, kx);
-            const float sn = sqrtf(fmaf(cx, cx, fmaf(cy, cy, cz * cz))) / ue;
-            omc = sn * sn / (1.0f + cosp);
+            const float sn = __fdividef(sqrtf(fmaf(cx, cx, fmaf(cy, cy, cz * cz))), ue);
+            omc = __fdividef(sn * sn, 1.0f + cosp);
         } else {
             omc = 1.0f - cosp;
         }
@@ -155,87 +155,171 @@ __device__ __forceinline__ void invariants_f64(float ux, float uy, float uz, flo
 // and its integral from 0 to t is F = A + B - C with w = x t:
 //   A = t (2 + w) / (2 (1 + w)^2)
 //   B = ln(1 + w) / x
-//   C = 2 g1(w) / x^2 - g2(w) / x^3,
-//   g1 = ln(1+w) - w/(1+w),  g2 = w - 2 ln(1+w) + w/(1+w).
-// g1 and g2 cancel for small w.  With z = w/(2+w) (so ln(1+w) = 2 atanh z and
-// w/(1+w) = 2z/(1+z)) both become sums of positive terms:
-//   g1 = 2 z^2 [ z S1 + 1/(1+z) ],   g2 = 4 z^3 S2,
+//   C = int_0^t s(2-s)/(1+xs)^2 ds = [(2x+2) ln(1+w) - w - (2x+1) w/(1+w)] / x^3.
+// C cancels for small |w|.  With z = w/(2+w) (ln(1+w) = 2 atanh z,
+// w/(1+w) = 2z/(1+z)) and q = z/x = t/(2+w) it becomes
+//   C = 4 q^2 [ z S1 + 1/(1+z) - q S2 ],   B = 2 q (1 + z^2 S1),
 //   S1 = sum_{j>=1} z^(2j-2)/(2j+1),  S2 = sum_{j>=1} 2j/(2j+1) z^(2j-2),
-// and with q = z/x = t/(2+w):  B = 2q (1 + z^2 S1),
-//   C = 4 q^2 [ z S1 + 1/(1+z) ] - 4 q^3 S2.
-// For w < 1 (z^2 < 1/9) ten terms of S1, S2 reach FP32 precision; above it the
-// direct forms lose at most a few bits.  The total cross section is
+// series of positive terms; for -0.6 < w < 1 (z^2 < 0.19) twelve terms reach
+// FP32 precision.  Outside that range the closed forms lose only a few bits.
 // sigma/sigma_T = 3/8 F(x, 2).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void kn_series(float z2, float& S1, float& S2)
+{
+    S1 = 0.0f;
+    S2 = 0.0f;
+#pragma unroll
+    for (int j = 12; j >= 1; --j) {
+        S1 = fmaf(S1, z2, 1.0f / (float)(2 * j + 1));
+        S2 = fmaf(S2, z2, (float)(2 * j) / (float)(2 * j + 1));
+    }
+}
+
+// C(x, t) in the series range -0.6 < x t < 1 (x may be negative).
+__device__ __forceinline__ float kn_C_series(float x, float t)
+{
+    const float w = x * t;
+    const float q = __fdividef(t, 2.0f + w);
+    const float z = x * q;
+    float S1, S2;
+    kn_series(z * z, S1, S2);
+    return 4.0f * q * q * (fmaf(z, S1, __fdividef(1.0f, 1.0f + z)) - q * S2);
+}
+
 __device__ __forceinline__ float kn_F(float x, float t)
 {
     const float w = x * t;
     const float opw = 1.0f + w;
-    const float A = t * (2.0f + w) / (2.0f * opw * opw);
-    float B, C;
+    const float A = __fdividef(t * (2.0f + w), 2.0f * opw * opw);
     if (w < 1.0f) {
-        const float q = t / (2.0f + w);
+        const float q = __fdividef(t, 2.0f + w);
         const float z = x * q;
         const float z2 = z * z;
-        float S1 = 0.0f, S2 = 0.0f;
-#pragma unroll
-        for (int j = 10; j >= 1; --j) {
-            S1 = fmaf(S1, z2, 1.0f / (float)(2 * j + 1));
-            S2 = fmaf(S2, z2, (float)(2 * j) / (float)(2 * j + 1));
-        }
-        B = 2.0f * q * fmaf(z2, S1, 1.0f);
-        const float q2 = q * q;
-        C = 4.0f * q2 * (fmaf(z, S1, 1.0f / (1.0f + z)) - q * S2);
-    } else {
-        const float L = log1pf(w);
-        const float r = w / opw;
-        B = L / x;
-        C = (2.0f * x * (L - r) - (w - 2.0f * L + r)) / (x * x * x);
+        float S1, S2;
+        kn_series(z2, S1, S2);
+        const float B = 2.0f * q * fmaf(z2, S1, 1.0f);
+        const float C = 4.0f * q * q * (fmaf(z, S1, __fdividef(1.0f, 1.0f + z)) - q * S2);
+        return A + B - C;
     }
+    const float L = log1pf(w);
+    const float B = __fdividef(L, x);
+    const float C = __fdividef(fmaf(2.0f * x + 2.0f, L, -w) - (2.0f * x + 1.0f) * __fdividef(w, opw), x * x * x);
     return A + B - C;
 }
 
-__device__ __forceinline__ float kn_f(float x, float t)
+// Complementary cumulative G(x, tau) = int_{2-tau}^{2} f(x, t) dt, computed
+// without forming F(2) - F(2 - tau).  With a = 1 + 2x and d = 1 + x(2 - tau)
+// (so a - d = x tau exactly):
+//   int xi^3 = tau (a + d) / (2 a^2 d^2),   int xi = ln(a/d)/x = log1p(x tau/d)/x,
+//   int xi^2 t(2-t) = C(-x/a, tau)/a^2, which for x tau/a >= 0.6 equals
+//   [2 (1 + x) log1p(x tau/d) - x tau (d + 1)/d] / x^3.
+__device__ __forceinline__ float kn_G(float x, float tau)
 {
-    const float xi = 1.0f / fmaf(x, t, 1.0f);
+    const float a = fmaf(2.0f, x, 1.0f);
+    const float d = fmaf(x, 2.0f - tau, 1.0f);
+    const float Ac = __fdividef(tau * (a + d), 2.0f * a * a * d * d);
+    const float Lc = log1pf(__fdividef(x * tau, d));
+    const float Bc = x > 0.0f ? __fdividef(Lc, x) : tau;
+    float Cc;
+    if (x * tau < 0.6f * a) {
+        Cc = __fdividef(kn_C_series(-__fdividef(x, a), tau), a * a);
+    } else {
+        Cc = __fdividef(fmaf(2.0f * (1.0f + x), Lc, -__fdividef(x * tau * (d + 1.0f), d)), x * x * x);
+    }
+    return Ac + Bc - Cc;
+}
+
+// Angular density at t (lower branch) and at t = 2 - s (upper branch).
+__device__ __forceinline__ float kn_f_lower(float x, float t)
+{
+    const float xi = __fdividef(1.0f, fmaf(x, t, 1.0f));
     const float xi2 = xi * xi;
     return fmaf(xi2, xi, xi) - xi2 * t * (2.0f - t);
+}
+__device__ __forceinline__ float kn_f_upper(float x, float s)
+{
+    const float xi = __fdividef(1.0f, fmaf(x, 2.0f - s, 1.0f));
+    const float xi2 = xi * xi;
+    return fmaf(xi2, xi, xi) - xi2 * s * (2.0f - s);
 }
 
 // sigma_KN(x) / sigma_T
 __device__ __forceinline__ float kn_sigma(float x) { return 0.375f * kn_F(x, 2.0f); }
 
 // ---------------------------------------------------------------------------
-// Scattering angle: the t in [0, 2] with F(x, t) = u1 F(x, 2).  Start from the
-// exact root of the Thomson-limit cubic (x -> 0: F = 2t - t^2 + t^3/3, i.e.
-// y^3 + 3y = 8 u1 - 4 with y = t - 1, solved by Cardano's formula) for x < 1,
-// or from the large-x form F ~ ln(1 + x t)/x otherwise, then at most eight
-// Newton steps kept inside a shrinking bracket (bisection when a step leaves
-// it).  F is strictly increasing, so the bracket always holds the root.
+// Scattering angle from the 24-bit draw r24 (u1 = (r24 + 1/2) 2^-24).
+// Lower half (r24 < 2^23): solve F(x, t) = u1 F(x, 2) for t.  Upper half:
+// solve G(x, tau) = (1 - u1) F(x, 2) for tau = 2 - t, with
+// 1 - u1 = (2^24 - 1 - r24 + 1/2) 2^-24 formed exactly, so that directions
+// near backscatter (t -> 2) keep full relative precision in tau.
+// Start: the exact root of the Thomson-limit cubic (x -> 0, where both halves
+// follow 2s - s^2 + s^3/3 = 8 uu/3, i.e. y^3 + 3y = 8uu - 4 with y = s - 1,
+// Cardano's formula) for x < 1; for x >= 1 the large-x forms
+// s = expm1(x target)/x (lower) or target/f(x, 2) (upper).  Then at most eight
+// Newton steps inside a shrinking bracket (bisection when a step leaves it).
+// Returns cos(theta'), sin(theta') and 1/(1 + x t) (the Compton energy ratio).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float kn_sample_t(float x, float u1, float F2)
+struct Angle {
+    float cth, sth, ratio;
+};
+
+__device__ __forceinline__ Angle kn_sample_angle(float x, uint32_t r24, float F2)
 {
-    const float target = u1 * F2;
-    float t;
+    const bool upper = r24 >= (1u << 23);
+    const float uu = ((float)(upper ? 16777215u - r24 : r24) + 0.5f) * 0x1.0p-24f;
+    const float target = uu * F2;
+    float s;
     if (x < 1.0f) {
-        const float q = fmaf(8.0f, u1, -4.0f);
+        const float q = fmaf(8.0f, uu, -4.0f);
         const float D = sqrtf(fmaf(0.25f * q, q, 1.0f));
-        t = cbrtf(0.5f * q + D) + cbrtf(0.5f * q - D) + 1.0f;
+        s = cbrtf(0.5f * q + D) + cbrtf(0.5f * q - D) + 1.0f;
     } else {
-        t = expm1f(target * x) / x;
+        s = upper ? __fdividef(target, kn_f_upper(x, 0.0f)) : __fdividef(expm1f(target * x), x);
     }
     float lo = 0.0f, hi = 2.0f;
-    t = fminf(fmaxf(t, 0.0f), 2.0f);
+    s = fminf(fmaxf(s, 0.0f), 2.0f);
     for (int it = 0; it < 8; ++it) {
-        const float R = kn_F(x, t) - target;
+        const float R = (upper ? kn_G(x, s) : kn_F(x, s)) - target;
         if (R == 0.0f) break;
-        if (R < 0.0f) lo = t; else hi = t;
-        float tn = t - R / kn_f(x, t);
-        if (!(tn >= lo && tn <= hi)) tn = 0.5f * (lo + hi);
-        if (tn == t) break;
-        t = tn;
+        if (R < 0.0f) lo = s; else hi = s;
+        float sn = s - __fdividef(R, upper ? kn_f_upper(x, s) : kn_f_lower(x, s));
+        if (!(sn >= lo && sn <= hi)) sn = 0.5f * (lo + hi);
+        if (sn == s) break;
+        s = sn;
     }
-    return t;
+    Angle a;
+    a.cth = upper ? s - 1.0f : 1.0f - s;
+    a.sth = sqrtf(s * (2.0f - s));
+    a.ratio = __fdividef(1.0f, upper ? fmaf(x, 2.0f - s, 1.0f) : fmaf(x, s, 1.0f));
+    return a;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reciprocal and reciprocal square root from an FP32 seed and one
+// Newton-Raphson step (the error squares: ~1e-14 relative).  Arguments far
+// outside the FP32 range take the full-precision operator instead.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double rcp_nr(double d)
+{
+    const double ad = fabs(d);
+    if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+    const double y = (double)__frcp_rn((float)d);
+    return fma(y, fma(-d, y, 1.0), y);
+}
+
+__device__ __forceinline__ double rsqrt_nr(double d)
+{
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+    const double y = (double)rsqrtf((float)d);
+    return fma(0.5 * y, fma(-d * y, y, 1.0), y);
+}
+
+__device__ __forceinline__ double sqrt_nr(double d)
+{
+    if (!(d > 1e-30 && d < 1e30)) return sqrt(d);
+    const float s0 = sqrtf((float)d);
+    const double s = (double)s0;
+    return fma(fma(-s, s, d), (double)(0.5f / s0), s);
 }
 
 // ---------------------------------------------------------------------------
@@ -243,44 +327,41 @@ __device__ __forceinline__ float kn_sample_t(float x, float u1, float F2)
 // update, where cancellation at large gamma breaks FP32):
 //   photon in the electron rest frame: k' = k + u [ (u.k)/(gamma+1) - eps ],
 //   direction n = k'/|k'|, scattered rest-frame photon of energy
-//   x/(1 + x t) at polar angle acos(1 - t) from n and azimuth phi in the
+//   x/(1 + x t) at polar angle theta' from n and azimuth phi in the
 //   orthonormal basis of Duff et al. (JCGT 6(1), 2017), boosted back with
 //   k1 = k1' + u [ (u.k1')/(gamma+1) + eps1' ], and u <- u + k - k1.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void collide_f64(float& ux, float& uy, float& uz, float& kx, float& ky, float& kz,
-                                            float x, float t, float u2)
+                                            float x, Angle ang, float u2)
 {
     const double U0 = ux, U1 = uy, U2 = uz, K0 = kx, K1 = ky, K2 = kz;
-    const double gamma = sqrt(1.0 + (U0 * U0 + U1 * U1 + U2 * U2));
-    const double eps = sqrt(K0 * K0 + K1 * K1 + K2 * K2);
+    const double gamma = sqrt_nr(1.0 + (U0 * U0 + U1 * U1 + U2 * U2));
+    const double eps = sqrt_nr(K0 * K0 + K1 * K1 + K2 * K2);
     const double uk = U0 * K0 + U1 * K1 + U2 * K2;
-    const double f = uk / (gamma + 1.0) - eps;
-    const double r0 = K0 + U0 * f, r1 = K1 + U1 * f, r2 = K2 + U2 * f;
-    const double inv = 1.0 / sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+    const double igp1 = rcp_nr(gamma + 1.0);
+    const double f = fma(uk, igp1, -eps);
+    const double r0 = fma(U0, f, K0), r1 = fma(U1, f, K1), r2 = fma(U2, f, K2);
+    const double inv = rsqrt_nr(r0 * r0 + r1 * r1 + r2 * r2);
     const double n0 = r0 * inv, n1 = r1 * inv, n2 = r2 * inv;
     // Duff et al. basis completing n
-    const double sg = copysign(1.0, n2);
-    const double a = -1.0 / (sg + n2);
+    const double sg = n2 >= 0.0 ? 1.0 : -1.0;
+    const double a = -rcp_nr(sg + n2);
     const double b = n0 * n1 * a;
-    const double b10 = 1.0 + sg * n0 * n0 * a, b11 = sg * b, b12 = -sg * n0;
-    const double b20 = b, b21 = sg + n1 * n1 * a, b22 = -n1;
+    const double b10 = fma(sg * n0 * n0, a, 1.0), b11 = sg * b, b12 = -sg * n0;
+    const double b20 = b, b21 = fma(n1 * n1, a, sg), b22 = -n1;
     float sphf, cphf;
     sincospif(2.0f * u2, &sphf, &cphf);
-    const double cth = 1.0 - (double)t;
-    const double sth = sqrt((double)t * (2.0 - (double)t));
-    const double xd = x;
-    const double e1r = xd / (1.0 + xd * (double)t);
-    const double cph = cphf, sph = sphf;
-    const double d0 = cth * n0 + sth * (cph * b10 + sph * b20);
-    const double d1 = cth * n1 + sth * (cph * b11 + sph * b21);
-    const double d2 = cth * n2 + sth * (cph * b12 + sph * b22);
+    const double cth = ang.cth, sth = ang.sth, cph = cphf, sph = sphf;
+    const double e1r = (double)x * (double)ang.ratio;
+    const double d0 = fma(cth, n0, sth * fma(cph, b10, sph * b20));
+    const double d1 = fma(cth, n1, sth * fma(cph, b11, sph * b21));
+    const double d2 = fma(cth, n2, sth * fma(cph, b12, sph * b22));
     const double q0 = e1r * d0, q1 = e1r * d1, q2 = e1r * d2;
-    const double uq = U0 * q0 + U1 * q1 + U2 * q2;
-    const double g = uq / (gamma + 1.0) + e1r;
-    const double k10 = q0 + U0 * g, k11 = q1 + U1 * g, k12 = q2 + U2 * g;
-    ux = (float)(U0 + K0 - k10);
-    uy = (float)(U1 + K1 - k11);
-    uz = (float)(U2 + K2 - k12);
+    const double g = fma(U0 * q0 + U1 * q1 + U2 * q2, igp1, e1r);
+    const double k10 = fma(U0, g, q0), k11 = fma(U1, g, q1), k12 = fma(U2, g, q2);
+    ux = (float)((U0 + K0) - k10);
+    uy = (float)((U1 + K1) - k11);
+    uz = (float)((U2 + K2) - k12);
     kx = (float)k10;
     ky = (float)k11;
     kz = (float)k12;

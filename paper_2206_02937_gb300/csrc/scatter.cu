@@ -1,23 +1,24 @@
 // scatter.cu -- probability, Bernoulli trial and collision of every pair
-// (arXiv 2206.02937, Sec. 3.1: "for each pair in this list, the probability
-// of interaction is then calculated and compared against a random number ...
-// for each pair deemed to collide, the kinetic collision is resolved and the
-// momentum of the particles is updated"; Sec. 3.2: the probability comes from
-// the Klein-Nishina cross section in the lepton rest frame, carried back to
-// the simulation frame).
+// (arXiv 2206.02937, Sec. 3.1: for each pair of the list the probability of
+// interaction is computed and compared with a random number, and each pair
+// deemed to collide has its kinetic collision resolved and its momenta
+// updated; Sec. 3.2: the probability comes from the Klein-Nishina cross
+// section in the lepton rest frame, carried back to the simulation frame).
 //
-// One fused kernel, one CTA per tile of 1024 pairs (256 threads x 4 pairs):
-//   phase 1  every pair: locate its cell (binary search in the tile's window
-//            of CellInfo records staged in shared memory), load the two
-//            momenta (coalesced: consecutive pairs are consecutive sorted
-//            particles), form x and v, sigma_KN, P = 1 - exp(-n dt s v), one
-//            Philox block, the Bernoulli decision; accepted pairs are
-//            appended to a shared-memory queue;
-//   phase 2  the queue is drained by all threads at full warp occupancy:
-//            inverse-CDF angle in FP32, rest-frame boost and momentum update
-//            in FP64, write-back of both momenta in place.
-// Accepted pairs are a few percent of all pairs, so compacting them keeps the
-// expensive branch from running with one live lane per warp.
+// One fused, persistent kernel.  Each CTA walks tiles of 1024 pairs
+// (256 threads x 4 pairs):
+//   phase 1  every pair of the tile: locate its cell (binary search in the
+//            tile's window of CellInfo records staged in shared memory), load
+//            both momenta (coalesced: consecutive pairs are consecutive
+//            sorted particles), form x and v, sigma_KN, P = 1 - exp(-n dt s v),
+//            one Philox block, the Bernoulli decision; accepted pairs are
+//            appended to a shared-memory queue that persists across tiles;
+//   phase 2  whenever the queue holds at least 256 entries, all 256 threads
+//            take one each: inverse-CDF angle in FP32, rest-frame boost and
+//            momentum update in FP64, write-back of both momenta in place.
+//            The last partial batch is drained after the final tile.
+// Accepted pairs are a few percent of all pairs; batching them keeps the
+// FP64 branch at full warp width instead of one live lane per warp.
 #include "ctx.hpp"
 #include "device_math.cuh"
 
@@ -26,6 +27,7 @@ namespace {
 
 constexpr int kScatterThreads = 256;
 constexpr int kPairsPerThread = kPairsPerTile / kScatterThreads;
+constexpr int kQueueCap = kPairsPerTile + kScatterThreads;
 
 struct ScatterArgs {
     float* u[3];  // electron momenta (sorted species, or explicit pair list)
@@ -45,7 +47,8 @@ struct ScatterArgs {
 
 struct QEntry {
     int32_t ie, ig;
-    float x, F2, u1, u2;
+    float x, F2;
+    uint32_t r1, r2;  // raw Philox words for the polar and azimuthal draws
 };
 
 __device__ __forceinline__ int find_cell(const CellInfo* win, int nwin, int64_t p)
@@ -58,120 +61,127 @@ __device__ __forceinline__ int find_cell(const CellInfo* win, int nwin, int64_t 
     return lo;
 }
 
+__device__ __forceinline__ void resolve(const ScatterArgs& a, const QEntry& e)
+{
+    float ux = a.u[0][e.ie], uy = a.u[1][e.ie], uz = a.u[2][e.ie];
+    float kx = a.k[0][e.ig], ky = a.k[1][e.ig], kz = a.k[2][e.ig];
+    const Angle ang = kn_sample_angle(e.x, e.r1 >> 8, e.F2);
+    collide_f64(ux, uy, uz, kx, ky, kz, e.x, ang, u24_closed0(e.r2));
+    a.u[0][e.ie] = ux;
+    a.u[1][e.ie] = uy;
+    a.u[2][e.ie] = uz;
+    a.k[0][e.ig] = kx;
+    a.k[1][e.ig] = ky;
+    a.k[2][e.ig] = kz;
+}
+
 template <bool kBinned>
-__global__ void __launch_bounds__(kScatterThreads) k_scatter(ScatterArgs a)
+__global__ void __launch_bounds__(kScatterThreads, 3) k_scatter(ScatterArgs a)
 {
     __shared__ CellInfo win[kCellWindow];
-    __shared__ QEntry queue[kPairsPerTile];
+    __shared__ QEntry queue[kQueueCap];
     __shared__ int qn;
     __shared__ unsigned red_pairs, red_scat;
 
-    const int64_t total = kBinned ? *a.n_pairs : a.n_explicit;
-    const int64_t p0 = (int64_t)blockIdx.x * kPairsPerTile;
-    if (p0 >= total) return;
     const int tid = threadIdx.x;
-
-    int c_first = 0, nwin = 0;
-    bool use_win = true;
-    if (kBinned) {
-        c_first = a.tile_cell[blockIdx.x];
-        const int c_last = a.tile_cell[blockIdx.x + 1];
-        nwin = c_last - c_first + 1;
-        use_win = nwin <= kCellWindow;
-        if (use_win)
-            for (int i = tid; i < nwin; i += kScatterThreads) win[i] = a.cinfo[c_first + i];
-    }
+    const int64_t total = kBinned ? *a.n_pairs : a.n_explicit;
+    const int64_t n_tiles = (total + kPairsPerTile - 1) / kPairsPerTile;
     if (tid == 0) {
         qn = 0;
         red_pairs = 0;
         red_scat = 0;
     }
-    __syncthreads();
+    unsigned my_pairs = 0, my_scat = 0;
 
-    // ---------------- phase 1: every pair ----------------
-    int ie[kPairsPerThread], ig[kPairsPerThread];
-    float dens[kPairsPerThread];
-    bool valid[kPairsPerThread];
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t p0 = tile * kPairsPerTile;
+        int c_first = 0, nwin = 0;
+        bool use_win = true;
+        if (kBinned) {
+            c_first = a.tile_cell[tile];
+            const int c_last = a.tile_cell[tile + 1];
+            nwin = c_last - c_first + 1;
+            use_win = nwin <= kCellWindow;
+            if (use_win)
+                for (int i = tid; i < nwin; i += kScatterThreads) win[i] = a.cinfo[c_first + i];
+        }
+        __syncthreads();
+
+        // ---------------- phase 1: every pair of the tile ----------------
+        int ie[kPairsPerThread], ig[kPairsPerThread];
+        float dens[kPairsPerThread];
+        bool valid[kPairsPerThread];
 #pragma unroll
-    for (int r = 0; r < kPairsPerThread; ++r) {
-        const int64_t p = p0 + r * kScatterThreads + tid;
-        valid[r] = p < total;
-        ie[r] = 0;
-        ig[r] = 0;
-        dens[r] = 0.0f;
-        if (valid[r]) {
-            if (kBinned) {
-                CellInfo ci;
-                if (use_win) {
-                    ci = win[find_cell(win, nwin, p)];
+        for (int r = 0; r < kPairsPerThread; ++r) {
+            const int64_t p = p0 + r * kScatterThreads + tid;
+            valid[r] = p < total;
+            ie[r] = 0;
+            ig[r] = 0;
+            dens[r] = 0.0f;
+            if (valid[r]) {
+                if (kBinned) {
+                    const CellInfo ci = use_win ? win[find_cell(win, nwin, p)]
+                                                : a.cinfo[c_first + find_cell(a.cinfo + c_first, nwin, p)];
+                    const int j = (int)(p - ci.pair_off);
+                    ie[r] = ci.e_start + j;
+                    ig[r] = ci.g_start + j;
+                    dens[r] = ci.dens;
                 } else {
-                    ci = a.cinfo[c_first + find_cell(a.cinfo + c_first, nwin, p)];
+                    ie[r] = (int)p;
+                    ig[r] = (int)p;
+                    dens[r] = a.n_dens[p];
                 }
-                const int j = (int)(p - ci.pair_off);
-                ie[r] = ci.e_start + j;
-                ig[r] = ci.g_start + j;
-                dens[r] = ci.dens;
-            } else {
-                ie[r] = (int)p;
-                ig[r] = (int)p;
-                dens[r] = a.n_dens[p];
             }
         }
-    }
-    float ux[kPairsPerThread], uy[kPairsPerThread], uz[kPairsPerThread];
-    float kx[kPairsPerThread], ky[kPairsPerThread], kz[kPairsPerThread];
+        float ux[kPairsPerThread], uy[kPairsPerThread], uz[kPairsPerThread];
+        float kx[kPairsPerThread], ky[kPairsPerThread], kz[kPairsPerThread];
 #pragma unroll
-    for (int r = 0; r < kPairsPerThread; ++r) {
-        if (valid[r]) {
-            ux[r] = a.u[0][ie[r]];
-            uy[r] = a.u[1][ie[r]];
-            uz[r] = a.u[2][ie[r]];
-            kx[r] = a.k[0][ig[r]];
-            ky[r] = a.k[1][ig[r]];
-            kz[r] = a.k[2][ig[r]];
-        } else {
-            ux[r] = uy[r] = uz[r] = kx[r] = ky[r] = kz[r] = 0.0f;
+        for (int r = 0; r < kPairsPerThread; ++r) {
+            if (valid[r]) {
+                ux[r] = a.u[0][ie[r]];
+                uy[r] = a.u[1][ie[r]];
+                uz[r] = a.u[2][ie[r]];
+                kx[r] = a.k[0][ig[r]];
+                ky[r] = a.k[1][ig[r]];
+                kz[r] = a.k[2][ig[r]];
+            } else {
+                ux[r] = uy[r] = uz[r] = kx[r] = ky[r] = kz[r] = 0.0f;
+            }
         }
-    }
-    unsigned my_pairs = 0, my_scat = 0;
 #pragma unroll
-    for (int r = 0; r < kPairsPerThread; ++r) {
-        if (!valid[r]) continue;
-        const int64_t p = p0 + r * kScatterThreads + tid;
-        const Invariants inv = invariants_f32(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r]);
-        float x = inv.x, v = inv.v;
-        if (inv.gamma > a.gamma64) invariants_f64(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r], &x, &v);
-        const float F2 = kn_F(x, 2.0f);
-        const float sig = 0.375f * F2;
-        const float P = inv.eps > 0.0f ? -expm1f(-(dens[r] * a.dt * sig * v)) : 0.0f;
-        const Philox4 rnd = draw(a.seed, a.step, kStreamScatter, (uint32_t)p);
-        const bool hit = u24_closed0(rnd.r0) < P;
-        if (a.prob_out) a.prob_out[p] = P;
-        if (a.flag_out) a.flag_out[p] = hit ? 1 : 0;
-        ++my_pairs;
-        if (hit) {
-            ++my_scat;
-            const int slot = atomicAdd(&qn, 1);
-            queue[slot] = QEntry{ie[r], ig[r], x, F2, u24_open(rnd.r1), u24_closed0(rnd.r2)};
+        for (int r = 0; r < kPairsPerThread; ++r) {
+            if (!valid[r]) continue;
+            const int64_t p = p0 + r * kScatterThreads + tid;
+            const Invariants inv = invariants_f32(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r]);
+            float x = inv.x, v = inv.v;
+            if (inv.gamma > a.gamma64) invariants_f64(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r], &x, &v);
+            const float F2 = kn_F(x, 2.0f);
+            const float sig = 0.375f * F2;
+            const float P = inv.eps > 0.0f ? -expm1f(-(dens[r] * a.dt * sig * v)) : 0.0f;
+            const Philox4 rnd = draw(a.seed, a.step, kStreamScatter, (uint32_t)p);
+            const bool hit = u24_closed0(rnd.r0) < P;
+            if (a.prob_out) a.prob_out[p] = P;
+            if (a.flag_out) a.flag_out[p] = hit ? 1 : 0;
+            ++my_pairs;
+            if (hit) {
+                ++my_scat;
+                const int slot = atomicAdd(&qn, 1);
+                queue[slot] = QEntry{ie[r], ig[r], x, F2, rnd.r1, rnd.r2};
+            }
         }
+        __syncthreads();
+
+        // ---------------- phase 2: full batches of accepted pairs ----------------
+        int nq = qn;
+        while (nq >= kScatterThreads) {
+            resolve(a, queue[nq - kScatterThreads + tid]);
+            nq -= kScatterThreads;
+        }
+        __syncthreads();
+        if (tid == 0) qn = nq;
     }
     __syncthreads();
-
-    // ---------------- phase 2: accepted pairs only ----------------
-    const int nq = qn;
-    for (int q = tid; q < nq; q += kScatterThreads) {
-        const QEntry e = queue[q];
-        float eux = a.u[0][e.ie], euy = a.u[1][e.ie], euz = a.u[2][e.ie];
-        float gkx = a.k[0][e.ig], gky = a.k[1][e.ig], gkz = a.k[2][e.ig];
-        const float t = kn_sample_t(e.x, e.u1, e.F2);
-        collide_f64(eux, euy, euz, gkx, gky, gkz, e.x, t, e.u2);
-        a.u[0][e.ie] = eux;
-        a.u[1][e.ie] = euy;
-        a.u[2][e.ie] = euz;
-        a.k[0][e.ig] = gkx;
-        a.k[1][e.ig] = gky;
-        a.k[2][e.ig] = gkz;
-    }
+    if (tid < qn) resolve(a, queue[tid]);
 
     // ---------------- counters ----------------
 #pragma unroll
@@ -184,7 +194,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(ScatterArgs a)
         atomicAdd(&red_scat, my_scat);
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && red_pairs) {
         atomicAdd(&a.stats->pairs_tested, (unsigned long long)red_pairs);
         atomicAdd(&a.stats->scatters, (unsigned long long)red_scat);
     }
@@ -203,6 +213,35 @@ __global__ void k_kn_ratio(const float* __restrict__ ux, const float* __restrict
         if (inv.gamma > gamma64) invariants_f64(a0, a1, a2, b0, b1, b2, &x, &v);
         r_out[i] = inv.eps > 0.0f ? 0.5f * kn_sigma(x) * v : 0.0f;
     }
+}
+
+__global__ void k_sample_angle(const float* __restrict__ x, const uint32_t* __restrict__ r, int64_t n,
+                               float* __restrict__ cth, float* __restrict__ sth, float* __restrict__ ratio)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float xi = x[i];
+        const Angle ang = kn_sample_angle(xi, r[i] >> 8, kn_F(xi, 2.0f));
+        cth[i] = ang.cth;
+        sth[i] = ang.sth;
+        ratio[i] = ang.ratio;
+    }
+}
+
+template <bool kBinned>
+int persistent_grid(int64_t max_pairs)
+{
+    static int per_sm = 0, n_sm = 0;
+    if (per_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<kBinned>, kScatterThreads, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int64_t tiles = (max_pairs + kPairsPerTile - 1) / kPairsPerTile;
+    const int64_t full = (int64_t)per_sm * n_sm;
+    return (int)(tiles < full ? tiles : full);
 }
 
 }  // namespace
@@ -232,8 +271,7 @@ compton_status launch_scatter_binned(compton_ctx* ctx, compton_species* e, compt
     a.prob_out = prob_out;
     a.flag_out = flag_out;
     a.stats = ctx->stats;
-    const int64_t tiles = (pairs->max_pairs + kPairsPerTile - 1) / kPairsPerTile;
-    k_scatter<true><<<(unsigned)tiles, kScatterThreads, 0, stream>>>(a);
+    k_scatter<true><<<persistent_grid<true>(pairs->max_pairs), kScatterThreads, 0, stream>>>(a);
     COMPTON_LAUNCH_CHECK(ctx, "k_scatter<binned>");
     return COMPTON_OK;
 }
@@ -262,8 +300,7 @@ compton_status launch_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, floa
     a.prob_out = prob_out;
     a.flag_out = flag_out;
     a.stats = ctx->stats;
-    const int64_t tiles = (n + kPairsPerTile - 1) / kPairsPerTile;
-    k_scatter<false><<<(unsigned)tiles, kScatterThreads, 0, stream>>>(a);
+    k_scatter<false><<<persistent_grid<false>(n), kScatterThreads, 0, stream>>>(a);
     COMPTON_LAUNCH_CHECK(ctx, "k_scatter<pairs>");
     return COMPTON_OK;
 }
@@ -277,6 +314,16 @@ compton_status launch_kn_ratio(compton_ctx* ctx, const float* ux, const float* u
     k_kn_ratio<<<(unsigned)blocks, 256, 0, stream>>>(ux, uy, uz, kx, ky, kz, n, ctx->cfg.gamma_fp64_threshold,
                                                      r_out);
     COMPTON_LAUNCH_CHECK(ctx, "k_kn_ratio");
+    return COMPTON_OK;
+}
+
+compton_status launch_sample_angle(compton_ctx* ctx, const float* x, const uint32_t* r, int64_t n, float* cth,
+                                   float* sth, float* ratio, cudaStream_t stream)
+{
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_sample_angle<<<(unsigned)blocks, 256, 0, stream>>>(x, r, n, cth, sth, ratio);
+    COMPTON_LAUNCH_CHECK(ctx, "k_sample_angle");
     return COMPTON_OK;
 }
 
