@@ -340,6 +340,83 @@ __device__ __forceinline__ void warp_rank_segment(const uint32_t* key, const uin
     }
 }
 
+// Sort the segment [a, a+n) (n <= 32 E) with one warp: a bitonic network over
+// 32 E slots held E per lane (slot i = 32 e + lane), keys (key << 32 | id) with
+// the shared-memory index as the final tie-break, so the order is a total one
+// and the network always yields a permutation.  Strides below 32 exchange
+// through shuffles, larger ones swap registers.  perm[a + rank] = index.
+template <int E>
+__device__ __forceinline__ void warp_bitonic_segment(const uint32_t* key, const uint32_t* sid, int32_t* perm,
+                                                     int a, int n)
+{
+    const int lane = (int)lane_id();
+    uint64_t k[E];
+    int32_t p[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = e * 32 + lane;
+        if (i < n) {
+            k[e] = ((uint64_t)key[a + i] << 32) | sid[a + i];
+            p[e] = a + i;
+        } else {
+            k[e] = ~0ull;
+            p[e] = 0x40000000 + i;  // padding sorts last, still totally ordered
+        }
+    }
+    constexpr int N = 32 * E;
+#pragma unroll
+    for (int kk = 2; kk <= N; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int je = j >> 5;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if ((e & je) == 0) {
+                        const int e2 = e | je;
+                        const bool asc = ((e * 32 + lane) & kk) == 0;
+                        const bool gt = (k[e] > k[e2]) || (k[e] == k[e2] && p[e] > p[e2]);
+                        if (gt == asc) {
+                            const uint64_t tk = k[e];
+                            k[e] = k[e2];
+                            k[e2] = tk;
+                            const int32_t tp = p[e];
+                            p[e] = p[e2];
+                            p[e2] = tp;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const uint64_t ok = __shfl_xor_sync(0xffffffffu, k[e], j);
+                    const int32_t op = __shfl_xor_sync(0xffffffffu, p[e], j);
+                    const bool take_min = (((lane & j) == 0) == (((e * 32 + lane) & kk) == 0));
+                    const bool other_smaller = (ok < k[e]) || (ok == k[e] && op < p[e]);
+                    if (take_min == other_smaller) {
+                        k[e] = ok;
+                        p[e] = op;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = e * 32 + lane;
+        if (i < n) perm[a + i] = p[e];
+    }
+}
+
+__device__ __forceinline__ void sort_segment(const uint32_t* key, const uint32_t* sid, int32_t* perm, int a, int n)
+{
+    if (n <= 32) warp_bitonic_segment<1>(key, sid, perm, a, n);
+    else if (n <= 64) warp_bitonic_segment<2>(key, sid, perm, a, n);
+    else if (n <= 128) warp_bitonic_segment<4>(key, sid, perm, a, n);
+    else if (n <= 256) warp_bitonic_segment<8>(key, sid, perm, a, n);
+    else warp_rank_segment(key, sid, perm, a, n);
+}
+
 __device__ __forceinline__ void gather_out(const SortGatherArgs& g, int s, const uint32_t* src, const uint32_t* sid,
                                            const int32_t* perm, int64_t o0, int R)
 {
@@ -391,7 +468,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_gather(SortGatherArgs g)
         for (int64_t c = c0 + warp; c < c1; c += nwarps) {
             const int a = off[c] - (int32_t)o0;
             const int n = off[c + 1] - off[c];
-            if (n > 0) warp_rank_segment(key, sid, perm, a, n);
+            if (n > 0) sort_segment(key, sid, perm, a, n);
         }
         __syncthreads();
         gather_out(g, s, src, sid, perm, o0, (int)R);

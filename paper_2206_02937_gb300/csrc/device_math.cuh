@@ -33,16 +33,14 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint3
 {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t lo0 = 0xD2511F53u * c0;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
-        const uint32_t n0 = hi1 ^ c1 ^ k0;
-        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;  // one wide multiply: high and low halves
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
         c0 = n0;
-        c1 = lo1;
+        c1 = (uint32_t)p1;
         c2 = n2;
-        c3 = lo0;
+        c3 = (uint32_t)p0;
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
@@ -160,19 +158,18 @@ __device__ __forceinline__ void invariants_f64(float ux, float uy, float uz, flo
 // w/(1+w) = 2z/(1+z)) and q = z/x = t/(2+w) it becomes
 //   C = 4 q^2 [ z S1 + 1/(1+z) - q S2 ],   B = 2 q (1 + z^2 S1),
 //   S1 = sum_{j>=1} z^(2j-2)/(2j+1),  S2 = sum_{j>=1} 2j/(2j+1) z^(2j-2),
-// series of positive terms; for -0.6 < w < 1 (z^2 < 0.19) twelve terms reach
-// FP32 precision.  Outside that range the closed forms lose only a few bits.
-// sigma/sigma_T = 3/8 F(x, 2).
+// series of positive terms; since sum_{j>=1} z^(2j-2) = 1/(1 - z^2),
+// S2 = 1/(1 - z^2) - S1 (about 2/3: no cancellation), so only S1 is summed.
+// For -0.6 < w < 1 (z^2 < 0.19) twelve terms reach FP32 precision.  Outside
+// that range the closed forms lose only a few bits.  sigma/sigma_T = 3/8 F(x, 2).
 // ---------------------------------------------------------------------------
+template <int kTerms>
 __device__ __forceinline__ void kn_series(float z2, float& S1, float& S2)
 {
     S1 = 0.0f;
-    S2 = 0.0f;
 #pragma unroll
-    for (int j = 12; j >= 1; --j) {
-        S1 = fmaf(S1, z2, 1.0f / (float)(2 * j + 1));
-        S2 = fmaf(S2, z2, (float)(2 * j) / (float)(2 * j + 1));
-    }
+    for (int j = kTerms; j >= 1; --j) S1 = fmaf(S1, z2, 1.0f / (float)(2 * j + 1));
+    S2 = __fdividef(1.0f, 1.0f - z2) - S1;
 }
 
 // C(x, t) in the series range -0.6 < x t < 1 (x may be negative).
@@ -182,7 +179,7 @@ __device__ __forceinline__ float kn_C_series(float x, float t)
     const float q = __fdividef(t, 2.0f + w);
     const float z = x * q;
     float S1, S2;
-    kn_series(z * z, S1, S2);
+    kn_series<12>(z * z, S1, S2);
     return 4.0f * q * q * (fmaf(z, S1, __fdividef(1.0f, 1.0f + z)) - q * S2);
 }
 
@@ -196,7 +193,7 @@ __device__ __forceinline__ float kn_F(float x, float t)
         const float z = x * q;
         const float z2 = z * z;
         float S1, S2;
-        kn_series(z2, S1, S2);
+        kn_series<12>(z2, S1, S2);
         const float B = 2.0f * q * fmaf(z2, S1, 1.0f);
         const float C = 4.0f * q * q * (fmaf(z, S1, __fdividef(1.0f, 1.0f + z)) - q * S2);
         return A + B - C;
@@ -244,7 +241,27 @@ __device__ __forceinline__ float kn_f_upper(float x, float s)
 }
 
 // sigma_KN(x) / sigma_T
-__device__ __forceinline__ float kn_sigma(float x) { return 0.375f * kn_F(x, 2.0f); }
+// F(x, 2) = (8/3) sigma_KN(x)/sigma_T, the total of the angular cumulative.  At
+// t = 2: w = 2x, q = 1/(1+x), z = x/(1+x), A = 2(1+x)/(1+2x)^2; in the series
+// range (x < 1/2, z^2 < 1/9) eight terms of S1 suffice.
+__device__ __forceinline__ float kn_F2(float x)
+{
+    if (x < 0.5f) {
+        const float q = __fdividef(1.0f, 1.0f + x);
+        const float z = x * q;
+        const float z2 = z * z;
+        float S1, S2;
+        kn_series<8>(z2, S1, S2);
+        const float opw = fmaf(2.0f, x, 1.0f);
+        const float A = __fdividef(2.0f * (1.0f + x), opw * opw);
+        const float B = 2.0f * q * fmaf(z2, S1, 1.0f);
+        const float C = 4.0f * q * q * (fmaf(z, S1, __fdividef(1.0f, 1.0f + z)) - q * S2);
+        return A + B - C;
+    }
+    return kn_F(x, 2.0f);
+}
+
+__device__ __forceinline__ float kn_sigma(float x) { return 0.375f * kn_F2(x); }
 
 // ---------------------------------------------------------------------------
 // Scattering angle from the 24-bit draw r24 (u1 = (r24 + 1/2) 2^-24).

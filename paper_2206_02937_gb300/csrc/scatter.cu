@@ -108,20 +108,26 @@ __global__ void __launch_bounds__(kScatterThreads, 3) k_scatter(ScatterArgs a)
         __syncthreads();
 
         // ---------------- phase 1: every pair of the tile ----------------
+        // Thread tid takes the 4 consecutive pairs p0 + 4 tid + r: one binary
+        // search for the first, a forward step (usually none) for the others.
         int ie[kPairsPerThread], ig[kPairsPerThread];
         float dens[kPairsPerThread];
         bool valid[kPairsPerThread];
+        const int64_t pb = p0 + (int64_t)tid * kPairsPerThread;
+        const CellInfo* cw = use_win ? win : a.cinfo + c_first;
+        int ci_idx = 0;
+        if (kBinned && pb < total) ci_idx = find_cell(cw, nwin, pb);
 #pragma unroll
         for (int r = 0; r < kPairsPerThread; ++r) {
-            const int64_t p = p0 + r * kScatterThreads + tid;
+            const int64_t p = pb + r;
             valid[r] = p < total;
             ie[r] = 0;
             ig[r] = 0;
             dens[r] = 0.0f;
             if (valid[r]) {
                 if (kBinned) {
-                    const CellInfo ci = use_win ? win[find_cell(win, nwin, p)]
-                                                : a.cinfo[c_first + find_cell(a.cinfo + c_first, nwin, p)];
+                    while (ci_idx + 1 < nwin && (int64_t)cw[ci_idx + 1].pair_off <= p) ++ci_idx;
+                    const CellInfo ci = cw[ci_idx];
                     const int j = (int)(p - ci.pair_off);
                     ie[r] = ci.e_start + j;
                     ig[r] = ci.g_start + j;
@@ -151,11 +157,11 @@ __global__ void __launch_bounds__(kScatterThreads, 3) k_scatter(ScatterArgs a)
 #pragma unroll
         for (int r = 0; r < kPairsPerThread; ++r) {
             if (!valid[r]) continue;
-            const int64_t p = p0 + r * kScatterThreads + tid;
+            const int64_t p = pb + r;
             const Invariants inv = invariants_f32(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r]);
             float x = inv.x, v = inv.v;
             if (inv.gamma > a.gamma64) invariants_f64(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r], &x, &v);
-            const float F2 = kn_F(x, 2.0f);
+            const float F2 = kn_F2(x);
             const float sig = 0.375f * F2;
             const float P = inv.eps > 0.0f ? -expm1f(-(dens[r] * a.dt * sig * v)) : 0.0f;
             const Philox4 rnd = draw(a.seed, a.step, kStreamScatter, (uint32_t)p);
@@ -221,7 +227,7 @@ __global__ void k_sample_angle(const float* __restrict__ x, const uint32_t* __re
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float xi = x[i];
-        const Angle ang = kn_sample_angle(xi, r[i] >> 8, kn_F(xi, 2.0f));
+        const Angle ang = kn_sample_angle(xi, r[i] >> 8, kn_F2(xi));
         cth[i] = ang.cth;
         sth[i] = ang.sth;
         ratio[i] = ang.ratio;

@@ -48,7 +48,8 @@ def test_draw_by_draw_including_tails():
         c_ref, s_ref = 1.0 - t, math.sqrt(t * (2.0 - t))
         # angle error in radians, and the Compton ratio
         assert math.hypot(cth[i] - c_ref, sth[i] - s_ref) < 3e-6, (x, r >> 8, cth[i], c_ref, sth[i], s_ref)
-        assert ratio[i] == pytest.approx(1.0 / (1.0 + x32 * t), rel=2e-6)
+        # d ratio / ratio = x ratio dt: at x = 3e3 an FP32 t gives a few 1e-6
+        assert ratio[i] == pytest.approx(1.0 / (1.0 + x32 * t), rel=1e-5)
 
 
 @pytest.mark.parametrize("x", [1e-4, 1e-2, 1.0, 100.0])
