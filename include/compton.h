@@ -69,6 +69,10 @@ typedef struct compton_config {
     int32_t device;              /* CUDA device ordinal                                        */
     float gamma_fp64_threshold;  /* electrons with gamma above this get the pair invariants
                                     recomputed in FP64 (0 = always, inf = never)               */
+    float collide_fp64_threshold; /* collisions with gamma * eps above this run the boost and
+                                    momentum update in FP64, below it in FP32 (whose error
+                                    relative to gamma + eps stays below 2e-6 up to 8);
+                                    0 = always FP64                                            */
     uint64_t mem_budget_bytes;   /* cap on library-owned device memory (0 = no cap)            */
 } compton_config;
 
@@ -195,6 +199,52 @@ compton_status compton_kn_ratio(struct compton_ctx* ctx, const float* ux_dev, co
                                 const float* uz_dev, const float* kx_dev, const float* ky_dev,
                                 const float* kz_dev, int64_t n, float* r_out_dev,
                                 compton_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Surrogate network (Sec. 2: a network object loaded once from exported   */
+/* parameters and run on any batch; Sec. 3.2: it replaces the probability */
+/* calculation).  Architecture: 6 inputs, 4 hidden layers of 64 SiLU       */
+/* units, 1 sigmoid output predicting r = sigma_KN v / (2 sigma_T), the    */
+/* probability normalised by the cell maximum P_max = 2 sigma_T c dt max w.*/
+/* Inputs f = [sgnlog(u/s_u)/n_u, sgnlog(k/s_k)/n_k], sgnlog(z) =          */
+/* sign(z) ln(1 + |z|).                                                    */
+/* Parameter vector (12993 floats): W0 (64x6), b0 (64), W1 (64x64), b1,    */
+/* W2, b2, W3, b3, W4 (1x64), b4; each W row-major (out, in).              */
+/* ---------------------------------------------------------------------- */
+
+/* Copy the parameters from host memory (n_params must be 12993), reset the
+ * Adam moments, and build the BF16 / FP8 / FP32 weight images the kernels
+ * read.  feature_scales_host (nullable) = {s_u, n_u, s_k, n_k}, all > 0;
+ * default {1, 7, 1e-4, 10}.  Synchronous. */
+compton_status compton_mlp_set_params(struct compton_ctx* ctx, const float* theta_host, int64_t n_params,
+                                      const float* feature_scales_host);
+
+/* Copy the current FP32 parameters to host memory.  Synchronous. */
+compton_status compton_mlp_get_params(struct compton_ctx* ctx, float* theta_host, int64_t n_params);
+
+/* Set the FP8 per-tensor activation scales from a calibration batch: the
+ * input of each hidden layer is stored as E4M3(h * 448 / max|h|) with the
+ * maxima measured by an FP32 forward pass over the n pairs given. */
+compton_status compton_mlp_calibrate(struct compton_ctx* ctx, const float* ux_dev, const float* uy_dev,
+                                     const float* uz_dev, const float* kx_dev, const float* ky_dev,
+                                     const float* kz_dev, int64_t n, compton_stream_t stream);
+
+/* r_out_dev[i] = network(u[i], k[i]) for i < n, in the precision `mode`
+ * selects (MLP_FP32: CUDA cores; MLP_BF16, MLP_FP8: tensor cores with FP32
+ * accumulation).  ENOMODEL before compton_mlp_set_params / load. */
+compton_status compton_mlp_infer(struct compton_ctx* ctx, const float* ux_dev, const float* uy_dev,
+                                 const float* uz_dev, const float* kx_dev, const float* ky_dev,
+                                 const float* kz_dev, int64_t n, compton_mode mode, float* r_out_dev,
+                                 compton_stream_t stream);
+
+/* Serialise the network (format "CMLP" version 1: header with the Adam step,
+ * feature and activation scales, then parameters and both Adam moments) to
+ * buf.  With buf NULL, *len receives the size needed; ERANGE if *len is too
+ * small.  Synchronous. */
+compton_status compton_mlp_save(struct compton_ctx* ctx, void* buf, size_t* len);
+
+/* Load a blob written by compton_mlp_save.  EINVAL on a bad header or size. */
+compton_status compton_mlp_load(struct compton_ctx* ctx, const void* buf, size_t len);
 
 /* The scattering-angle sampler of compton_scatter_step on its own, for
  * validation (the paper resolves each collision by sampling the scattered

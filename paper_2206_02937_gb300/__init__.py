@@ -28,7 +28,7 @@ MODE_PLAIN, MODE_MLP_FP32, MODE_MLP_BF16, MODE_MLP_FP8 = range(4)
 class compton_config(ctypes.Structure):
     _fields_ = [("n_cells", c_i64), ("max_particles", c_i64), ("w_over_v", c_f64), ("dt", c_f64),
                 ("seed", c_u64), ("device", c_i32), ("gamma_fp64_threshold", c_f32),
-                ("mem_budget_bytes", c_u64)]
+                ("collide_fp64_threshold", c_f32), ("mem_budget_bytes", c_u64)]
 
 
 class compton_species(ctypes.Structure):
@@ -138,9 +138,10 @@ class Species:
 
 
 def compton_init(n_cells: int, max_particles: int, w_over_v: float, dt: float, seed: int, device: int = 0,
-                 gamma_fp64_threshold: float = 1.0e3, mem_budget_bytes: int = 0) -> int:
+                 gamma_fp64_threshold: float = 1.0e3, mem_budget_bytes: int = 0,
+                 collide_fp64_threshold: float = 8.0) -> int:
     cfg = compton_config(n_cells, max_particles, w_over_v, dt, seed, device, gamma_fp64_threshold,
-                         mem_budget_bytes)
+                         collide_fp64_threshold, mem_budget_bytes)
     out = c_p()
     _check(lib().compton_init(ctypes.byref(cfg), ctypes.byref(out)), "compton_init")
     return out.value
@@ -201,3 +202,61 @@ def compton_kn_sample_angle(ctx: int, x, r, cth_out, sth_out, ratio_out, stream=
     n = int(x.shape[0])
     _check(lib().compton_kn_sample_angle(c_p(ctx), _ptr(x), _ptr(r), n, _ptr(cth_out), _ptr(sth_out),
                                          _ptr(ratio_out), _stream_ptr(stream)), "compton_kn_sample_angle", ctx)
+
+
+SIGNATURES.update({
+    "compton_mlp_set_params": (c_i32, [c_p, c_p, c_i64, c_p]),
+    "compton_mlp_get_params": (c_i32, [c_p, c_p, c_i64]),
+    "compton_mlp_calibrate": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_i64, c_p]),
+    "compton_mlp_infer": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_i64, c_i32, c_p, c_p]),
+    "compton_mlp_save": (c_i32, [c_p, c_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "compton_mlp_load": (c_i32, [c_p, c_p, ctypes.c_size_t]),
+})
+
+N_MLP_PARAMS = 12993
+
+
+def _host_f32(a):
+    import numpy as np
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def compton_mlp_set_params(ctx: int, theta, feature_scales=None) -> None:
+    th = _host_f32(theta)
+    fs = None if feature_scales is None else _host_f32(feature_scales)
+    _check(lib().compton_mlp_set_params(c_p(ctx), c_p(th.ctypes.data), int(th.shape[0]),
+                                        c_p(0) if fs is None else c_p(fs.ctypes.data)),
+           "compton_mlp_set_params", ctx)
+
+
+def compton_mlp_get_params(ctx: int):
+    import numpy as np
+    th = np.zeros(N_MLP_PARAMS, dtype=np.float32)
+    _check(lib().compton_mlp_get_params(c_p(ctx), c_p(th.ctypes.data), N_MLP_PARAMS), "compton_mlp_get_params", ctx)
+    return th
+
+
+def compton_mlp_calibrate(ctx: int, u, k, stream=None) -> None:
+    n = int(u.shape[1])
+    _check(lib().compton_mlp_calibrate(c_p(ctx), _ptr(u[0]), _ptr(u[1]), _ptr(u[2]), _ptr(k[0]), _ptr(k[1]),
+                                       _ptr(k[2]), n, _stream_ptr(stream)), "compton_mlp_calibrate", ctx)
+
+
+def compton_mlp_infer(ctx: int, u, k, mode: int, r_out, stream=None) -> None:
+    n = int(u.shape[1])
+    _check(lib().compton_mlp_infer(c_p(ctx), _ptr(u[0]), _ptr(u[1]), _ptr(u[2]), _ptr(k[0]), _ptr(k[1]),
+                                   _ptr(k[2]), n, int(mode), _ptr(r_out), _stream_ptr(stream)),
+           "compton_mlp_infer", ctx)
+
+
+def compton_mlp_save(ctx: int) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(lib().compton_mlp_save(c_p(ctx), c_p(0), ctypes.byref(n)), "compton_mlp_save", ctx)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().compton_mlp_save(c_p(ctx), ctypes.cast(buf, c_p), ctypes.byref(n)), "compton_mlp_save", ctx)
+    return buf.raw[:n.value]
+
+
+def compton_mlp_load(ctx: int, blob: bytes) -> None:
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(lib().compton_mlp_load(c_p(ctx), ctypes.cast(buf, c_p), len(blob)), "compton_mlp_load", ctx)

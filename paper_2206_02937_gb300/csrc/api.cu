@@ -79,6 +79,7 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     if (cfg->max_particles < 0 || cfg->max_particles >= INT32_MAX - compton::kSortCap) return COMPTON_EINVAL;
     if (!(cfg->dt >= 0.0) || !(cfg->w_over_v >= 0.0) || std::isinf(cfg->dt) || std::isinf(cfg->w_over_v))
         return COMPTON_EINVAL;
+    if (!(cfg->gamma_fp64_threshold >= 0.0f) || !(cfg->collide_fp64_threshold >= 0.0f)) return COMPTON_EINVAL;
     compton_ctx* ctx = new (std::nothrow) compton_ctx();
     if (!ctx) return COMPTON_ENOMEM;
     ctx->cfg = *cfg;
@@ -107,6 +108,13 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     size_t o_tc = cv.take<int32_t>(ctx->max_pair_tiles + 1);
     size_t o_np = cv.take<int64_t>(1);
     size_t o_st = cv.take<compton::DeviceStats>(1);
+    const size_t NP = compton::kMlpParams;
+    size_t o_th = cv.take<float>(NP), o_gr = cv.take<float>(NP), o_am = cv.take<float>(NP),
+           o_av = cv.take<float>(NP);
+    size_t o_wb = cv.take<uint8_t>(4 * 8192), o_w8 = cv.take<uint8_t>(4 * 8192), o_wt = cv.take<float>(4 * 4096);
+    size_t o_bi = cv.take<float>(256), o_w4 = cv.take<float>(64), o_b4 = cv.take<float>(1);
+    size_t o_sw = cv.take<float>(4), o_swi = cv.take<float>(4), o_sai = cv.take<float>(4), o_lo = cv.take<float>(2),
+           o_ax = cv.take<float>(4);
     const size_t total = align_up(cv.used, 256);
     if (cfg->mem_budget_bytes && total > cfg->mem_budget_bytes) {
         delete ctx;
@@ -131,6 +139,26 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     ctx->tile_cell = reinterpret_cast<int32_t*>(base + o_tc);
     ctx->n_pairs = reinterpret_cast<int64_t*>(base + o_np);
     ctx->stats = reinterpret_cast<compton::DeviceStats*>(base + o_st);
+    compton::MlpDev& m = ctx->mlp;
+    m.theta = reinterpret_cast<float*>(base + o_th);
+    m.grad = reinterpret_cast<float*>(base + o_gr);
+    m.adam_m = reinterpret_cast<float*>(base + o_am);
+    m.adam_v = reinterpret_cast<float*>(base + o_av);
+    m.wbf16 = base + o_wb;
+    m.wfp8 = base + o_w8;
+    m.wt32 = reinterpret_cast<float*>(base + o_wt);
+    m.bias = reinterpret_cast<float*>(base + o_bi);
+    m.w4 = reinterpret_cast<float*>(base + o_w4);
+    m.b4 = reinterpret_cast<float*>(base + o_b4);
+    m.scale_w = reinterpret_cast<float*>(base + o_sw);
+    m.scale_w_inv = reinterpret_cast<float*>(base + o_swi);
+    m.scale_a_inv = reinterpret_cast<float*>(base + o_sai);
+    m.loss = reinterpret_cast<float*>(base + o_lo);
+    m.amax = reinterpret_cast<float*>(base + o_ax);
+    m.fs[0] = 1.0f;   // s_u
+    m.fs[1] = 7.0f;   // n_u
+    m.fs[2] = 1e-4f;  // s_k
+    m.fs[3] = 10.0f;  // n_k
     e = cudaMemset(ctx->arena, 0, total);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -233,6 +261,128 @@ compton_status compton_kn_ratio(compton_ctx* ctx, const float* ux, const float* 
     if (n == 0) return COMPTON_OK;
     if (!ux || !uy || !uz || !kx || !ky || !kz || !r_out) return COMPTON_EINVAL;
     return compton::launch_kn_ratio(ctx, ux, uy, uz, kx, ky, kz, n, r_out, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Surrogate network
+// ---------------------------------------------------------------------------
+compton_status compton_mlp_set_params(compton_ctx* ctx, const float* theta, int64_t n_params,
+                                      const float* feature_scales)
+{
+    if (!ctx || !theta || n_params != compton::kMlpParams) return COMPTON_EINVAL;
+    if (feature_scales) {
+        for (int i = 0; i < 4; ++i)
+            if (!(feature_scales[i] > 0.0f) || std::isinf(feature_scales[i])) return COMPTON_EINVAL;
+        for (int i = 0; i < 4; ++i) ctx->mlp.fs[i] = feature_scales[i];
+    }
+    COMPTON_CUDA_TRY(ctx, cudaSetDevice(ctx->cfg.device));
+    COMPTON_CUDA_TRY(ctx, cudaMemcpy(ctx->mlp.theta, theta, sizeof(float) * n_params, cudaMemcpyHostToDevice));
+    COMPTON_CUDA_TRY(ctx, cudaMemset(ctx->mlp.adam_m, 0, sizeof(float) * n_params));
+    COMPTON_CUDA_TRY(ctx, cudaMemset(ctx->mlp.adam_v, 0, sizeof(float) * n_params));
+    ctx->adam_step = 0;
+    // default FP8 activation scales until compton_mlp_calibrate: |inputs| <= 4
+    const float sai[4] = {112.0f, 112.0f, 112.0f, 112.0f};
+    COMPTON_CUDA_TRY(ctx, cudaMemcpy(ctx->mlp.scale_a_inv, sai, sizeof(sai), cudaMemcpyHostToDevice));
+    compton_status st = compton::mlp_repack(ctx, nullptr);
+    if (st != COMPTON_OK) return st;
+    COMPTON_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    ctx->mlp_loaded = true;
+    return COMPTON_OK;
+}
+
+compton_status compton_mlp_get_params(compton_ctx* ctx, float* theta, int64_t n_params)
+{
+    if (!ctx || !theta || n_params != compton::kMlpParams) return COMPTON_EINVAL;
+    if (!ctx->mlp_loaded) return COMPTON_ENOMODEL;
+    COMPTON_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    COMPTON_CUDA_TRY(ctx, cudaMemcpy(theta, ctx->mlp.theta, sizeof(float) * n_params, cudaMemcpyDeviceToHost));
+    return COMPTON_OK;
+}
+
+compton_status compton_mlp_calibrate(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
+                                     const float* kx, const float* ky, const float* kz, int64_t n,
+                                     compton_stream_t stream)
+{
+    if (!ctx || n <= 0 || !ux || !uy || !uz || !kx || !ky || !kz) return COMPTON_EINVAL;
+    if (!ctx->mlp_loaded) return COMPTON_ENOMODEL;
+    return compton::launch_mlp_calibrate(ctx, ux, uy, uz, kx, ky, kz, n, stream);
+}
+
+compton_status compton_mlp_infer(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
+                                 const float* kx, const float* ky, const float* kz, int64_t n, compton_mode mode,
+                                 float* r_out, compton_stream_t stream)
+{
+    if (!ctx || n < 0) return COMPTON_EINVAL;
+    if (mode != COMPTON_MODE_MLP_FP32 && mode != COMPTON_MODE_MLP_BF16 && mode != COMPTON_MODE_MLP_FP8)
+        return COMPTON_EINVAL;
+    if (!ctx->mlp_loaded) return COMPTON_ENOMODEL;
+    if (n == 0) return COMPTON_OK;
+    if (!ux || !uy || !uz || !kx || !ky || !kz || !r_out) return COMPTON_EINVAL;
+    return compton::launch_mlp_infer(ctx, ux, uy, uz, kx, ky, kz, n, mode, r_out, stream);
+}
+
+namespace {
+struct MlpBlobHeader {
+    char magic[4];
+    uint32_t version;
+    int64_t n_params;
+    int64_t adam_step;
+    float fs[4];
+    float scale_a_inv[4];
+};
+}  // namespace
+
+compton_status compton_mlp_save(compton_ctx* ctx, void* buf, size_t* len)
+{
+    if (!ctx || !len) return COMPTON_EINVAL;
+    if (!ctx->mlp_loaded) return COMPTON_ENOMODEL;
+    const size_t NP = compton::kMlpParams;
+    const size_t need = sizeof(MlpBlobHeader) + 3 * NP * sizeof(float);
+    if (!buf || *len < need) {
+        *len = need;
+        return buf ? COMPTON_ERANGE : COMPTON_OK;
+    }
+    COMPTON_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    MlpBlobHeader h;
+    std::memcpy(h.magic, "CMLP", 4);
+    h.version = 1;
+    h.n_params = (int64_t)NP;
+    h.adam_step = ctx->adam_step;
+    for (int i = 0; i < 4; ++i) h.fs[i] = ctx->mlp.fs[i];
+    COMPTON_CUDA_TRY(ctx, cudaMemcpy(h.scale_a_inv, ctx->mlp.scale_a_inv, sizeof(h.scale_a_inv),
+                                     cudaMemcpyDeviceToHost));
+    char* p = static_cast<char*>(buf);
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    const float* src[3] = {ctx->mlp.theta, ctx->mlp.adam_m, ctx->mlp.adam_v};
+    for (int i = 0; i < 3; ++i) {
+        COMPTON_CUDA_TRY(ctx, cudaMemcpy(p, src[i], NP * sizeof(float), cudaMemcpyDeviceToHost));
+        p += NP * sizeof(float);
+    }
+    *len = need;
+    return COMPTON_OK;
+}
+
+compton_status compton_mlp_load(compton_ctx* ctx, const void* buf, size_t len)
+{
+    if (!ctx || !buf || len < sizeof(MlpBlobHeader)) return COMPTON_EINVAL;
+    MlpBlobHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    const size_t NP = compton::kMlpParams;
+    if (std::memcmp(h.magic, "CMLP", 4) != 0 || h.version != 1 || h.n_params != (int64_t)NP ||
+        len != sizeof(h) + 3 * NP * sizeof(float))
+        return COMPTON_EINVAL;
+    const char* p = static_cast<const char*>(buf) + sizeof(h);
+    compton_status st = compton_mlp_set_params(ctx, reinterpret_cast<const float*>(p), (int64_t)NP, h.fs);
+    if (st != COMPTON_OK) return st;
+    p += NP * sizeof(float);
+    COMPTON_CUDA_TRY(ctx, cudaMemcpy(ctx->mlp.adam_m, p, NP * sizeof(float), cudaMemcpyHostToDevice));
+    p += NP * sizeof(float);
+    COMPTON_CUDA_TRY(ctx, cudaMemcpy(ctx->mlp.adam_v, p, NP * sizeof(float), cudaMemcpyHostToDevice));
+    COMPTON_CUDA_TRY(ctx, cudaMemcpy(ctx->mlp.scale_a_inv, h.scale_a_inv, sizeof(h.scale_a_inv),
+                                     cudaMemcpyHostToDevice));
+    ctx->adam_step = h.adam_step;
+    return COMPTON_OK;
 }
 
 compton_status compton_kn_sample_angle(compton_ctx* ctx, const float* x, const uint32_t* r, int64_t n,

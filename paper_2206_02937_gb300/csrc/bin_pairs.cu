@@ -310,44 +310,45 @@ struct SortGatherArgs {
     int64_t nb_e;
 };
 
-// (ka, ia, ja) < (kb, ib, jb) lexicographically; j (position) only breaks
-// ties between equal ids, which valid input does not have.
-__device__ __forceinline__ int before(uint32_t kj, uint32_t dj, int j, uint32_t ki, uint32_t di, int i)
+// Sort keys are (key << 32 | id) in 64 bits; the shared-memory position j
+// breaks ties between equal ids (invalid input), so every order is total and
+// every sort yields a permutation.
+__device__ __forceinline__ int before64(uint64_t kj, int j, uint64_t ki, int i)
 {
-    return (kj < ki) | ((kj == ki) & ((dj < di) | ((dj == di) & (j < i))));
+    return (kj < ki) | ((kj == ki) & (j < i));
 }
 
-// Rank the segment [a, a+n) of the shared arrays with one warp; perm[a+rank] = i.
-__device__ __forceinline__ void warp_rank_segment(const uint32_t* key, const uint32_t* sid, int32_t* perm, int a,
-                                                  int n)
+// Rank the elements base .. base + 32E - 1 of the segment [a, a+n) against the
+// whole segment with one warp: each lane holds E of them in registers and one
+// broadcast read of key64[j] serves all E comparisons.  perm[a + rank] = index.
+template <int E>
+__device__ __forceinline__ void warp_rank_chunk(const uint64_t* key64, int32_t* perm, int a, int n, int base)
 {
     const int lane = (int)lane_id();
-    for (int base = 0; base < n; base += 32) {
-        const int i = a + base + lane;
-        const bool have = base + lane < n;
-        const uint32_t ki = have ? key[i] : 0u;
-        const uint32_t di = have ? sid[i] : 0u;
-        int rank = 0;
-        int j = a;
-        for (; j + 4 <= a + n; j += 4) {
-            rank += before(key[j], sid[j], j, ki, di, i);
-            rank += before(key[j + 1], sid[j + 1], j + 1, ki, di, i);
-            rank += before(key[j + 2], sid[j + 2], j + 2, ki, di, i);
-            rank += before(key[j + 3], sid[j + 3], j + 3, ki, di, i);
-        }
-        for (; j < a + n; ++j) rank += before(key[j], sid[j], j, ki, di, i);
-        if (have) perm[a + rank] = i;
+    uint64_t k[E];
+    int idx[E], rank[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        idx[e] = a + base + 32 * e + lane;
+        k[e] = base + 32 * e + lane < n ? key64[idx[e]] : 0ull;
+        rank[e] = 0;
     }
+    for (int j = a; j < a + n; ++j) {
+        const uint64_t kj = key64[j];
+#pragma unroll
+        for (int e = 0; e < E; ++e) rank[e] += before64(kj, j, k[e], idx[e]);
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (base + 32 * e + lane < n) perm[a + rank[e]] = idx[e];
 }
 
 // Sort the segment [a, a+n) (n <= 32 E) with one warp: a bitonic network over
-// 32 E slots held E per lane (slot i = 32 e + lane), keys (key << 32 | id) with
-// the shared-memory index as the final tie-break, so the order is a total one
-// and the network always yields a permutation.  Strides below 32 exchange
-// through shuffles, larger ones swap registers.  perm[a + rank] = index.
+// 32 E slots held E per lane (slot i = 32 e + lane), ordered by (key64, index)
+// so the order is total and the network always yields a permutation.  Strides
+// below 32 exchange through shuffles, larger ones swap registers.
 template <int E>
-__device__ __forceinline__ void warp_bitonic_segment(const uint32_t* key, const uint32_t* sid, int32_t* perm,
-                                                     int a, int n)
+__device__ __forceinline__ void warp_bitonic_segment(const uint64_t* key64, int32_t* perm, int a, int n)
 {
     const int lane = (int)lane_id();
     uint64_t k[E];
@@ -356,11 +357,11 @@ __device__ __forceinline__ void warp_bitonic_segment(const uint32_t* key, const 
     for (int e = 0; e < E; ++e) {
         const int i = e * 32 + lane;
         if (i < n) {
-            k[e] = ((uint64_t)key[a + i] << 32) | sid[a + i];
+            k[e] = key64[a + i];
             p[e] = a + i;
         } else {
             k[e] = ~0ull;
-            p[e] = 0x40000000 + i;  // padding sorts last, still totally ordered
+            p[e] = 0x40000000 + i;  // padding sorts last
         }
     }
     constexpr int N = 32 * E;
@@ -408,16 +409,18 @@ __device__ __forceinline__ void warp_bitonic_segment(const uint32_t* key, const 
     }
 }
 
-__device__ __forceinline__ void sort_segment(const uint32_t* key, const uint32_t* sid, int32_t* perm, int a, int n)
+// Cells of up to 64 particles: bitonic network in registers; larger cells:
+// register-held ranking (n broadcast reads per 32E elements).
+__device__ __forceinline__ void sort_segment(const uint64_t* key64, int32_t* perm, int a, int n)
 {
-    if (n <= 32) warp_bitonic_segment<1>(key, sid, perm, a, n);
-    else if (n <= 64) warp_bitonic_segment<2>(key, sid, perm, a, n);
-    else if (n <= 128) warp_bitonic_segment<4>(key, sid, perm, a, n);
-    else if (n <= 256) warp_bitonic_segment<8>(key, sid, perm, a, n);
-    else warp_rank_segment(key, sid, perm, a, n);
+    if (n <= 32) warp_bitonic_segment<1>(key64, perm, a, n);
+    else if (n <= 64) warp_bitonic_segment<2>(key64, perm, a, n);
+    else if (n <= 128) warp_rank_chunk<4>(key64, perm, a, n, 0);
+    else
+        for (int base = 0; base < n; base += 256) warp_rank_chunk<8>(key64, perm, a, n, base);
 }
 
-__device__ __forceinline__ void gather_out(const SortGatherArgs& g, int s, const uint32_t* src, const uint32_t* sid,
+__device__ __forceinline__ void gather_out(const SortGatherArgs& g, int s, const uint32_t* src, const uint64_t* key64,
                                            const int32_t* perm, int64_t o0, int R)
 {
     const float* __restrict__ iu0 = g.in_u[s][0];
@@ -431,17 +434,17 @@ __device__ __forceinline__ void gather_out(const SortGatherArgs& g, int s, const
         g.out_u[s][1][o0 + p] = iu1[sidx];
         g.out_u[s][2][o0 + p] = iu2[sidx];
         g.out_cell[s][o0 + p] = icell[sidx];
-        g.out_id[s][o0 + p] = sid[i];
+        g.out_id[s][o0 + p] = (uint32_t)key64[i];
     }
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_sort_gather(SortGatherArgs g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint32_t* key = reinterpret_cast<uint32_t*>(smem_raw);
-    uint32_t* src = key + kSortCap;
-    uint32_t* sid = src + kSortCap;
-    int32_t* perm = reinterpret_cast<int32_t*>(sid + kSortCap);
+    uint64_t* key64 = reinterpret_cast<uint64_t*>(smem_raw);
+    uint32_t* src = reinterpret_cast<uint32_t*>(key64 + kSortCap);
+    int32_t* perm = reinterpret_cast<int32_t*>(src + kSortCap);
+    __shared__ int next_cell;
 
     const int s = (int64_t)blockIdx.x < g.nb_e ? 0 : 1;
     const int64_t b = s == 0 ? blockIdx.x : blockIdx.x - g.nb_e;
@@ -454,24 +457,27 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_gather(SortGatherArgs g)
     const int64_t o0 = off[c0];
     const int64_t R = (int64_t)off[c1] - o0;
     if (R <= 0) return;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
 
     if (R <= kSortCap) {
         for (int i = threadIdx.x; i < R; i += blockDim.x) {
             const uint2 r = rec[o0 + i];
-            key[i] = r.x;
+            key64[i] = ((uint64_t)r.x << 32) | in_id[r.y];
             src[i] = r.y;
-            sid[i] = in_id[r.y];
         }
+        if (threadIdx.x == 0) next_cell = 0;
         __syncthreads();
-        for (int64_t c = c0 + warp; c < c1; c += nwarps) {
+        // warps take cells in order as they finish (balances uneven cell sizes)
+        for (;;) {
+            int c = 0;
+            if (lane_id() == 0) c = atomicAdd(&next_cell, 1);
+            c = __shfl_sync(0xffffffffu, c, 0) + (int)c0;
+            if (c >= c1) break;
             const int a = off[c] - (int32_t)o0;
             const int n = off[c + 1] - off[c];
-            if (n > 0) sort_segment(key, sid, perm, a, n);
+            if (n > 0) sort_segment(key64, perm, a, n);
         }
         __syncthreads();
-        gather_out(g, s, src, sid, perm, o0, (int)R);
+        gather_out(g, s, src, key64, perm, o0, (int)R);
         return;
     }
 
@@ -483,19 +489,18 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_gather(SortGatherArgs g)
         if (n <= kSortCap) {
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
                 const uint2 r = rec[o + i];
-                key[i] = r.x;
+                key64[i] = ((uint64_t)r.x << 32) | in_id[r.y];
                 src[i] = r.y;
-                sid[i] = in_id[r.y];
             }
             __syncthreads();
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const uint32_t ki = key[i], di = sid[i];
+                const uint64_t ki = key64[i];
                 int rank = 0;
-                for (int j = 0; j < n; ++j) rank += before(key[j], sid[j], j, ki, di, i);
+                for (int j = 0; j < n; ++j) rank += before64(key64[j], j, ki, i);
                 perm[rank] = i;
             }
             __syncthreads();
-            gather_out(g, s, src, sid, perm, o, (int)n);
+            gather_out(g, s, src, key64, perm, o, (int)n);
             __syncthreads();
         } else {
             // Oversized cell: rank against the records in global memory.

@@ -26,10 +26,42 @@ struct __align__(16) CellInfo {
     float dens;        // pair density n_c = max(N_e, N_g) * w_over_v
 };
 
-enum : unsigned { kErrCellRange = 1u, kErrCapacity = 2u };
+enum : unsigned { kErrCellRange = 1u, kErrCapacity = 2u, kErrTimeout = 4u };
 
 struct DeviceStats {
     unsigned long long pairs_tested, scatters, mlp_fallbacks, error_flags;
+};
+
+// Surrogate network: 6 -> 64 -> 64 -> 64 -> 64 -> 1, parameter vector of
+// 12993 floats (W0 64x6, b0, W1 64x64, b1, W2, b2, W3, b3, W4 1x64, b4).
+constexpr int kMlpParams = 12993;
+__host__ __device__ constexpr int mlp_off_w(int l)
+{
+    return l == 0 ? 0 : l == 1 ? 448 : l == 2 ? 4608 : l == 3 ? 8768 : 12928;
+}
+__host__ __device__ constexpr int mlp_off_b(int l)
+{
+    return l == 0 ? 384 : l == 1 ? 4544 : l == 2 ? 8704 : l == 3 ? 12864 : 12992;
+}
+
+// Device-side network state (all pointers into one context allocation).
+struct MlpDev {
+    float* theta;        // [kMlpParams] FP32 master parameters
+    float* grad;         // [kMlpParams]
+    float* adam_m;       // [kMlpParams]
+    float* adam_v;       // [kMlpParams]
+    void* wbf16;         // 4 x 8 KB BF16 tiles, 128-byte swizzled K-major
+    void* wfp8;          // 4 x 8 KB E4M3 tiles (K padded to 128)
+    float* wt32;         // 4 x 64 x 64 transposed FP32 weights
+    float* bias;         // 4 x 64
+    float* w4;           // 64
+    float* b4;           // 1
+    float* scale_w;      // 4 per-tensor FP8 weight scales
+    float* scale_w_inv;  // 4
+    float* scale_a_inv;  // 4: 1 / FP8 activation scale of each layer input
+    float* loss;         // [2] weighted |error| sum and weight sum of the last step
+    float* amax;         // [4] calibration: max |input| of each hidden layer
+    float fs[4];         // feature scales s_u, n_u, s_k, n_k
 };
 
 }  // namespace compton
@@ -51,6 +83,10 @@ struct compton_ctx {
     int64_t* n_pairs = nullptr;                  // device scalar
     compton::DeviceStats* stats = nullptr;       // device counters
     int64_t max_scan_tiles = 0, max_sort_tiles = 0, max_pair_tiles = 0;
+    // surrogate network
+    compton::MlpDev mlp{};
+    bool mlp_loaded = false;
+    int64_t adam_step = 0;
 };
 
 namespace compton {
@@ -91,5 +127,12 @@ compton_status launch_kn_ratio(compton_ctx* ctx, const float* ux, const float* u
                                cudaStream_t stream);
 compton_status launch_sample_angle(compton_ctx* ctx, const float* x, const uint32_t* r, int64_t n, float* cth,
                                    float* sth, float* ratio, cudaStream_t stream);
+compton_status mlp_repack(compton_ctx* ctx, cudaStream_t stream);
+compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
+                                const float* kx, const float* ky, const float* kz, int64_t n, compton_mode mode,
+                                float* r_out, cudaStream_t stream);
+compton_status launch_mlp_calibrate(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
+                                    const float* kx, const float* ky, const float* kz, int64_t n,
+                                    cudaStream_t stream);
 
 }  // namespace compton

@@ -1,0 +1,473 @@
+// mlp.cu -- the surrogate network that replaces the probability calculation
+// (arXiv 2206.02937, Sec. 2: a network object loaded once and run on any batch
+// of inputs; Sec. 3.2: inputs are the lepton and photon momenta in units of
+// m_e c, fully connected layers, sigmoid output y' in [0, 1]).
+//
+// Network: 6 inputs -> 4 hidden layers of 64 SiLU units -> 1 sigmoid output,
+// predicting r = sigma_KN v / (2 sigma_T), the probability normalised by the
+// cell maximum P_max = 2 sigma_T c dt max w of Sec. 3.2.  Inputs are
+// f = [sgnlog(u/s_u)/n_u, sgnlog(k/s_k)/n_k] with sgnlog(z) = sign(z) ln(1+|z|).
+//
+// Kernels:
+//   k_mlp_pack   FP32 parameter vector -> BF16 weight tiles in the 128-byte
+//                swizzled K-major layout the tensor core reads (layer 0's six
+//                inputs zero-padded to K = 64), FP8 E4M3 tiles (K padded to 128)
+//                with per-tensor scales, transposed FP32 copies for the CUDA
+//                core path, biases and the output layer.
+//   k_mlp_bf16   tcgen05 forward: 128 samples per tile, one row per thread;
+//                per hidden layer four 128x64x16 BF16 MMAs into a 64-column
+//                FP32 TMEM accumulator, then bias + SiLU in registers and the
+//                BF16 activations written back to shared memory as the next
+//                layer's A operand; the 64 -> 1 output layer on the CUDA cores.
+//   k_mlp_fp8    the same with E4M3 operands (kind::f8f6f4, K = 32 per MMA)
+//                and per-tensor scales, FP32 accumulation.
+//   k_mlp_fp32   FP32 forward on the CUDA cores (reference precision).
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "ctx.hpp"
+#include "device_math.cuh"
+#include "tc_ptx.cuh"
+
+namespace compton {
+
+namespace {
+
+constexpr int kMlpThreads = 128;
+constexpr int kTileM = 128;
+// shared-memory layout of the tensor-core kernels (base aligned to 1024 B)
+constexpr uint32_t kOffW = 0;                           // 4 weight tiles
+constexpr uint32_t kWTileBytes = 8192;                  // 64 rows x 128 B
+constexpr uint32_t kOffA0 = kOffW + 4 * kWTileBytes;    // layer-0 A tile (128 x 128 B)
+constexpr uint32_t kOffA = kOffA0 + 16384;              // hidden A tile
+constexpr uint32_t kOffBias = kOffA + 16384;            // 4 x 64 floats
+constexpr uint32_t kOffW4 = kOffBias + 1024;            // 64 floats
+constexpr uint32_t kOffScale = kOffW4 + 256;            // 8 floats
+constexpr uint32_t kOffBar = kOffScale + 32;            // mbarrier
+constexpr uint32_t kOffSlot = kOffBar + 8;              // TMEM address
+constexpr uint32_t kSmemTc = kOffSlot + 8 + 1024;       // + alignment slack
+
+constexpr uint64_t kWaitNs = 2000000000ull;             // 2 s bound on every wait
+
+__device__ __forceinline__ float sgnlog(float z) { return copysignf(log1pf(fabsf(z)), z); }
+
+__device__ __forceinline__ void features(const MlpDev& m, float ux, float uy, float uz, float kx, float ky, float kz,
+                                         float* f)
+{
+    const float iu = __fdividef(1.0f, m.fs[0]), nu = __fdividef(1.0f, m.fs[1]);
+    const float ik = __fdividef(1.0f, m.fs[2]), nk = __fdividef(1.0f, m.fs[3]);
+    f[0] = sgnlog(ux * iu) * nu;
+    f[1] = sgnlog(uy * iu) * nu;
+    f[2] = sgnlog(uz * iu) * nu;
+    f[3] = sgnlog(kx * ik) * nk;
+    f[4] = sgnlog(ky * ik) * nk;
+    f[5] = sgnlog(kz * ik) * nk;
+}
+
+__device__ __forceinline__ float silu_fast(float z) { return 0.5f * z * (1.0f + tc::tanh_approx(0.5f * z)); }
+__device__ __forceinline__ float silu_exact(float z) { return z / (1.0f + expf(-z)); }
+__device__ __forceinline__ float sigmoid_exact(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d)
+{
+    const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+__device__ __forceinline__ float e4m3_round(float x)
+{
+    const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+    const __half_raw h = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
+    return __half2float(__half(h));
+}
+
+// ---------------------------------------------------------------------------
+// Packing.  theta layout (float, 12993): W0 (64x6), b0, W1 (64x64), b1, W2, b2,
+// W3, b3, W4 (1x64), b4; W stored (out, in) row-major.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float theta_w(const float* th, int l, int n, int k)
+{
+    if (l == 0) return k < 6 ? th[n * 6 + k] : 0.0f;
+    return th[mlp_off_w(l) + n * 64 + k];
+}
+
+__global__ void k_mlp_pack(MlpDev m)
+{
+    const float* th = m.theta;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // BF16 tiles: 4 x 64 x 64
+    if (i < 4 * 64 * 64) {
+        const int l = i / 4096, n = (i / 64) % 64, k = i % 64;
+        uint8_t* base = reinterpret_cast<uint8_t*>(m.wbf16) + l * kWTileBytes;
+        const __nv_bfloat16 v = __float2bfloat16_rn(theta_w(th, l, n, k));
+        *reinterpret_cast<__nv_bfloat16*>(base + tc::sw128_offset(n, k >> 3) + (k & 7) * 2) = v;
+        // transposed FP32 copy for the CUDA-core path: wt[l][k][n]
+        m.wt32[l * 4096 + k * 64 + n] = theta_w(th, l, n, k);
+    }
+    // FP8 tiles: 4 x 64 rows x 128 B (K = 64 real + 64 zero)
+    if (i < 4 * 64 * 128) {
+        const int l = i / 8192, n = (i / 128) % 64, k = i % 128;
+        uint8_t* base = reinterpret_cast<uint8_t*>(m.wfp8) + l * kWTileBytes;
+        const float w = k < 64 ? theta_w(th, l, n, k) * m.scale_w_inv[l] : 0.0f;
+        base[tc::sw128_offset(n, k >> 4) + (k & 15)] = __nv_cvt_float_to_fp8(w, __NV_SATFINITE, __NV_E4M3);
+    }
+    if (i < 4 * 64) {
+        const int l = i / 64, n = i % 64;
+        m.bias[i] = th[mlp_off_b(l) + n];
+    }
+    if (i < 64) m.w4[i] = th[mlp_off_w(4) + i];
+    if (i == 0) m.b4[0] = th[mlp_off_b(4)];
+}
+
+// Per-tensor amax of each layer's weights (for the FP8 scales): one block per layer.
+__global__ void k_mlp_weight_amax(MlpDev m)
+{
+    __shared__ float red[32];
+    const int l = blockIdx.x;
+    const int n_el = l == 0 ? 64 * 6 : 64 * 64;
+    const float* w = m.theta + mlp_off_w(l);
+    float a = 0.0f;
+    for (int i = threadIdx.x; i < n_el; i += blockDim.x) a = fmaxf(a, fabsf(w[i]));
+    for (int d = 16; d > 0; d >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, d));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = fmaxf(t, red[i]);
+        const float s = t > 0.0f ? t / 448.0f : 1.0f;  // 448 = largest finite E4M3
+        m.scale_w[l] = s;
+        m.scale_w_inv[l] = 1.0f / s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core forward (BF16 or FP8 operands).  kFp8 selects the operand type.
+// ---------------------------------------------------------------------------
+struct MlpArgs {
+    MlpDev m;
+    const float* u[3];
+    const float* k[3];
+    int64_t n;
+    float* r_out;
+    DeviceStats* stats;
+};
+
+template <bool kFp8>
+__global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* Wt = sm + kOffW;
+    uint8_t* A0 = sm + kOffA0;
+    uint8_t* Ah = sm + kOffA;
+    float* bias = reinterpret_cast<float*>(sm + kOffBias);
+    float* w4 = reinterpret_cast<float*>(sm + kOffW4);
+    float* scale = reinterpret_cast<float*>(sm + kOffScale);  // [0..3] w scales, [4..7] 1/activation scales
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kOffBar);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(sm + kOffSlot);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const MlpDev& m = a.m;
+    const uint4* wsrc = reinterpret_cast<const uint4*>(kFp8 ? m.wfp8 : m.wbf16);
+    for (int i = tid; i < (int)(4 * kWTileBytes / 16); i += kMlpThreads) reinterpret_cast<uint4*>(Wt)[i] = wsrc[i];
+    for (int i = tid; i < 2 * 16384 / 16; i += kMlpThreads) reinterpret_cast<uint4*>(A0)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < 256; i += kMlpThreads) bias[i] = m.bias[i];
+    if (tid < 64) w4[tid] = m.w4[tid];
+    if (tid < 4) {
+        scale[tid] = m.scale_w[tid];
+        scale[4 + tid] = m.scale_a_inv[tid];
+    }
+    const float b4 = m.b4[0];
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_barrier_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(slot, 64);
+        tc::tmem_relinquish();
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *slot;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    constexpr uint32_t idesc = kFp8 ? tc::make_idesc(0, 0, 128, 64) : tc::make_idesc(1, 1, 128, 64);
+    const uint32_t sW = tc::smem_u32(Wt), sA0 = tc::smem_u32(A0), sA = tc::smem_u32(Ah);
+    uint32_t phase = 0;
+    bool failed = false;
+    const int64_t n_tiles = (a.n + kTileM - 1) / kTileM;
+
+    for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+        const int64_t row = tile * kTileM + tid;
+        float f[6] = {0, 0, 0, 0, 0, 0};
+        if (row < a.n) features(m, a.u[0][row], a.u[1][row], a.u[2][row], a.k[0][row], a.k[1][row], a.k[2][row], f);
+        if (kFp8) {
+            const float s = scale[4];
+            *reinterpret_cast<uint4*>(A0 + tc::sw128_offset(tid, 0)) =
+                make_uint4(pack_e4m3x4(f[0] * s, f[1] * s, f[2] * s, f[3] * s), pack_e4m3x4(f[4] * s, f[5] * s, 0, 0),
+                           0u, 0u);
+        } else {
+            *reinterpret_cast<uint4*>(A0 + tc::sw128_offset(tid, 0)) =
+                make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]), 0u);
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+
+        float acc_out = 0.0f;
+        for (int l = 0; l < 4; ++l) {
+            if (tid == 0) {
+                const uint64_t ad = tc::sw128_kmajor_desc(l == 0 ? sA0 : sA);
+                const uint64_t bd = tc::sw128_kmajor_desc(sW + l * kWTileBytes);
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {
+                    // 32-byte K step inside the 128-byte swizzle atom
+                    if (kFp8) tc::mma_f8(tmem, ad + 2 * ks, bd + 2 * ks, idesc, ks > 0);
+                    else tc::mma_bf16(tmem, ad + 2 * ks, bd + 2 * ks, idesc, ks > 0);
+                }
+                tc::mma_commit(bar);
+            }
+            const bool ok = tc::mbar_wait(bar, phase, kWaitNs);
+            phase ^= 1u;
+            tc::fence_after_sync();
+            if (ok) {
+                const float deq = kFp8 ? scale[l] / scale[4 + l] : 1.0f;  // w scale x activation scale
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float v[32];
+                    tc::tmem_ld32(trow + 32 * h, v);
+                    if (l < 3) {
+                        const float snext = kFp8 ? scale[4 + l + 1] : 1.0f;
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int c = 0; c < 32; c += 2) {
+                            const float s0 = silu_fast(fmaf(v[c], deq, bias[l * 64 + 32 * h + c]));
+                            const float s1 = silu_fast(fmaf(v[c + 1], deq, bias[l * 64 + 32 * h + c + 1]));
+                            pk[c / 2] = pack_bf16x2(s0, s1);
+                            if (kFp8) {
+                                v[c] = s0 * snext;
+                                v[c + 1] = s1 * snext;
+                            }
+                        }
+                        if (kFp8) {
+                            // 32 values -> 32 bytes = chunks 2h, 2h+1 of the 64-byte real half of the row
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                const uint4 val = make_uint4(
+                                    pack_e4m3x4(v[16 * q + 0], v[16 * q + 1], v[16 * q + 2], v[16 * q + 3]),
+                                    pack_e4m3x4(v[16 * q + 4], v[16 * q + 5], v[16 * q + 6], v[16 * q + 7]),
+                                    pack_e4m3x4(v[16 * q + 8], v[16 * q + 9], v[16 * q + 10], v[16 * q + 11]),
+                                    pack_e4m3x4(v[16 * q + 12], v[16 * q + 13], v[16 * q + 14], v[16 * q + 15]));
+                                *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(tid, 2 * h + q)) = val;
+                            }
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(tid, 4 * h + q)) =
+                                    make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            const float s = silu_fast(fmaf(v[c], deq, bias[3 * 64 + 32 * h + c]));
+                            acc_out = fmaf(s, w4[32 * h + c], acc_out);
+                        }
+                    }
+                }
+            }
+            if (l < 3) tc::fence_proxy_async_smem();
+            tc::fence_before_sync();
+            const int bad = __syncthreads_or(ok ? 0 : 1);
+            tc::fence_after_sync();
+            if (bad) {
+                failed = true;
+                break;
+            }
+        }
+        if (!failed && row < a.n) a.r_out[row] = __fdividef(1.0f, 1.0f + __expf(-(acc_out + b4)));
+    }
+    if (failed && tid == 0) atomicOr(&a.stats->error_flags, (unsigned long long)kErrTimeout);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 64);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 forward on the CUDA cores: one sample per thread, activations in shared
+// memory laid out [unit][thread] (conflict-free), transposed weights read as
+// broadcasts, 64 accumulators in registers.
+// ---------------------------------------------------------------------------
+constexpr int kF32Threads = 128;
+
+template <bool kCalib>
+__global__ void __launch_bounds__(kF32Threads) k_mlp_fp32(MlpArgs a)
+{
+    extern __shared__ float smf[];
+    float* wt = smf;                    // 4 x 64 x 64 (layer 0 uses the first 6 rows)
+    float* hs = wt + 4 * 4096;          // 64 x kF32Threads
+    float* bias = hs + 64 * kF32Threads;
+    float* w4 = bias + 256;
+    const int tid = threadIdx.x;
+    const MlpDev& m = a.m;
+    for (int i = tid; i < 4 * 4096 / 4; i += kF32Threads)
+        reinterpret_cast<float4*>(wt)[i] = reinterpret_cast<const float4*>(m.wt32)[i];
+    for (int i = tid; i < 256; i += kF32Threads) bias[i] = m.bias[i];
+    if (tid < 64) w4[tid] = m.w4[tid];
+    const float b4 = m.b4[0];
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * kF32Threads;
+    for (int64_t row = (int64_t)blockIdx.x * kF32Threads + tid; row < a.n; row += stride) {
+        float f[6];
+        features(m, a.u[0][row], a.u[1][row], a.u[2][row], a.k[0][row], a.k[1][row], a.k[2][row], f);
+        float amax[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            hs[i * kF32Threads + tid] = f[i];
+            if (kCalib) amax[0] = fmaxf(amax[0], fabsf(f[i]));
+        }
+        float out = b4;
+        for (int l = 0; l < 4; ++l) {
+            float acc[64];
+#pragma unroll
+            for (int j = 0; j < 64; ++j) acc[j] = bias[l * 64 + j];
+            const int n_in = l == 0 ? 6 : 64;
+            for (int i = 0; i < n_in; ++i) {
+                const float hi = hs[i * kF32Threads + tid];
+                const float4* wr = reinterpret_cast<const float4*>(wt + l * 4096 + i * 64);
+#pragma unroll
+                for (int j4 = 0; j4 < 16; ++j4) {
+                    const float4 w = wr[j4];
+                    acc[4 * j4 + 0] = fmaf(w.x, hi, acc[4 * j4 + 0]);
+                    acc[4 * j4 + 1] = fmaf(w.y, hi, acc[4 * j4 + 1]);
+                    acc[4 * j4 + 2] = fmaf(w.z, hi, acc[4 * j4 + 2]);
+                    acc[4 * j4 + 3] = fmaf(w.w, hi, acc[4 * j4 + 3]);
+                }
+            }
+            if (l < 3) {
+#pragma unroll
+                for (int j = 0; j < 64; ++j) {
+                    const float s = silu_exact(acc[j]);
+                    hs[j * kF32Threads + tid] = s;
+                    if (kCalib) amax[l + 1] = fmaxf(amax[l + 1], fabsf(s));
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 64; ++j) out = fmaf(silu_exact(acc[j]), w4[j], out);
+            }
+        }
+        if (kCalib) {
+#pragma unroll
+            for (int l = 0; l < 4; ++l) atomicMax(reinterpret_cast<int*>(m.amax) + l, __float_as_int(amax[l]));
+        } else {
+            a.r_out[row] = sigmoid_exact(out);
+        }
+    }
+}
+
+// FP8 activation scales from the calibration maxima: inputs of layer l are
+// stored as E4M3(h * 448 / amax_l).
+__global__ void k_mlp_set_act_scales(MlpDev m)
+{
+    const int l = threadIdx.x;
+    if (l < 4) {
+        const float a = m.amax[l];
+        m.scale_a_inv[l] = a > 0.0f ? 448.0f / a : 1.0f;
+    }
+}
+
+int grid_persistent(const void* kernel, int threads, int smem, int64_t work_items, int per_item)
+{
+    int dev = 0, n_sm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t need = (work_items + per_item - 1) / per_item;
+    const int64_t full = (int64_t)per_sm * n_sm;
+    return (int)(need < 1 ? 1 : (need < full ? need : full));
+}
+
+}  // namespace
+
+compton_status mlp_repack(compton_ctx* ctx, cudaStream_t stream)
+{
+    MlpDev m = ctx->mlp;
+    k_mlp_weight_amax<<<4, 256, 0, stream>>>(m);
+    COMPTON_LAUNCH_CHECK(ctx, "k_mlp_weight_amax");
+    k_mlp_pack<<<(4 * 64 * 128 + 255) / 256, 256, 0, stream>>>(m);
+    COMPTON_LAUNCH_CHECK(ctx, "k_mlp_pack");
+    return COMPTON_OK;
+}
+
+compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
+                                const float* kx, const float* ky, const float* kz, int64_t n, compton_mode mode,
+                                float* r_out, cudaStream_t stream)
+{
+    MlpArgs a;
+    a.m = ctx->mlp;
+    a.u[0] = ux;
+    a.u[1] = uy;
+    a.u[2] = uz;
+    a.k[0] = kx;
+    a.k[1] = ky;
+    a.k[2] = kz;
+    a.n = n;
+    a.r_out = r_out;
+    a.stats = ctx->stats;
+    if (mode == COMPTON_MODE_MLP_FP32) {
+        const int smem = (4 * 4096 + 64 * kF32Threads + 256 + 64) * 4;
+        COMPTON_CUDA_TRY(ctx, cudaFuncSetAttribute(k_mlp_fp32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   smem));
+        const int grid = grid_persistent((const void*)k_mlp_fp32<false>, kF32Threads, smem, n, kF32Threads);
+        k_mlp_fp32<false><<<grid, kF32Threads, smem, stream>>>(a);
+        COMPTON_LAUNCH_CHECK(ctx, "k_mlp_fp32");
+        return COMPTON_OK;
+    }
+    const bool fp8 = mode == COMPTON_MODE_MLP_FP8;
+    const void* kern = fp8 ? (const void*)k_mlp_tc<true> : (const void*)k_mlp_tc<false>;
+    COMPTON_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTc));
+    const int grid = grid_persistent(kern, kMlpThreads, (int)kSmemTc, n, kTileM);
+    if (fp8) k_mlp_tc<true><<<grid, kMlpThreads, kSmemTc, stream>>>(a);
+    else k_mlp_tc<false><<<grid, kMlpThreads, kSmemTc, stream>>>(a);
+    COMPTON_LAUNCH_CHECK(ctx, fp8 ? "k_mlp_tc<fp8>" : "k_mlp_tc<bf16>");
+    return COMPTON_OK;
+}
+
+compton_status launch_mlp_calibrate(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
+                                    const float* kx, const float* ky, const float* kz, int64_t n,
+                                    cudaStream_t stream)
+{
+    MlpArgs a;
+    a.m = ctx->mlp;
+    a.u[0] = ux;
+    a.u[1] = uy;
+    a.u[2] = uz;
+    a.k[0] = kx;
+    a.k[1] = ky;
+    a.k[2] = kz;
+    a.n = n;
+    a.r_out = nullptr;
+    a.stats = ctx->stats;
+    const int smem = (4 * 4096 + 64 * kF32Threads + 256 + 64) * 4;
+    COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->mlp.amax, 0, 4 * sizeof(float), stream));
+    COMPTON_CUDA_TRY(ctx, cudaFuncSetAttribute(k_mlp_fp32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int grid = grid_persistent((const void*)k_mlp_fp32<true>, kF32Threads, smem, n, kF32Threads);
+    k_mlp_fp32<true><<<grid, kF32Threads, smem, stream>>>(a);
+    COMPTON_LAUNCH_CHECK(ctx, "k_mlp_fp32<calib>");
+    k_mlp_set_act_scales<<<1, 32, 0, stream>>>(ctx->mlp);
+    COMPTON_LAUNCH_CHECK(ctx, "k_mlp_set_act_scales");
+    return COMPTON_OK;
+}
+
+}  // namespace compton

@@ -40,6 +40,7 @@ struct ScatterArgs {
     float dt;
     uint64_t seed, step;
     float gamma64;
+    float collide64_sq;  // (gamma eps)^2 above which the collision runs in FP64
     float* prob_out;
     uint8_t* flag_out;
     DeviceStats* stats;
@@ -66,7 +67,10 @@ __device__ __forceinline__ void resolve(const ScatterArgs& a, const QEntry& e)
     float ux = a.u[0][e.ie], uy = a.u[1][e.ie], uz = a.u[2][e.ie];
     float kx = a.k[0][e.ig], ky = a.k[1][e.ig], kz = a.k[2][e.ig];
     const Angle ang = kn_sample_angle(e.x, e.r1 >> 8, e.F2);
-    collide_f64(ux, uy, uz, kx, ky, kz, e.x, ang, u24_closed0(e.r2));
+    // FP64 where FP32 cancellation would exceed the tolerance (gamma eps large)
+    const float ge2 = fmaf(ux, ux, fmaf(uy, uy, fmaf(uz, uz, 1.0f))) * fmaf(kx, kx, fmaf(ky, ky, kz * kz));
+    if (ge2 > a.collide64_sq) collide_f64(ux, uy, uz, kx, ky, kz, e.x, ang, u24_closed0(e.r2));
+    else collide_f32(ux, uy, uz, kx, ky, kz, e.x, ang, u24_closed0(e.r2));
     a.u[0][e.ie] = ux;
     a.u[1][e.ie] = uy;
     a.u[2][e.ie] = uz;
@@ -163,7 +167,7 @@ __global__ void __launch_bounds__(kScatterThreads, 3) k_scatter(ScatterArgs a)
             if (inv.gamma > a.gamma64) invariants_f64(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r], &x, &v);
             const float F2 = kn_F2(x);
             const float sig = 0.375f * F2;
-            const float P = inv.eps > 0.0f ? -expm1f(-(dens[r] * a.dt * sig * v)) : 0.0f;
+            const float P = inv.eps > 0.0f ? one_minus_exp_neg(dens[r] * a.dt * sig * v) : 0.0f;
             const Philox4 rnd = draw(a.seed, a.step, kStreamScatter, (uint32_t)p);
             const bool hit = u24_closed0(rnd.r0) < P;
             if (a.prob_out) a.prob_out[p] = P;
@@ -274,6 +278,7 @@ compton_status launch_scatter_binned(compton_ctx* ctx, compton_species* e, compt
     a.seed = ctx->cfg.seed;
     a.step = step;
     a.gamma64 = ctx->cfg.gamma_fp64_threshold;
+    a.collide64_sq = ctx->cfg.collide_fp64_threshold * ctx->cfg.collide_fp64_threshold;
     a.prob_out = prob_out;
     a.flag_out = flag_out;
     a.stats = ctx->stats;
@@ -303,6 +308,7 @@ compton_status launch_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, floa
     a.seed = seed;
     a.step = step;
     a.gamma64 = ctx->cfg.gamma_fp64_threshold;
+    a.collide64_sq = ctx->cfg.collide_fp64_threshold * ctx->cfg.collide_fp64_threshold;
     a.prob_out = prob_out;
     a.flag_out = flag_out;
     a.stats = ctx->stats;
