@@ -74,6 +74,8 @@ typedef struct compton_config {
                                     relative to gamma + eps stays below 2e-6 up to 8);
                                     0 = always FP64                                            */
     uint64_t mem_budget_bytes;   /* cap on library-owned device memory (0 = no cap)            */
+    int64_t max_train_batch;     /* largest minibatch of compton_mlp_train_step (sizes its
+                                    scratch: 2060 bytes per sample); 0 = no training           */
 } compton_config;
 
 /* One species in structure-of-arrays form (all device pointers, length n).
@@ -236,6 +238,24 @@ compton_status compton_mlp_infer(struct compton_ctx* ctx, const float* ux_dev, c
                                  const float* uz_dev, const float* kx_dev, const float* ky_dev,
                                  const float* kz_dev, int64_t n, compton_mode mode, float* r_out_dev,
                                  compton_stream_t stream);
+
+/* One Adam step of the network on a minibatch (Sec. 3.2: mean absolute error
+ * loss, Adam optimizer): inputs u, k (device SoA, length n), targets y_dev
+ * (the analytic r, e.g. from compton_kn_ratio), per-sample weights w_dev
+ * (nullable = 1; the data balancing of Sec. 3.2), learning rate lr.
+ * Loss L = sum w |y' - y| / sum w with the subgradient 0 at y' = y; Adam with
+ * beta1 = 0.9, beta2 = 0.999, eps = 1e-7 on the FP32 master parameters; the
+ * BF16 / FP8 / FP32 inference images are rebuilt after the step.
+ * loss_out_host (nullable): if given, the call synchronises and stores the
+ * loss of this minibatch (before the update).  ERANGE if n > max_train_batch. */
+compton_status compton_mlp_train_step(struct compton_ctx* ctx, const float* ux_dev, const float* uy_dev,
+                                      const float* uz_dev, const float* kx_dev, const float* ky_dev,
+                                      const float* kz_dev, const float* y_dev, const float* w_dev, int64_t n,
+                                      float lr, float* loss_out_host, compton_stream_t stream);
+
+/* The gradient dL/dtheta of the last compton_mlp_train_step (the loss
+ * normalised by sum w), same layout as the parameters.  Synchronous. */
+compton_status compton_mlp_get_grad(struct compton_ctx* ctx, float* grad_host, int64_t n_params);
 
 /* Serialise the network (format "CMLP" version 1: header with the Adam step,
  * feature and activation scales, then parameters and both Adam moments) to

@@ -28,7 +28,7 @@ MODE_PLAIN, MODE_MLP_FP32, MODE_MLP_BF16, MODE_MLP_FP8 = range(4)
 class compton_config(ctypes.Structure):
     _fields_ = [("n_cells", c_i64), ("max_particles", c_i64), ("w_over_v", c_f64), ("dt", c_f64),
                 ("seed", c_u64), ("device", c_i32), ("gamma_fp64_threshold", c_f32),
-                ("collide_fp64_threshold", c_f32), ("mem_budget_bytes", c_u64)]
+                ("collide_fp64_threshold", c_f32), ("mem_budget_bytes", c_u64), ("max_train_batch", c_i64)]
 
 
 class compton_species(ctypes.Structure):
@@ -139,9 +139,9 @@ class Species:
 
 def compton_init(n_cells: int, max_particles: int, w_over_v: float, dt: float, seed: int, device: int = 0,
                  gamma_fp64_threshold: float = 1.0e3, mem_budget_bytes: int = 0,
-                 collide_fp64_threshold: float = 8.0) -> int:
+                 collide_fp64_threshold: float = 8.0, max_train_batch: int = 0) -> int:
     cfg = compton_config(n_cells, max_particles, w_over_v, dt, seed, device, gamma_fp64_threshold,
-                         collide_fp64_threshold, mem_budget_bytes)
+                         collide_fp64_threshold, mem_budget_bytes, max_train_batch)
     out = c_p()
     _check(lib().compton_init(ctypes.byref(cfg), ctypes.byref(out)), "compton_init")
     return out.value
@@ -211,6 +211,8 @@ SIGNATURES.update({
     "compton_mlp_infer": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_i64, c_i32, c_p, c_p]),
     "compton_mlp_save": (c_i32, [c_p, c_p, ctypes.POINTER(ctypes.c_size_t)]),
     "compton_mlp_load": (c_i32, [c_p, c_p, ctypes.c_size_t]),
+    "compton_mlp_train_step": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_i64, c_f32,
+                                       ctypes.POINTER(c_f32), c_p]),
 })
 
 N_MLP_PARAMS = 12993
@@ -260,3 +262,24 @@ def compton_mlp_save(ctx: int) -> bytes:
 def compton_mlp_load(ctx: int, blob: bytes) -> None:
     buf = ctypes.create_string_buffer(blob, len(blob))
     _check(lib().compton_mlp_load(c_p(ctx), ctypes.cast(buf, c_p), len(blob)), "compton_mlp_load", ctx)
+
+
+def compton_mlp_train_step(ctx: int, u, k, y, w, lr: float = 1e-3, want_loss: bool = True, stream=None):
+    """One Adam step on a minibatch; returns the minibatch loss (synchronising) or None."""
+    n = int(u.shape[1])
+    loss = c_f32(0.0)
+    _check(lib().compton_mlp_train_step(c_p(ctx), _ptr(u[0]), _ptr(u[1]), _ptr(u[2]), _ptr(k[0]), _ptr(k[1]),
+                                        _ptr(k[2]), _ptr(y), _ptr(w), n, float(lr),
+                                        ctypes.byref(loss) if want_loss else None, _stream_ptr(stream)),
+           "compton_mlp_train_step", ctx)
+    return float(loss.value) if want_loss else None
+
+
+SIGNATURES["compton_mlp_get_grad"] = (c_i32, [c_p, c_p, c_i64])
+
+
+def compton_mlp_get_grad(ctx: int):
+    import numpy as np
+    g = np.zeros(N_MLP_PARAMS, dtype=np.float32)
+    _check(lib().compton_mlp_get_grad(c_p(ctx), c_p(g.ctypes.data), N_MLP_PARAMS), "compton_mlp_get_grad", ctx)
+    return g

@@ -115,6 +115,11 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     size_t o_bi = cv.take<float>(256), o_w4 = cv.take<float>(64), o_b4 = cv.take<float>(1);
     size_t o_sw = cv.take<float>(4), o_swi = cv.take<float>(4), o_sai = cv.take<float>(4), o_lo = cv.take<float>(2),
            o_ax = cv.take<float>(4);
+    if (cfg->max_train_batch < 0 || cfg->max_train_batch > (int64_t)1 << 31) {
+        delete ctx;
+        return COMPTON_EINVAL;
+    }
+    size_t o_tr = cv.take<uint8_t>(cfg->max_train_batch > 0 ? compton::train_scratch_bytes(cfg->max_train_batch) : 1);
     const size_t total = align_up(cv.used, 256);
     if (cfg->mem_budget_bytes && total > cfg->mem_budget_bytes) {
         delete ctx;
@@ -155,6 +160,7 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     m.scale_a_inv = reinterpret_cast<float*>(base + o_sai);
     m.loss = reinterpret_cast<float*>(base + o_lo);
     m.amax = reinterpret_cast<float*>(base + o_ax);
+    ctx->train_scratch = base + o_tr;
     m.fs[0] = 1.0f;   // s_u
     m.fs[1] = 7.0f;   // n_u
     m.fs[2] = 1e-4f;  // s_k
@@ -319,6 +325,37 @@ compton_status compton_mlp_infer(compton_ctx* ctx, const float* ux, const float*
     if (n == 0) return COMPTON_OK;
     if (!ux || !uy || !uz || !kx || !ky || !kz || !r_out) return COMPTON_EINVAL;
     return compton::launch_mlp_infer(ctx, ux, uy, uz, kx, ky, kz, n, mode, r_out, stream);
+}
+
+compton_status compton_mlp_train_step(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
+                                      const float* kx, const float* ky, const float* kz, const float* y,
+                                      const float* w, int64_t n, float lr, float* loss_out,
+                                      compton_stream_t stream)
+{
+    if (!ctx || n <= 0 || !ux || !uy || !uz || !kx || !ky || !kz || !y) return COMPTON_EINVAL;
+    if (!(lr >= 0.0f) || std::isinf(lr)) return COMPTON_EINVAL;
+    if (!ctx->mlp_loaded) return COMPTON_ENOMODEL;
+    if (n > ctx->cfg.max_train_batch) return COMPTON_ERANGE;
+    compton_status st = compton::launch_mlp_train_step(ctx, ux, uy, uz, kx, ky, kz, y, w, n, lr, stream);
+    if (st != COMPTON_OK || !loss_out) return st;
+    float l[2];
+    COMPTON_CUDA_TRY(ctx, cudaMemcpyAsync(l, ctx->mlp.loss, sizeof(l), cudaMemcpyDeviceToHost, stream));
+    COMPTON_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+    *loss_out = l[1] > 0.0f ? l[0] / l[1] : 0.0f;
+    return COMPTON_OK;
+}
+
+compton_status compton_mlp_get_grad(compton_ctx* ctx, float* grad, int64_t n_params)
+{
+    if (!ctx || !grad || n_params != compton::kMlpParams) return COMPTON_EINVAL;
+    if (!ctx->mlp_loaded) return COMPTON_ENOMODEL;
+    COMPTON_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    float l[2];
+    COMPTON_CUDA_TRY(ctx, cudaMemcpy(l, ctx->mlp.loss, sizeof(l), cudaMemcpyDeviceToHost));
+    COMPTON_CUDA_TRY(ctx, cudaMemcpy(grad, ctx->mlp.grad, sizeof(float) * n_params, cudaMemcpyDeviceToHost));
+    const float inv = l[1] > 0.0f ? 1.0f / l[1] : 0.0f;
+    for (int64_t i = 0; i < n_params; ++i) grad[i] *= inv;
+    return COMPTON_OK;
 }
 
 namespace {

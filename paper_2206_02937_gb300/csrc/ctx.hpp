@@ -87,6 +87,7 @@ struct compton_ctx {
     compton::MlpDev mlp{};
     bool mlp_loaded = false;
     int64_t adam_step = 0;
+    void* train_scratch = nullptr;  // inside the arena, sized by cfg.max_train_batch
 };
 
 namespace compton {
@@ -131,6 +132,10 @@ compton_status mlp_repack(compton_ctx* ctx, cudaStream_t stream);
 compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                 const float* kx, const float* ky, const float* kz, int64_t n, compton_mode mode,
                                 float* r_out, cudaStream_t stream);
+size_t train_scratch_bytes(int64_t max_batch);
+compton_status launch_mlp_train_step(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
+                                     const float* kx, const float* ky, const float* kz, const float* y,
+                                     const float* w, int64_t n, float lr, cudaStream_t stream);
 compton_status launch_mlp_calibrate(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                     const float* kx, const float* ky, const float* kz, int64_t n,
                                     cudaStream_t stream);

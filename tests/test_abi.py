@@ -35,7 +35,7 @@ def test_strerror_without_gpu():
 
 def test_init_rejects_bad_config_without_touching_the_gpu():
     b.build()
-    cfg = cg.compton_config(0, 10, 1.0, 0.05, 1, 0, 1e3, 8.0, 0)  # n_cells = 0
+    cfg = cg.compton_config(0, 10, 1.0, 0.05, 1, 0, 1e3, 8.0, 0, 0)  # n_cells = 0
     out = ctypes.c_void_p()
     assert cg.lib().compton_init(ctypes.byref(cfg), ctypes.byref(out)) == cg.COMPTON_EINVAL
     assert cg.lib().compton_init(None, ctypes.byref(out)) == cg.COMPTON_EINVAL
