@@ -70,6 +70,8 @@ def lib():
         L.or_onb.restype = None
         L.or_scatter_event.argtypes = [P, P, d, d, u64, u64, u32, P, P, P, P, P]
         L.or_scatter_event.restype = None
+        L.or_collide.argtypes = [P, P, u64, u64, u32, P, P]
+        L.or_collide.restype = None
         L.or_pair_key.argtypes = [u64, u64, u32, u32]
         L.or_pair_key.restype = u32
         L.or_sort_species.argtypes = [i64, P, P, i64, u64, u64, u32, P, P]
@@ -173,6 +175,16 @@ def scatter_event(u, k, n_dens, dt, seed, step, ctr_id):
                            int(ctr_id), _p(uo), _p(ko), ctypes.byref(P), ctypes.byref(f),
                            ctypes.byref(x))
     return uo, ko, P.value, f.value, x.value
+
+
+def collide(u, k, seed, step, ctr_id):
+    """The collision of one pair with its own draws (always applied)."""
+    uu = np.ascontiguousarray(u, dtype=np.float64)
+    kk = np.ascontiguousarray(k, dtype=np.float64)
+    uo = np.zeros(3)
+    ko = np.zeros(3)
+    lib().or_collide(_p(uu), _p(kk), int(seed), int(step), int(ctr_id), _p(uo), _p(ko))
+    return uo, ko
 
 
 def pair_key(seed, step, stream, pid) -> int:

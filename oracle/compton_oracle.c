@@ -264,14 +264,52 @@ void or_onb(const double n[3], double b1[3], double b2[3])
     b2[2] = -n[1];
 }
 
+/* The collision of one pair with its own draws (Sec. 3.1, "the kinetic
+ * collision is resolved"): t from the inverse cumulative cross section with
+ * word 1 of the scattering draw, phi = 2 pi u2 from word 2, the scattered
+ * photon built in the rest frame (energy x/(1 + x t), polar angle from the
+ * incoming rest-frame direction, azimuth about it in the Duff et al. basis),
+ * boosted back, and the electron given the momentum the photon lost:
+ * u <- u + k - k1. */
+void or_collide(const double u[3], const double k[3], uint64_t seed, uint64_t step, uint32_t ctr_id,
+                double u_out[3], double k_out[3])
+{
+    double inv[2];
+    or_invariants(u, k, inv);
+    double x = inv[0];
+    double eps = norm3(k);
+    uint32_t r[4];
+    draw(seed, step, 3u, ctr_id, r);
+    double u1 = unif_open(r[1]);
+    double u2 = unif_closed0(r[2]);
+    double t = or_kn_sample_t(x, u1);
+    double phi = 2.0 * OR_PI * u2;
+    double eps_r, kr[3];
+    or_boost_to_rest(u, eps, k, &eps_r, kr);
+    /* the rest-frame energy is the invariant x; its direction is kr/|kr| */
+    double krn = norm3(kr);
+    double n[3] = {kr[0] / krn, kr[1] / krn, kr[2] / krn};
+    double b1[3], b2[3];
+    or_onb(n, b1, b2);
+    double cth = 1.0 - t;
+    double sth = sqrt(t * (2.0 - t));
+    double cph = cos(phi), sph = sin(phi);
+    double e1r = x / (1.0 + x * t);
+    double k1r[3];
+    for (int i = 0; i < 3; ++i)
+        k1r[i] = e1r * (cth * n[i] + sth * (cph * b1[i] + sph * b2[i]));
+    double e1, k1[3];
+    or_boost_to_lab(u, e1r, k1r, &e1, k1);
+    for (int i = 0; i < 3; ++i) {
+        u_out[i] = u[i] + k[i] - k1[i];
+        k_out[i] = k1[i];
+    }
+}
+
 /* One pair event (Sec. 3.1, Sec. 3.2).
  *   a = n dt s(x) v,  P = 1 - exp(-a)   (evaluated as -expm1(-a));
  *   scatter iff u0 < P, u0 from word 0 of the scattering draw;
- *   if scattered: t from the inverse cumulative cross section with word 1,
- *   phi = 2 pi u2 from word 2, the scattered photon built in the rest frame
- *   (energy x/(1 + x t), polar angle from the incoming rest-frame direction,
- *   azimuth about it in the Duff et al. basis), boosted back, and the
- *   electron given the momentum the photon lost: u <- u + k - k1.
+ *   if scattered: or_collide.
  * n_dens is the pair density (normalised units), dt the time step.
  * Outputs: u_out, k_out (unchanged when not scattered), P, flag, x. */
 void or_scatter_event(const double u[3], const double k[3], double n_dens, double dt,
@@ -293,32 +331,7 @@ void or_scatter_event(const double u[3], const double k[3], double n_dens, doubl
     double u0 = unif_closed0(r[0]);
     int flag = (u0 < P) ? 1 : 0;
     for (int i = 0; i < 3; ++i) { u_out[i] = u[i]; k_out[i] = k[i]; }
-    if (flag) {
-        double u1 = unif_open(r[1]);
-        double u2 = unif_closed0(r[2]);
-        double t = or_kn_sample_t(x, u1);
-        double phi = 2.0 * OR_PI * u2;
-        double eps_r, kr[3];
-        or_boost_to_rest(u, eps, k, &eps_r, kr);
-        /* the rest-frame energy is the invariant x; its direction is kr/|kr| */
-        double krn = norm3(kr);
-        double n[3] = {kr[0] / krn, kr[1] / krn, kr[2] / krn};
-        double b1[3], b2[3];
-        or_onb(n, b1, b2);
-        double cth = 1.0 - t;
-        double sth = sqrt(t * (2.0 - t));
-        double cph = cos(phi), sph = sin(phi);
-        double e1r = x / (1.0 + x * t);
-        double k1r[3];
-        for (int i = 0; i < 3; ++i)
-            k1r[i] = e1r * (cth * n[i] + sth * (cph * b1[i] + sph * b2[i]));
-        double e1, k1[3];
-        or_boost_to_lab(u, e1r, k1r, &e1, k1);
-        for (int i = 0; i < 3; ++i) {
-            u_out[i] = u[i] + k[i] - k1[i];
-            k_out[i] = k1[i];
-        }
-    }
+    if (flag) or_collide(u, k, seed, step, ctr_id, u_out, k_out);
     *P_out = P;
     *flag_out = flag;
     *x_out = x;
