@@ -70,6 +70,8 @@ def lib():
         L.or_onb.restype = None
         L.or_scatter_event.argtypes = [P, P, d, d, u64, u64, u32, P, P, P, P, P]
         L.or_scatter_event.restype = None
+        L.or_bernoulli_u0.argtypes = [u64, u64, u32]
+        L.or_bernoulli_u0.restype = d
         L.or_collide.argtypes = [P, P, u64, u64, u32, P, P]
         L.or_collide.restype = None
         L.or_pair_key.argtypes = [u64, u64, u32, u32]
@@ -175,6 +177,17 @@ def scatter_event(u, k, n_dens, dt, seed, step, ctr_id):
                            int(ctr_id), _p(uo), _p(ko), ctypes.byref(P), ctypes.byref(f),
                            ctypes.byref(x))
     return uo, ko, P.value, f.value, x.value
+
+
+def bernoulli_u0(seed, step, p) -> float:
+    """The uniform the probability of pair p is compared with (Sec. 3.1)."""
+    return float(lib().or_bernoulli_u0(int(seed), int(step), int(p)))
+
+
+def angle_words(seed, step, p):
+    """The two Philox words of pair p's scattering angles (stream 4)."""
+    return philox4x32_10([int(p) & 0xFFFFFFFF, int(step) & 0xFFFFFFFF, 4, int(step) >> 32],
+                         [int(seed) & 0xFFFFFFFF, int(seed) >> 32])[:2]
 
 
 def collide(u, k, seed, step, ctr_id):

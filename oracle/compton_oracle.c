@@ -65,9 +65,13 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
     out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
 }
 
-/* Counter layout used by the whole method: (particle id, step low word,
- * stream, step high word) under key (seed low word, seed high word).
- * Streams: 1 = electron pairing key, 2 = photon pairing key, 3 = scattering. */
+/* Counter layout used by the whole method: (id, step low word, stream, step
+ * high word) under key (seed low word, seed high word).  Streams:
+ *   1  electron pairing key   (id = particle id, word 0)
+ *   2  photon pairing key     (id = particle id, word 0)
+ *   3  Bernoulli trial        (id = pair index / 4, word = pair index mod 4:
+ *                              one block serves four consecutive pairs)
+ *   4  scattering angles      (id = pair index, words 0 and 1) */
 static void draw(uint64_t seed, uint64_t step, uint32_t stream, uint32_t id, uint32_t out[4])
 {
     uint32_t ctr[4] = {id, (uint32_t)step, stream, (uint32_t)(step >> 32)};
@@ -264,9 +268,19 @@ void or_onb(const double n[3], double b1[3], double b2[3])
     b2[2] = -n[1];
 }
 
+/* The uniform of the Bernoulli trial of pair p (Sec. 3.1: the probability
+ * is compared against a random number): word p mod 4 of the stream-3 block
+ * at counter p / 4. */
+double or_bernoulli_u0(uint64_t seed, uint64_t step, uint32_t p)
+{
+    uint32_t r[4];
+    draw(seed, step, 3u, p >> 2, r);
+    return unif_closed0(r[p & 3u]);
+}
+
 /* The collision of one pair with its own draws (Sec. 3.1, "the kinetic
  * collision is resolved"): t from the inverse cumulative cross section with
- * word 1 of the scattering draw, phi = 2 pi u2 from word 2, the scattered
+ * word 0 of the stream-4 draw, phi = 2 pi u2 from word 1, the scattered
  * photon built in the rest frame (energy x/(1 + x t), polar angle from the
  * incoming rest-frame direction, azimuth about it in the Duff et al. basis),
  * boosted back, and the electron given the momentum the photon lost:
@@ -279,9 +293,9 @@ void or_collide(const double u[3], const double k[3], uint64_t seed, uint64_t st
     double x = inv[0];
     double eps = norm3(k);
     uint32_t r[4];
-    draw(seed, step, 3u, ctr_id, r);
-    double u1 = unif_open(r[1]);
-    double u2 = unif_closed0(r[2]);
+    draw(seed, step, 4u, ctr_id, r);
+    double u1 = unif_open(r[0]);
+    double u2 = unif_closed0(r[1]);
     double t = or_kn_sample_t(x, u1);
     double phi = 2.0 * OR_PI * u2;
     double eps_r, kr[3];
@@ -308,7 +322,7 @@ void or_collide(const double u[3], const double k[3], uint64_t seed, uint64_t st
 
 /* One pair event (Sec. 3.1, Sec. 3.2).
  *   a = n dt s(x) v,  P = 1 - exp(-a)   (evaluated as -expm1(-a));
- *   scatter iff u0 < P, u0 from word 0 of the scattering draw;
+ *   scatter iff u0 < P, u0 = or_bernoulli_u0;
  *   if scattered: or_collide.
  * n_dens is the pair density (normalised units), dt the time step.
  * Outputs: u_out, k_out (unchanged when not scattered), P, flag, x. */
@@ -326,9 +340,7 @@ void or_scatter_event(const double u[3], const double k[3], double n_dens, doubl
         double a = n_dens * dt * s * v;
         P = -expm1(-a);
     }
-    uint32_t r[4];
-    draw(seed, step, 3u, ctr_id, r);
-    double u0 = unif_closed0(r[0]);
+    double u0 = or_bernoulli_u0(seed, step, ctr_id);
     int flag = (u0 < P) ? 1 : 0;
     for (int i = 0; i < 3; ++i) { u_out[i] = u[i]; k_out[i] = k[i]; }
     if (flag) or_collide(u, k, seed, step, ctr_id, u_out, k_out);

@@ -83,11 +83,7 @@ def _dev_array(torch, ptr, n):
 
 def u0_of_pairs(seed, step, n_pairs):
     """The Bernoulli uniform of every pair, from the oracle's Philox."""
-    u0 = np.zeros(n_pairs)
-    for p in range(n_pairs):
-        r = oracle.philox4x32_10([p, step & 0xFFFFFFFF, 3, step >> 32], [seed & 0xFFFFFFFF, seed >> 32])
-        u0[p] = (int(r[0]) >> 8) / 2.0**24
-    return u0
+    return np.array([oracle.bernoulli_u0(seed, step, p) for p in range(n_pairs)])
 
 
 def energy_scale(u, k):

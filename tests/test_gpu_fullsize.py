@@ -57,8 +57,7 @@ def test_full_size_sampled_pairs_match_oracle(full):
         n_dens = max(off_e[c + 1] - off_e[c], off_g[c + 1] - off_g[c]) * w.w_over_v
         uo, ko, P, f, _ = oracle.scatter_event(u, k, n_dens, w.dt, w.seed, 3, int(p))
         assert abs(g["P"][p] - P) <= 2e-5 * P + 1e-9
-        r = oracle.philox4x32_10([int(p), 3, 3, 0], [w.seed, 0])
-        u0 = (int(r[0]) >> 8) / 2.0**24
+        u0 = oracle.bernoulli_u0(w.seed, 3, int(p))
         if g["flag"][p] != f:
             assert abs(u0 - P) < 1e-6
             flips += 1

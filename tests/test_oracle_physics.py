@@ -303,9 +303,10 @@ def test_probability_closed_form_and_bernoulli():
         xr, vr = _x_v_mp(u, k)
         a = n * dt * kn_mp(xr) * vr
         assert P == pytest.approx(float(1 - mpmath.exp(-a)), rel=1e-12)
-        # Bernoulli: word 0 of Philox(counter=(id, step, 3, 0), key=(seed, 0))
-        r = oracle.philox4x32_10([i, 3, 3, 0], [17, 0])
-        u0 = (int(r[0]) >> 8) / 2.0**24
+        # Bernoulli: word i mod 4 of Philox(counter=(i / 4, step, 3, 0), key=(seed, 0))
+        r = oracle.philox4x32_10([i >> 2, 3, 3, 0], [17, 0])
+        u0 = (int(r[i & 3]) >> 8) / 2.0**24
+        assert oracle.bernoulli_u0(17, 3, i) == u0
         assert flag == int(u0 < P)
         if not flag:
             assert np.array_equal(uo, u) and np.array_equal(ko, k)
@@ -344,8 +345,8 @@ def test_scattered_events_conserve_energy_momentum():
         assert dE < 1e-12 and dp < 1e-12 and ds < 1e-11
         # scattered photon energy follows the Compton formula in the rest frame
         er1, _ = oracle.boost_to_rest(u, ko)
-        r = oracle.philox4x32_10([i, 0, 3, 0], [23, 0])
-        t = oracle.kn_sample_t(x, ((int(r[1]) >> 8) + 0.5) / 2.0**24)
+        r = oracle.philox4x32_10([i, 0, 4, 0], [23, 0])  # angle draws: stream 4
+        t = oracle.kn_sample_t(x, ((int(r[0]) >> 8) + 0.5) / 2.0**24)
         assert er1 == pytest.approx(x / (1 + x * t), rel=1e-8)
     assert seen > 1000
 
