@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--ppc", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mlp", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--train-steps", type=int, default=600)
     return ap.parse_args()
 
 
@@ -174,7 +178,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     A = [species(w.e), species(w.g)]
     B = [cg.Species.empty_like(A[0]), cg.Species.empty_like(A[1])]
     nmax = max(w.n_e, w.n_g)
-    ctx = cg.compton_init(w.n_cells, nmax, w.w_over_v, w.dt, w.seed, device=local_rank)
+    ctx = cg.compton_init(w.n_cells, nmax, w.w_over_v, w.dt, w.seed, device=local_rank,
+                          max_train_batch=8192)
     stream = torch.cuda.current_stream(dev)
 
     def one_step(step, src, dst, ev=None):
@@ -250,6 +255,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if not args.no_e2e:
         e2e = run_e2e(args, cg, torch, ctx, w, stream, dev)
 
+    mlp = None
+    if not args.no_mlp:
+        mlp = run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step, peaks)
+        step += args.warmup + args.steps + 2
+
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = run_serving(args, cg, torch, ctx, bufs[step % 2], dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         r, npairs, dt, sample = cpu_oracle_rate()
@@ -276,10 +290,162 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "mlp": mlp,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def train_surrogate(cg, torch, ctx, dev, n_samples=262144, steps=600, batch=8192, lr=1e-3):
+    """Train the network on the GPU on analytic targets over the surrogate's
+    range (gamma log-uniform on [1, 1e3], eps log-uniform on [1e-4, 1]);
+    weights Glorot-uniform, seed 0.  Not timed."""
+    from paper_2206_02937_gb300 import workloads as wl
+    rng = np.random.default_rng(0)
+    theta = np.zeros(12993, dtype=np.float32)
+    at = 0
+    for o, i in [(64, 6), (64, 64), (64, 64), (64, 64), (1, 64)]:
+        lim = np.sqrt(6.0 / (o + i))
+        theta[at:at + o * i] = rng.uniform(-lim, lim, o * i)
+        at += o * i + o
+    cg.compton_mlp_set_params(ctx, theta)
+    u, k = wl.c3(n_samples, seed=30)
+    ut, kt = torch.from_numpy(u).to(dev), torch.from_numpy(k).to(dev)
+    r = torch.zeros(n_samples, device=dev)
+    cg.compton_kn_ratio(ctx, ut, kt, r)
+    gen = torch.Generator(device=dev).manual_seed(0)
+    losses = []
+    for it in range(steps):
+        idx = torch.randint(0, n_samples, (batch,), device=dev, generator=gen)
+        loss = cg.compton_mlp_train_step(ctx, ut[:, idx].contiguous(), kt[:, idx].contiguous(),
+                                         r[idx].contiguous(), None, lr, want_loss=(it % 100 == 0 or it == steps - 1))
+        if loss is not None:
+            losses.append(loss)
+    cg.compton_mlp_calibrate(ctx, ut[:, :65536].contiguous(), kt[:, :65536].contiguous())
+    torch.cuda.synchronize()
+    return {"steps": steps, "batch": batch, "lr": lr, "samples": n_samples, "loss_first": losses[0],
+            "loss_last": losses[-1]}
+
+
+def run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step0, peaks):
+    """The whole step with the surrogate probability (BF16 tensor cores), its
+    network kernel alone, and its error against the analytic path on the same
+    pairs and draws."""
+    train = train_surrogate(cg, torch, ctx, dev, steps=args.train_steps)
+    mode = cg.MODE_MLP_BF16
+    step = step0
+
+    def one(src, dst, st, md, prob=None):
+        pairs = cg.compton_bin_pairs(ctx, src[0], src[1], dst[0], dst[1], st, stream)
+        cg.compton_scatter_step(ctx, dst[0], dst[1], pairs, md, st, prob, None, stream)
+        return pairs
+
+    for _ in range(args.warmup):
+        one(bufs[step % 2], bufs[(step + 1) % 2], step, mode)
+        step += 1
+    torch.cuda.synchronize()
+    cg.compton_get_stats(ctx, reset=True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        one(bufs[step % 2], bufs[(step + 1) % 2], step, mode)
+        step += 1
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    st = cg.compton_get_stats(ctx, reset=True)
+    # network kernel alone on 16.8M samples (electron/photon arrays as pairs)
+    src = bufs[step % 2]
+    n = min(src[0].n, src[1].n)
+    u = torch.stack([src[0].ux[:n], src[0].uy[:n], src[0].uz[:n]])
+    k = torch.stack([src[1].ux[:n], src[1].uy[:n], src[1].uz[:n]])
+    rr = torch.empty(n, device=dev)
+    kern = {}
+    for md, name in ((cg.MODE_MLP_BF16, "bf16"), (cg.MODE_MLP_FP8, "fp8"), (cg.MODE_MLP_FP32, "fp32")):
+        cg.compton_mlp_infer(ctx, u, k, md, rr, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            cg.compton_mlp_infer(ctx, u, k, md, rr, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kern[name] = e0.elapsed_time(e1) / 3
+    flops = 2.0 * (6 * 64 + 3 * 64 * 64 + 64) * n
+    peak_bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    achieved = flops / (kern["bf16"] * 1e-3) / 1e12
+    # error against the analytic path: same input, same step, both modes
+    P_pl = torch.empty(n, device=dev)
+    P_ml = torch.empty(n, device=dev)
+    a_copy = [cg.Species(*[t.clone() for t in (s.ux, s.uy, s.uz, s.cell, s.id)]) for s in bufs[step % 2]]
+    scratch = [cg.Species.empty_like(s) for s in a_copy]
+    one(a_copy, scratch, 777, cg.MODE_PLAIN, P_pl)
+    np_pairs = int(cg.compton_get_stats(ctx, reset=True)["pairs_tested"])
+    one(a_copy, scratch, 777, mode, P_ml)
+    torch.cuda.synchronize()
+    pl, mlv = P_pl[:np_pairs].double(), P_ml[:np_pairs].double()
+    rel = ((mlv - pl).abs() / pl.clamp_min(1e-30))
+    err = {"mean_abs_P": float((mlv - pl).abs().mean()), "mean_rel_P": float(rel.mean()),
+           "median_rel_P": float(rel.median()), "mean_P_plain": float(pl.mean()),
+           "collision_rate_ratio": float(mlv.sum() / pl.sum())}
+    return {"mode": "bf16", "metric": METRIC, "value": st["pairs_tested"] / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms / args.steps, "fallback_fraction": st["mlp_fallbacks"] / max(1, st["pairs_tested"]),
+            "network_kernel_ms": kern, "network_samples": n,
+            "roofline": {"kernel": "k_mlp_tc<bf16>", "bound": "tensor", "achieved": achieved, "peak": peak_bf16,
+                         "unit": "TFLOP/s", "frac": achieved / peak_bf16,
+                         "note": "algorithmic FLOPs 2(6*64+3*64*64+64) per sample; peak: measured bf16 burst"},
+            "error_vs_plain": err, "train": train}
+
+
+def run_serving(args, cg, torch, ctx, src, dev):
+    """Continuous batching: requests arrive as a Poisson stream at 200/s with
+    sizes log-uniform in [1e3, 1e7] pairs, each a slice of the device-resident
+    sorted particle arrays, half plain and half BF16 surrogate, admitted under
+    a 40 GB budget.  Latency = completion - scheduled arrival."""
+    rng = np.random.default_rng(4)
+    n_req = args.serve_requests
+    arrivals = np.cumsum(rng.exponential(1.0 / 200.0, n_req))
+    sizes = np.floor(10 ** rng.uniform(3, 7, n_req)).astype(np.int64)
+    n_pool = min(src[0].n, src[1].n)
+    u_pool = torch.stack([src[0].ux[:n_pool], src[0].uy[:n_pool], src[0].uz[:n_pool]])
+    k_pool = torch.stack([src[1].ux[:n_pool], src[1].uy[:n_pool], src[1].uz[:n_pool]])
+    budget = 40 << 30
+    cg.compton_serve_start(ctx, budget, 1024)
+    outs, pending, lat, pairs_done = {}, {}, [], 0
+    t_start = time.perf_counter()
+    i = 0
+    while i < n_req or pending:
+        now = time.perf_counter() - t_start
+        while i < n_req and arrivals[i] <= now:
+            n = int(sizes[i])
+            off = int(rng.integers(0, n_pool - n))
+            uo = torch.empty((3, n), device=dev)
+            ko = torch.empty((3, n), device=dev)
+            mode = cg.MODE_PLAIN if i % 2 == 0 else cg.MODE_MLP_BF16
+            t = cg.compton_submit(ctx, u_pool[:, off:off + n], k_pool[:, off:off + n], uo, ko, 1.0, 5000 + i, 0, mode)
+            pending[t] = (i, n)
+            outs[t] = (uo, ko)
+            i += 1
+        for t in list(pending):
+            r = cg.compton_poll(ctx, t)
+            if r is not None:
+                idx, n = pending.pop(t)
+                done = time.perf_counter() - t_start
+                lat.append(done - arrivals[idx])
+                pairs_done += n
+                outs.pop(t)
+        time.sleep(0.0002)
+    wall = time.perf_counter() - t_start
+    info = cg.compton_serve_info(ctx)
+    cg.compton_serve_stop(ctx)
+    lat_ms = np.array(lat) * 1e3
+    return {"requests": n_req, "arrival_rate_per_s": 200, "sizes": "log-uniform [1e3, 1e7] pairs",
+            "modes": "50/50 plain / bf16 surrogate", "budget_gb": budget / 2**30,
+            "peak_pool_gb": info["peak"] / 2**30, "p50_ms": float(np.percentile(lat_ms, 50)),
+            "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
+            "pairs": int(pairs_done), "wall_s": wall, "pairs_per_s": pairs_done / wall,
+            "offered_pairs_per_s": float(sizes.sum() / arrivals[-1])}
 
 
 def run_e2e(args, cg, torch, ctx, w, stream, dev):

@@ -266,6 +266,73 @@ compton_status compton_mlp_save(struct compton_ctx* ctx, void* buf, size_t* len)
 /* Load a blob written by compton_mlp_save.  EINVAL on a bad header or size. */
 compton_status compton_mlp_load(struct compton_ctx* ctx, const void* buf, size_t len);
 
+/* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of pre-paired batches (Sec. 2: the network */
+/* object runs "for any given batch of inputs"; a PIC code produces such   */
+/* batches from many tiles and time steps).                                */
+/* ---------------------------------------------------------------------- */
+
+/* One request: n pre-paired electrons/photons (device arrays, read), the
+ * arrays that receive the momenta after the step (device, may equal the
+ * inputs), the pair density per pair (n_dens_dev, nullable) or one value
+ * (n_dens), the request's Philox seed and step, and the probability mode.
+ * Pair i of a request uses counter id i under key seed, exactly as
+ * compton_scatter_pairs, so its result does not depend on what else runs. */
+typedef struct compton_request {
+    const float* ux_in_dev;
+    const float* uy_in_dev;
+    const float* uz_in_dev;
+    const float* kx_in_dev;
+    const float* ky_in_dev;
+    const float* kz_in_dev;
+    float* ux_out_dev;
+    float* uy_out_dev;
+    float* uz_out_dev;
+    float* kx_out_dev;
+    float* ky_out_dev;
+    float* kz_out_dev;
+    const float* n_dens_dev;
+    float n_dens;
+    int64_t n;
+    uint64_t seed;
+    uint64_t step;
+    compton_mode mode;
+} compton_request;
+
+typedef struct compton_result {
+    compton_status status;
+    uint64_t scatters;  /* collisions in this request                      */
+    double latency_s;   /* from compton_submit to completion (host clock)  */
+    double queue_s;     /* from compton_submit to admission                */
+} compton_result;
+
+/* Start the serving engine: a device pool of pool_bytes (the memory budget;
+ * each admitted request holds 28 bytes per pair, 32 in surrogate modes) and
+ * at most max_active requests admitted at once.  The pool is allocated here,
+ * once.  EINVAL if already started. */
+compton_status compton_serve_start(struct compton_ctx* ctx, uint64_t pool_bytes, int32_t max_active);
+
+/* Stop the engine after the work in flight; requests not yet done are
+ * dropped.  compton_destroy calls it. */
+compton_status compton_serve_stop(struct compton_ctx* ctx);
+
+/* Queue a request; returns at once with a ticket.  The engine admits it when
+ * a block of the pool fits it and runs its tiles together with the other
+ * admitted requests.  The caller keeps the input and output arrays alive and
+ * unchanged until compton_poll returns OK.  ERANGE if the request can never
+ * fit the pool, EBUSY if the queue is full (retry), ENOMODEL for a surrogate
+ * mode without a network.  Thread-safe. */
+compton_status compton_submit(struct compton_ctx* ctx, const compton_request* req, uint64_t* ticket);
+
+/* ENOTREADY until the request's outputs are written, then OK with *out
+ * filled (the ticket is retired).  EINVAL for an unknown ticket.
+ * Thread-safe. */
+compton_status compton_poll(struct compton_ctx* ctx, uint64_t ticket, compton_result* out);
+
+/* Pool bytes in use now, the peak since start, and the pool size. */
+compton_status compton_serve_info(struct compton_ctx* ctx, uint64_t* bytes_in_use, uint64_t* peak_bytes,
+                                  uint64_t* pool_bytes);
+
 /* The scattering-angle sampler of compton_scatter_step on its own, for
  * validation (the paper resolves each collision by sampling the scattered
  * photon, Sec. 3.1).  For each i: x_dev[i] is the rest-frame photon energy,

@@ -283,3 +283,62 @@ def compton_mlp_get_grad(ctx: int):
     g = np.zeros(N_MLP_PARAMS, dtype=np.float32)
     _check(lib().compton_mlp_get_grad(c_p(ctx), c_p(g.ctypes.data), N_MLP_PARAMS), "compton_mlp_get_grad", ctx)
     return g
+
+
+class compton_request(ctypes.Structure):
+    _fields_ = [(nm, c_p) for nm in ("ux_in_dev", "uy_in_dev", "uz_in_dev", "kx_in_dev", "ky_in_dev", "kz_in_dev",
+                                     "ux_out_dev", "uy_out_dev", "uz_out_dev", "kx_out_dev", "ky_out_dev",
+                                     "kz_out_dev", "n_dens_dev")] + \
+               [("n_dens", c_f32), ("n", c_i64), ("seed", c_u64), ("step", c_u64), ("mode", c_i32)]
+
+
+class compton_result(ctypes.Structure):
+    _fields_ = [("status", c_i32), ("scatters", c_u64), ("latency_s", c_f64), ("queue_s", c_f64)]
+
+
+SIGNATURES.update({
+    "compton_serve_start": (c_i32, [c_p, c_u64, c_i32]),
+    "compton_serve_stop": (c_i32, [c_p]),
+    "compton_submit": (c_i32, [c_p, ctypes.POINTER(compton_request), ctypes.POINTER(c_u64)]),
+    "compton_poll": (c_i32, [c_p, c_u64, ctypes.POINTER(compton_result)]),
+    "compton_serve_info": (c_i32, [c_p, ctypes.POINTER(c_u64), ctypes.POINTER(c_u64), ctypes.POINTER(c_u64)]),
+})
+
+
+def compton_serve_start(ctx: int, pool_bytes: int, max_active: int = 1024) -> None:
+    _check(lib().compton_serve_start(c_p(ctx), int(pool_bytes), int(max_active)), "compton_serve_start", ctx)
+
+
+def compton_serve_stop(ctx: int) -> None:
+    _check(lib().compton_serve_stop(c_p(ctx)), "compton_serve_stop", ctx)
+
+
+def compton_submit(ctx: int, u_in, k_in, u_out, k_out, n_dens, seed: int, step: int = 0,
+                   mode: int = MODE_PLAIN) -> int:
+    """u_in, k_in, u_out, k_out: (3, n) float32 CUDA tensors (rows contiguous);
+    n_dens: a float or an (n,) float32 CUDA tensor.  Returns the ticket."""
+    n = int(u_in.shape[1])
+    dens_ptr, dens_val = (c_p(0), float(n_dens)) if isinstance(n_dens, (int, float)) else (_ptr(n_dens), 0.0)
+    r = compton_request(*[_ptr(t) for t in (u_in[0], u_in[1], u_in[2], k_in[0], k_in[1], k_in[2],
+                                            u_out[0], u_out[1], u_out[2], k_out[0], k_out[1], k_out[2])],
+                        dens_ptr, dens_val, n, int(seed), int(step), int(mode))
+    t = c_u64(0)
+    _check(lib().compton_submit(c_p(ctx), ctypes.byref(r), ctypes.byref(t)), "compton_submit", ctx)
+    return int(t.value)
+
+
+def compton_poll(ctx: int, ticket: int):
+    """None while the request is running, else a dict with its result."""
+    res = compton_result()
+    st = lib().compton_poll(c_p(ctx), int(ticket), ctypes.byref(res))
+    if st == COMPTON_ENOTREADY:
+        return None
+    _check(st, "compton_poll", ctx)
+    return dict(status=res.status, scatters=res.scatters, latency_s=res.latency_s, queue_s=res.queue_s)
+
+
+def compton_serve_info(ctx: int) -> dict:
+    a, b, c = c_u64(0), c_u64(0), c_u64(0)
+    _check(lib().compton_serve_info(c_p(ctx), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "compton_serve_info", ctx)
+    return dict(in_use=a.value, peak=b.value, pool=c.value)

@@ -120,6 +120,7 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
         return COMPTON_EINVAL;
     }
     size_t o_tr = cv.take<uint8_t>(cfg->max_train_batch > 0 ? compton::train_scratch_bytes(cfg->max_train_batch) : 1);
+    size_t o_rb = cv.take<float>(P > 0 ? P : 1);
     const size_t total = align_up(cv.used, 256);
     if (cfg->mem_budget_bytes && total > cfg->mem_budget_bytes) {
         delete ctx;
@@ -161,6 +162,7 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     m.loss = reinterpret_cast<float*>(base + o_lo);
     m.amax = reinterpret_cast<float*>(base + o_ax);
     ctx->train_scratch = base + o_tr;
+    ctx->r_buf = reinterpret_cast<float*>(base + o_rb);
     m.fs[0] = 1.0f;   // s_u
     m.fs[1] = 7.0f;   // n_u
     m.fs[2] = 1e-4f;  // s_k
@@ -180,6 +182,7 @@ compton_status compton_destroy(compton_ctx* ctx)
 {
     if (!ctx) return COMPTON_OK;
     cudaSetDevice(ctx->cfg.device);
+    compton::serve_stop(ctx);
     cudaDeviceSynchronize();
     if (ctx->arena) cudaFree(ctx->arena);
     delete ctx;
@@ -242,7 +245,8 @@ compton_status compton_scatter_step(compton_ctx* ctx, compton_species* e, compto
     if (!ctx || !pairs || !species_ok(e) || !species_ok(g)) return COMPTON_EINVAL;
     if (pairs->cell_info_dev != ctx->cinfo || pairs->n_cells != ctx->cfg.n_cells) return COMPTON_EINVAL;
     if (pairs->max_pairs > (e->n < g->n ? e->n : g->n)) return COMPTON_EINVAL;
-    if (mode != COMPTON_MODE_PLAIN) return COMPTON_ENOMODEL;
+    if ((int)mode < 0 || (int)mode > 3) return COMPTON_EINVAL;
+    if (mode != COMPTON_MODE_PLAIN && !ctx->mlp_loaded) return COMPTON_ENOMODEL;
     return compton::launch_scatter_binned(ctx, e, g, pairs, mode, step, prob_out, flag_out, stream);
 }
 
@@ -254,7 +258,8 @@ compton_status compton_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, flo
     if (!ctx || n < 0 || n > INT32_MAX) return COMPTON_EINVAL;
     if (n == 0) return COMPTON_OK;
     if (!ux || !uy || !uz || !kx || !ky || !kz || !n_dens) return COMPTON_EINVAL;
-    if (mode != COMPTON_MODE_PLAIN) return COMPTON_ENOMODEL;
+    if ((int)mode < 0 || (int)mode > 3) return COMPTON_EINVAL;
+    if (mode != COMPTON_MODE_PLAIN && !ctx->mlp_loaded) return COMPTON_ENOMODEL;
     return compton::launch_scatter_pairs(ctx, ux, uy, uz, kx, ky, kz, n_dens, n, seed, step, mode, prob_out,
                                          flag_out, stream);
 }
@@ -420,6 +425,49 @@ compton_status compton_mlp_load(compton_ctx* ctx, const void* buf, size_t len)
                                      cudaMemcpyHostToDevice));
     ctx->adam_step = h.adam_step;
     return COMPTON_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Serving
+// ---------------------------------------------------------------------------
+compton_status compton_serve_start(compton_ctx* ctx, uint64_t pool_bytes, int32_t max_active)
+{
+    if (!ctx || pool_bytes < 4096 || max_active <= 0 || max_active > 65536) return COMPTON_EINVAL;
+    if (ctx->serve) return COMPTON_EINVAL;
+    COMPTON_CUDA_TRY(ctx, cudaSetDevice(ctx->cfg.device));
+    return compton::serve_start(ctx, pool_bytes, max_active);
+}
+
+compton_status compton_serve_stop(compton_ctx* ctx)
+{
+    if (!ctx) return COMPTON_EINVAL;
+    return compton::serve_stop(ctx);
+}
+
+compton_status compton_submit(compton_ctx* ctx, const compton_request* r, uint64_t* ticket)
+{
+    if (!ctx || !r || !ticket || !ctx->serve) return COMPTON_EINVAL;
+    if (r->n <= 0 || r->n > INT32_MAX) return COMPTON_EINVAL;
+    if (!r->ux_in_dev || !r->uy_in_dev || !r->uz_in_dev || !r->kx_in_dev || !r->ky_in_dev || !r->kz_in_dev ||
+        !r->ux_out_dev || !r->uy_out_dev || !r->uz_out_dev || !r->kx_out_dev || !r->ky_out_dev || !r->kz_out_dev)
+        return COMPTON_EINVAL;
+    if ((int)r->mode < 0 || (int)r->mode > 3) return COMPTON_EINVAL;
+    if (!r->n_dens_dev && !(r->n_dens >= 0.0f)) return COMPTON_EINVAL;
+    if (r->mode != COMPTON_MODE_PLAIN && !ctx->mlp_loaded) return COMPTON_ENOMODEL;
+    return compton::serve_submit(ctx, r, ticket);
+}
+
+compton_status compton_poll(compton_ctx* ctx, uint64_t ticket, compton_result* out)
+{
+    if (!ctx || !out) return COMPTON_EINVAL;
+    return compton::serve_poll(ctx, ticket, out);
+}
+
+compton_status compton_serve_info(compton_ctx* ctx, uint64_t* bytes_in_use, uint64_t* peak_bytes,
+                                  uint64_t* pool_bytes)
+{
+    if (!ctx || !bytes_in_use || !peak_bytes || !pool_bytes) return COMPTON_EINVAL;
+    return compton::serve_info(ctx, bytes_in_use, peak_bytes, pool_bytes);
 }
 
 compton_status compton_kn_sample_angle(compton_ctx* ctx, const float* x, const uint32_t* r, int64_t n,

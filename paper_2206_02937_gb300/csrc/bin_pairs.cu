@@ -348,7 +348,7 @@ __device__ __forceinline__ void warp_rank_chunk(const uint64_t* key64, int32_t* 
 // so the order is total and the network always yields a permutation.  Strides
 // below 32 exchange through shuffles, larger ones swap registers.
 template <int E>
-__device__ __forceinline__ void warp_bitonic_segment(const uint64_t* key64, int32_t* perm, int a, int n)
+__device__ __forceinline__ void warp_bitonic_segment(uint64_t* key64, int32_t* perm, int a, int n)
 {
     const int lane = (int)lane_id();
     uint64_t k[E];
@@ -402,27 +402,94 @@ __device__ __forceinline__ void warp_bitonic_segment(const uint64_t* key64, int3
             }
         }
     }
+    __syncwarp();
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int i = e * 32 + lane;
-        if (i < n) perm[a + i] = p[e];
+        if (i < n) {
+            perm[a + i] = p[e];
+            key64[a + i] = k[e];
+        }
     }
+    __syncwarp();
 }
 
-// Cells of up to 64 particles: bitonic network in registers; larger cells:
-// register-held ranking (n broadcast reads per 32E elements).
-__device__ __forceinline__ void sort_segment(const uint64_t* key64, int32_t* perm, int a, int n)
+// Count of sorted keys in key64[b .. b+m) below k (strict) or not above k.
+__device__ __forceinline__ int count_below(const uint64_t* key64, int b, int m, uint64_t k, bool or_equal)
+{
+    int pos = 0;
+#pragma unroll
+    for (int step = 32; step > 0; step >>= 1) {
+        if (pos + step <= m) {
+            const uint64_t v = key64[b + pos + step - 1];
+            if (v < k || (or_equal && v == k)) pos += step;
+        }
+    }
+    return pos;
+}
+
+// Segments of 65..256: each 64-element chunk sorted by the bitonic network
+// (keys written back in sorted order, source indices in perm), then every
+// element's final rank = its rank in its chunk + the number of elements
+// before it in each other sorted chunk (binary search; ties go to the lower
+// chunk, so ranks stay unique).  Results are written after all ranks are
+// known.
+__device__ __forceinline__ void warp_chunk_merge_segment(uint64_t* key64, int32_t* perm, int a, int n)
+{
+    const int lane = (int)lane_id();
+    const int nc = (n + 63) >> 6;
+    for (int c = 0; c < nc; ++c) {
+        const int cn = n - 64 * c < 64 ? n - 64 * c : 64;
+        warp_bitonic_segment<2>(key64, perm, a + 64 * c, cn);
+    }
+    uint64_t kk[8];
+    int32_t pp[8];
+    int rank[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int idx = lane + 32 * t;
+        rank[t] = -1;
+        if (idx < n) {
+            const int c = idx >> 6;
+            kk[t] = key64[a + idx];
+            pp[t] = perm[a + idx];
+            int r = idx & 63;
+            for (int c2 = 0; c2 < nc; ++c2) {
+                if (c2 == c) continue;
+                const int cn2 = n - 64 * c2 < 64 ? n - 64 * c2 : 64;
+                r += count_below(key64, a + 64 * c2, cn2, kk[t], c2 < c);
+            }
+            rank[t] = r;
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        if (rank[t] >= 0) {
+            key64[a + rank[t]] = kk[t];
+            perm[a + rank[t]] = pp[t];
+        }
+    }
+    __syncwarp();
+}
+
+// Cells of up to 64 particles: bitonic network in registers; up to 256:
+// sorted 64-element chunks merged by rank; larger: register-held ranking
+// against the whole cell.  Only perm is meaningful afterwards (key64 may hold
+// keys in sorted or in original order, depending on the path).
+__device__ __forceinline__ void sort_segment(uint64_t* key64, int32_t* perm, int a, int n)
 {
     if (n <= 32) warp_bitonic_segment<1>(key64, perm, a, n);
     else if (n <= 64) warp_bitonic_segment<2>(key64, perm, a, n);
-    else if (n <= 128) warp_rank_chunk<4>(key64, perm, a, n, 0);
+    else if (n <= 256) warp_chunk_merge_segment(key64, perm, a, n);
     else
         for (int base = 0; base < n; base += 256) warp_rank_chunk<8>(key64, perm, a, n, base);
 }
 
-__device__ __forceinline__ void gather_out(const SortGatherArgs& g, int s, const uint32_t* src, const uint64_t* key64,
-                                           const int32_t* perm, int64_t o0, int R)
+__device__ __forceinline__ void gather_out(const SortGatherArgs& g, int s, const uint32_t* src, const int32_t* perm,
+                                           int64_t o0, int R)
 {
+    const uint32_t* __restrict__ iid = g.in_id[s];
     const float* __restrict__ iu0 = g.in_u[s][0];
     const float* __restrict__ iu1 = g.in_u[s][1];
     const float* __restrict__ iu2 = g.in_u[s][2];
@@ -434,11 +501,11 @@ __device__ __forceinline__ void gather_out(const SortGatherArgs& g, int s, const
         g.out_u[s][1][o0 + p] = iu1[sidx];
         g.out_u[s][2][o0 + p] = iu2[sidx];
         g.out_cell[s][o0 + p] = icell[sidx];
-        g.out_id[s][o0 + p] = (uint32_t)key64[i];
+        g.out_id[s][o0 + p] = iid[sidx];
     }
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_gather(SortGatherArgs g)
+__global__ void __launch_bounds__(kSortThreads, 2) k_sort_gather(SortGatherArgs g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t* key64 = reinterpret_cast<uint64_t*>(smem_raw);
@@ -477,7 +544,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_gather(SortGatherArgs g)
             if (n > 0) sort_segment(key64, perm, a, n);
         }
         __syncthreads();
-        gather_out(g, s, src, key64, perm, o0, (int)R);
+        gather_out(g, s, src, perm, o0, (int)R);
         return;
     }
 
@@ -500,7 +567,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_gather(SortGatherArgs g)
                 perm[rank] = i;
             }
             __syncthreads();
-            gather_out(g, s, src, key64, perm, o, (int)n);
+            gather_out(g, s, src, perm, o, (int)n);
             __syncthreads();
         } else {
             // Oversized cell: rank against the records in global memory.

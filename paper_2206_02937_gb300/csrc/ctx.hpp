@@ -64,6 +64,8 @@ struct MlpDev {
     float fs[4];         // feature scales s_u, n_u, s_k, n_k
 };
 
+struct ServeEngine;
+
 }  // namespace compton
 
 struct compton_ctx {
@@ -88,6 +90,8 @@ struct compton_ctx {
     bool mlp_loaded = false;
     int64_t adam_step = 0;
     void* train_scratch = nullptr;  // inside the arena, sized by cfg.max_train_batch
+    float* r_buf = nullptr;         // [max_particles] network output per pair (surrogate modes)
+    compton::ServeEngine* serve = nullptr;  // continuous-batching engine (compton_serve_start)
 };
 
 namespace compton {
@@ -131,7 +135,7 @@ compton_status launch_sample_angle(compton_ctx* ctx, const float* x, const uint3
 compton_status mlp_repack(compton_ctx* ctx, cudaStream_t stream);
 compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                 const float* kx, const float* ky, const float* kz, int64_t n, compton_mode mode,
-                                float* r_out, cudaStream_t stream);
+                                float* r_out, cudaStream_t stream, bool binned = false);
 size_t train_scratch_bytes(int64_t max_batch);
 compton_status launch_mlp_train_step(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                      const float* kx, const float* ky, const float* kz, const float* y,
@@ -139,5 +143,10 @@ compton_status launch_mlp_train_step(compton_ctx* ctx, const float* ux, const fl
 compton_status launch_mlp_calibrate(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                     const float* kx, const float* ky, const float* kz, int64_t n,
                                     cudaStream_t stream);
+compton_status serve_start(compton_ctx* ctx, uint64_t pool_bytes, int32_t max_active);
+compton_status serve_stop(compton_ctx* ctx);
+compton_status serve_submit(compton_ctx* ctx, const compton_request* r, uint64_t* ticket);
+compton_status serve_poll(compton_ctx* ctx, uint64_t ticket, compton_result* out);
+compton_status serve_info(compton_ctx* ctx, uint64_t* in_use, uint64_t* peak, uint64_t* pool);
 
 }  // namespace compton

@@ -54,7 +54,10 @@ __device__ __forceinline__ Philox4 draw(uint64_t seed, uint64_t step, uint32_t s
                          (uint32_t)(seed >> 32));
 }
 
-enum : uint32_t { kStreamPairE = 1u, kStreamPairG = 2u, kStreamScatter = 3u };
+// Streams: pairing keys of electrons (1) and photons (2) at the particle id;
+// the Bernoulli uniforms of pairs 4j..4j+3 as the four words of the stream-3
+// block at counter j; the two angle words of pair p from stream 4 at p.
+enum : uint32_t { kStreamPairE = 1u, kStreamPairG = 2u, kStreamScatter = 3u, kStreamAngle = 4u };
 
 // Uniform on [0, 1) from the top 24 bits of a word (exact in FP32).
 __device__ __forceinline__ float u24_closed0(uint32_t r) { return (float)(r >> 8) * 0x1.0p-24f; }
@@ -303,9 +306,13 @@ __device__ __forceinline__ Angle kn_sample_angle(float x, uint32_t r24, float F2
         if (R == 0.0f) break;
         if (R < 0.0f) lo = s; else hi = s;
         float sn = s - __fdividef(R, upper ? kn_f_upper(x, s) : kn_f_lower(x, s));
-        if (!(sn >= lo && sn <= hi)) sn = 0.5f * (lo + hi);
-        if (sn == s) break;
+        const bool newton = sn >= lo && sn <= hi;
+        if (!newton) sn = 0.5f * (lo + hi);
+        // a Newton step this small is at the FP32 resolution of s: the next
+        // one would only move s between neighbouring floats
+        const bool done = newton && fabsf(sn - s) <= 2.5e-7f * s;
         s = sn;
+        if (done) break;
     }
     Angle a;
     a.cth = upper ? s - 1.0f : 1.0f - s;

@@ -157,7 +157,34 @@ struct MlpArgs {
     int64_t n;
     float* r_out;
     DeviceStats* stats;
+    // binned input (pairs of a compton_bin_pairs list) when cinfo != nullptr
+    const CellInfo* cinfo;
+    const int32_t* tile_cell;
+    const int64_t* n_pairs;
 };
+
+// Electron and photon index of pair p of a binned pair list: the cell is
+// found by binary search between the cells of p's 1024-pair scatter tile.
+__device__ __forceinline__ void binned_pair(const MlpArgs& a, int64_t p, int& ie, int& ig)
+{
+    const int64_t t = p / kPairsPerTile;
+    int lo = a.tile_cell[t], hi = a.tile_cell[t + 1];
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int64_t)a.cinfo[mid].pair_off <= p) lo = mid; else hi = mid - 1;
+    }
+    const CellInfo ci = a.cinfo[lo];
+    const int j = (int)(p - ci.pair_off);
+    ie = ci.e_start + j;
+    ig = ci.g_start + j;
+}
+
+__device__ __forceinline__ void load_pair_features(const MlpArgs& a, int64_t row, float* f)
+{
+    int ie = (int)row, ig = (int)row;
+    if (a.cinfo) binned_pair(a, row, ie, ig);
+    features(a.m, a.u[0][ie], a.u[1][ie], a.u[2][ie], a.k[0][ig], a.k[1][ig], a.k[2][ig], f);
+}
 
 template <bool kFp8>
 __global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
@@ -204,12 +231,13 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
     const uint32_t sW = tc::smem_u32(Wt), sA0 = tc::smem_u32(A0), sA = tc::smem_u32(Ah);
     uint32_t phase = 0;
     bool failed = false;
-    const int64_t n_tiles = (a.n + kTileM - 1) / kTileM;
+    const int64_t n_rows = a.cinfo ? *a.n_pairs : a.n;
+    const int64_t n_tiles = (n_rows + kTileM - 1) / kTileM;
 
     for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
         const int64_t row = tile * kTileM + tid;
         float f[6] = {0, 0, 0, 0, 0, 0};
-        if (row < a.n) features(m, a.u[0][row], a.u[1][row], a.u[2][row], a.k[0][row], a.k[1][row], a.k[2][row], f);
+        if (row < n_rows) load_pair_features(a, row, f);
         if (kFp8) {
             const float s = scale[4];
             *reinterpret_cast<uint4*>(A0 + tc::sw128_offset(tid, 0)) =
@@ -294,7 +322,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
                 break;
             }
         }
-        if (!failed && row < a.n) a.r_out[row] = __fdividef(1.0f, 1.0f + __expf(-(acc_out + b4)));
+        if (!failed && row < n_rows) a.r_out[row] = __fdividef(1.0f, 1.0f + __expf(-(acc_out + b4)));
     }
     if (failed && tid == 0) atomicOr(&a.stats->error_flags, (unsigned long long)kErrTimeout);
     tc::fence_before_sync();
@@ -327,9 +355,10 @@ __global__ void __launch_bounds__(kF32Threads) k_mlp_fp32(MlpArgs a)
     const float b4 = m.b4[0];
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * kF32Threads;
-    for (int64_t row = (int64_t)blockIdx.x * kF32Threads + tid; row < a.n; row += stride) {
+    const int64_t n_rows = a.cinfo ? *a.n_pairs : a.n;
+    for (int64_t row = (int64_t)blockIdx.x * kF32Threads + tid; row < n_rows; row += stride) {
         float f[6];
-        features(m, a.u[0][row], a.u[1][row], a.u[2][row], a.k[0][row], a.k[1][row], a.k[2][row], f);
+        load_pair_features(a, row, f);
         float amax[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
@@ -412,7 +441,7 @@ compton_status mlp_repack(compton_ctx* ctx, cudaStream_t stream)
 
 compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                 const float* kx, const float* ky, const float* kz, int64_t n, compton_mode mode,
-                                float* r_out, cudaStream_t stream)
+                                float* r_out, cudaStream_t stream, bool binned)
 {
     MlpArgs a;
     a.m = ctx->mlp;
@@ -425,6 +454,9 @@ compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* 
     a.n = n;
     a.r_out = r_out;
     a.stats = ctx->stats;
+    a.cinfo = binned ? ctx->cinfo : nullptr;
+    a.tile_cell = binned ? ctx->tile_cell : nullptr;
+    a.n_pairs = binned ? ctx->n_pairs : nullptr;
     if (mode == COMPTON_MODE_MLP_FP32) {
         const int smem = (4 * 4096 + 64 * kF32Threads + 256 + 64) * 4;
         COMPTON_CUDA_TRY(ctx, cudaFuncSetAttribute(k_mlp_fp32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -448,6 +480,7 @@ compton_status launch_mlp_calibrate(compton_ctx* ctx, const float* ux, const flo
                                     const float* kx, const float* ky, const float* kz, int64_t n,
                                     cudaStream_t stream)
 {
+    const bool binned = false;
     MlpArgs a;
     a.m = ctx->mlp;
     a.u[0] = ux;
@@ -459,6 +492,9 @@ compton_status launch_mlp_calibrate(compton_ctx* ctx, const float* ux, const flo
     a.n = n;
     a.r_out = nullptr;
     a.stats = ctx->stats;
+    a.cinfo = binned ? ctx->cinfo : nullptr;
+    a.tile_cell = binned ? ctx->tile_cell : nullptr;
+    a.n_pairs = binned ? ctx->n_pairs : nullptr;
     const int smem = (4 * 4096 + 64 * kF32Threads + 256 + 64) * 4;
     COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->mlp.amax, 0, 4 * sizeof(float), stream));
     COMPTON_CUDA_TRY(ctx, cudaFuncSetAttribute(k_mlp_fp32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

@@ -44,12 +44,14 @@ struct ScatterArgs {
     float* prob_out;
     uint8_t* flag_out;
     DeviceStats* stats;
+    const float* r_mlp;  // network output per pair (surrogate modes)
 };
 
 struct QEntry {
     int32_t ie, ig;
     float x, F2;
-    uint32_t r1, r2;  // raw Philox words for the polar and azimuthal draws
+    uint32_t p;  // pair index: counter of its angle draws
+    uint32_t pad;
 };
 
 __device__ __forceinline__ int find_cell(const CellInfo* win, int nwin, int64_t p)
@@ -66,11 +68,20 @@ __device__ __forceinline__ void resolve(const ScatterArgs& a, const QEntry& e)
 {
     float ux = a.u[0][e.ie], uy = a.u[1][e.ie], uz = a.u[2][e.ie];
     float kx = a.k[0][e.ig], ky = a.k[1][e.ig], kz = a.k[2][e.ig];
-    const Angle ang = kn_sample_angle(e.x, e.r1 >> 8, e.F2);
+    float x = e.x, F2 = e.F2;
+    if (x < 0.0f) {  // probability came from the network: the collision needs x and F(x, 2)
+        const Invariants inv = invariants_f32(ux, uy, uz, kx, ky, kz);
+        float v = inv.v;
+        x = inv.x;
+        if (inv.gamma > a.gamma64) invariants_f64(ux, uy, uz, kx, ky, kz, &x, &v);
+        F2 = kn_F2(x);
+    }
+    const Philox4 rnd = draw(a.seed, a.step, kStreamAngle, e.p);
+    const Angle ang = kn_sample_angle(x, rnd.r0 >> 8, F2);
     // FP64 where FP32 cancellation would exceed the tolerance (gamma eps large)
     const float ge2 = fmaf(ux, ux, fmaf(uy, uy, fmaf(uz, uz, 1.0f))) * fmaf(kx, kx, fmaf(ky, ky, kz * kz));
-    if (ge2 > a.collide64_sq) collide_f64(ux, uy, uz, kx, ky, kz, e.x, ang, u24_closed0(e.r2));
-    else collide_f32(ux, uy, uz, kx, ky, kz, e.x, ang, u24_closed0(e.r2));
+    if (ge2 > a.collide64_sq) collide_f64(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(rnd.r1));
+    else collide_f32(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(rnd.r1));
     a.u[0][e.ie] = ux;
     a.u[1][e.ie] = uy;
     a.u[2][e.ie] = uz;
@@ -79,13 +90,17 @@ __device__ __forceinline__ void resolve(const ScatterArgs& a, const QEntry& e)
     a.k[2][e.ig] = kz;
 }
 
-template <bool kBinned>
+// kMlp: the probability of in-range pairs is P = 1 - exp(-2 n dt r) with r
+// from the surrogate network (a.r_mlp, one value per pair); pairs outside the
+// network's training range (gamma > 1e3, eps outside [1e-4, 1]) use the
+// analytic probability and are counted as fallbacks.
+template <bool kBinned, bool kMlp>
 __global__ void __launch_bounds__(kScatterThreads, 3) k_scatter(ScatterArgs a)
 {
     __shared__ CellInfo win[kCellWindow];
     __shared__ QEntry queue[kQueueCap];
     __shared__ int qn;
-    __shared__ unsigned red_pairs, red_scat;
+    __shared__ unsigned red_pairs, red_scat, red_fb;
 
     const int tid = threadIdx.x;
     const int64_t total = kBinned ? *a.n_pairs : a.n_explicit;
@@ -94,8 +109,9 @@ __global__ void __launch_bounds__(kScatterThreads, 3) k_scatter(ScatterArgs a)
         qn = 0;
         red_pairs = 0;
         red_scat = 0;
+        red_fb = 0;
     }
-    unsigned my_pairs = 0, my_scat = 0;
+    unsigned my_pairs = 0, my_scat = 0, my_fb = 0;
 
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t p0 = tile * kPairsPerTile;
@@ -158,25 +174,42 @@ __global__ void __launch_bounds__(kScatterThreads, 3) k_scatter(ScatterArgs a)
                 ux[r] = uy[r] = uz[r] = kx[r] = ky[r] = kz[r] = 0.0f;
             }
         }
+        // the Bernoulli uniforms of the thread's four pairs: one Philox block
+        const Philox4 rnd4 = draw(a.seed, a.step, kStreamScatter, (uint32_t)(pb >> 2));
+        const uint32_t words[4] = {rnd4.r0, rnd4.r1, rnd4.r2, rnd4.r3};
 #pragma unroll
         for (int r = 0; r < kPairsPerThread; ++r) {
             if (!valid[r]) continue;
             const int64_t p = pb + r;
-            const Invariants inv = invariants_f32(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r]);
-            float x = inv.x, v = inv.v;
-            if (inv.gamma > a.gamma64) invariants_f64(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r], &x, &v);
-            const float F2 = kn_F2(x);
-            const float sig = 0.375f * F2;
-            const float P = inv.eps > 0.0f ? one_minus_exp_neg(dens[r] * a.dt * sig * v) : 0.0f;
-            const Philox4 rnd = draw(a.seed, a.step, kStreamScatter, (uint32_t)p);
-            const bool hit = u24_closed0(rnd.r0) < P;
+            float x = -1.0f, F2 = 0.0f, P;
+            bool analytic = true;
+            if (kMlp) {
+                const float g2 = fmaf(ux[r], ux[r], fmaf(uy[r], uy[r], fmaf(uz[r], uz[r], 1.0f)));
+                const float e2 = fmaf(kx[r], kx[r], fmaf(ky[r], ky[r], kz[r] * kz[r]));
+                if (g2 <= 1.0e6f && e2 >= 1.0e-8f && e2 <= 1.0f) {
+                    analytic = false;
+                    P = one_minus_exp_neg(2.0f * dens[r] * a.dt * a.r_mlp[p]);
+                } else {
+                    ++my_fb;
+                }
+            }
+            if (analytic) {
+                const Invariants inv = invariants_f32(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r]);
+                float v = inv.v;
+                x = inv.x;
+                if (inv.gamma > a.gamma64) invariants_f64(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r], &x, &v);
+                F2 = kn_F2(x);
+                const float sig = 0.375f * F2;
+                P = inv.eps > 0.0f ? one_minus_exp_neg(dens[r] * a.dt * sig * v) : 0.0f;
+            }
+            const bool hit = u24_closed0(words[r]) < P;
             if (a.prob_out) a.prob_out[p] = P;
             if (a.flag_out) a.flag_out[p] = hit ? 1 : 0;
             ++my_pairs;
             if (hit) {
                 ++my_scat;
                 const int slot = atomicAdd(&qn, 1);
-                queue[slot] = QEntry{ie[r], ig[r], x, F2, rnd.r1, rnd.r2};
+                queue[slot] = QEntry{ie[r], ig[r], x, F2, (uint32_t)p, 0u};
             }
         }
         __syncthreads();
@@ -198,15 +231,18 @@ __global__ void __launch_bounds__(kScatterThreads, 3) k_scatter(ScatterArgs a)
     for (int d = 16; d > 0; d >>= 1) {
         my_pairs += __shfl_xor_sync(0xffffffffu, my_pairs, d);
         my_scat += __shfl_xor_sync(0xffffffffu, my_scat, d);
+        my_fb += __shfl_xor_sync(0xffffffffu, my_fb, d);
     }
     if ((tid & 31) == 0) {
         atomicAdd(&red_pairs, my_pairs);
         atomicAdd(&red_scat, my_scat);
+        atomicAdd(&red_fb, my_fb);
     }
     __syncthreads();
     if (tid == 0 && red_pairs) {
         atomicAdd(&a.stats->pairs_tested, (unsigned long long)red_pairs);
         atomicAdd(&a.stats->scatters, (unsigned long long)red_scat);
+        if (red_fb) atomicAdd(&a.stats->mlp_fallbacks, (unsigned long long)red_fb);
     }
 }
 
@@ -231,14 +267,14 @@ __global__ void k_sample_angle(const float* __restrict__ x, const uint32_t* __re
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float xi = x[i];
-        const Angle ang = kn_sample_angle(xi, r[i] >> 8, kn_F2(xi));
+        const Angle ang = kn_sample_angle(xi, r[i] >> 8, kn_F2(xi));  // r: a raw angle word
         cth[i] = ang.cth;
         sth[i] = ang.sth;
         ratio[i] = ang.ratio;
     }
 }
 
-template <bool kBinned>
+template <bool kBinned, bool kMlp>
 int persistent_grid(int64_t max_pairs)
 {
     static int per_sm = 0, n_sm = 0;
@@ -246,7 +282,7 @@ int persistent_grid(int64_t max_pairs)
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<kBinned>, kScatterThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<kBinned, kMlp>, kScatterThreads, 0);
         if (per_sm < 1) per_sm = 1;
     }
     const int64_t tiles = (max_pairs + kPairsPerTile - 1) / kPairsPerTile;
@@ -260,8 +296,13 @@ compton_status launch_scatter_binned(compton_ctx* ctx, compton_species* e, compt
                                      const compton_pairs* pairs, compton_mode mode, uint64_t step,
                                      float* prob_out, uint8_t* flag_out, cudaStream_t stream)
 {
-    (void)mode;
     if (pairs->max_pairs <= 0) return COMPTON_OK;
+    const bool mlp = mode != COMPTON_MODE_PLAIN;
+    if (mlp) {
+        compton_status st = launch_mlp_infer(ctx, e->ux_dev, e->uy_dev, e->uz_dev, g->ux_dev, g->uy_dev, g->uz_dev,
+                                             pairs->max_pairs, mode, ctx->r_buf, stream, true);
+        if (st != COMPTON_OK) return st;
+    }
     ScatterArgs a;
     a.u[0] = e->ux_dev;
     a.u[1] = e->uy_dev;
@@ -282,7 +323,9 @@ compton_status launch_scatter_binned(compton_ctx* ctx, compton_species* e, compt
     a.prob_out = prob_out;
     a.flag_out = flag_out;
     a.stats = ctx->stats;
-    k_scatter<true><<<persistent_grid<true>(pairs->max_pairs), kScatterThreads, 0, stream>>>(a);
+    a.r_mlp = ctx->r_buf;
+    if (mlp) k_scatter<true, true><<<persistent_grid<true, true>(pairs->max_pairs), kScatterThreads, 0, stream>>>(a);
+    else k_scatter<true, false><<<persistent_grid<true, false>(pairs->max_pairs), kScatterThreads, 0, stream>>>(a);
     COMPTON_LAUNCH_CHECK(ctx, "k_scatter<binned>");
     return COMPTON_OK;
 }
@@ -291,7 +334,12 @@ compton_status launch_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, floa
                                     float* kz, const float* n_dens, int64_t n, uint64_t seed, uint64_t step,
                                     compton_mode mode, float* prob_out, uint8_t* flag_out, cudaStream_t stream)
 {
-    (void)mode;
+    const bool mlp = mode != COMPTON_MODE_PLAIN;
+    if (mlp) {
+        if (n > ctx->cfg.max_particles) return COMPTON_ERANGE;
+        compton_status st = launch_mlp_infer(ctx, ux, uy, uz, kx, ky, kz, n, mode, ctx->r_buf, stream, false);
+        if (st != COMPTON_OK) return st;
+    }
     ScatterArgs a;
     a.u[0] = ux;
     a.u[1] = uy;
@@ -312,7 +360,9 @@ compton_status launch_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, floa
     a.prob_out = prob_out;
     a.flag_out = flag_out;
     a.stats = ctx->stats;
-    k_scatter<false><<<persistent_grid<false>(n), kScatterThreads, 0, stream>>>(a);
+    a.r_mlp = ctx->r_buf;
+    if (mlp) k_scatter<false, true><<<persistent_grid<false, true>(n), kScatterThreads, 0, stream>>>(a);
+    else k_scatter<false, false><<<persistent_grid<false, false>(n), kScatterThreads, 0, stream>>>(a);
     COMPTON_LAUNCH_CHECK(ctx, "k_scatter<pairs>");
     return COMPTON_OK;
 }
