@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=300)
-    ap.add_argument("--train-steps", type=int, default=600)
+    ap.add_argument("--train-steps", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -223,15 +223,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     frac_scat = stats["scatters"] / max(1, pairs)
     pairs_per_step = pairs / args.steps
 
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        p = torch.tensor([float(pairs)], device=dev, dtype=torch.float64)
-        dist.all_reduce(p)
-        pairs_all = float(p.item())
-    else:
-        pairs_all = float(pairs)
+    from paper_2206_02937_gb300.dist import reduce_timing
+    total_ms, pairs_all = reduce_timing(total_ms, pairs, dev)
     value = pairs_all / (total_ms * 1e-3)
 
     # roofline of the scatter kernel (one launch per compton_scatter_step)
@@ -298,10 +291,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         dist.destroy_process_group()
 
 
-def train_surrogate(cg, torch, ctx, dev, n_samples=262144, steps=600, batch=8192, lr=1e-3):
+def train_surrogate(cg, torch, ctx, dev, n_samples=1 << 20, steps=2000, batch=8192, lr=1e-3):
     """Train the network on the GPU on analytic targets over the surrogate's
-    range (gamma log-uniform on [1, 1e3], eps log-uniform on [1e-4, 1]);
-    weights Glorot-uniform, seed 0.  Not timed."""
+    range (gamma log-uniform on [1, 1e3], eps log-uniform on [1e-4, 1]),
+    with the data-balancing weights of the paper (32 log bins of r on
+    [1e-6, 1]); weights Glorot-uniform, seed 0.  Not timed."""
     from paper_2206_02937_gb300 import workloads as wl
     rng = np.random.default_rng(0)
     theta = np.zeros(12993, dtype=np.float32)
@@ -315,18 +309,22 @@ def train_surrogate(cg, torch, ctx, dev, n_samples=262144, steps=600, batch=8192
     ut, kt = torch.from_numpy(u).to(dev), torch.from_numpy(k).to(dev)
     r = torch.zeros(n_samples, device=dev)
     cg.compton_kn_ratio(ctx, ut, kt, r)
+    wts = torch.zeros(n_samples, device=dev)
+    edges = (1e-6 * (1e6) ** (np.arange(33) / 32)).astype(np.float32)
+    cg.compton_mlp_balance_weights(ctx, r, edges, wts)
     gen = torch.Generator(device=dev).manual_seed(0)
     losses = []
     for it in range(steps):
         idx = torch.randint(0, n_samples, (batch,), device=dev, generator=gen)
         loss = cg.compton_mlp_train_step(ctx, ut[:, idx].contiguous(), kt[:, idx].contiguous(),
-                                         r[idx].contiguous(), None, lr, want_loss=(it % 100 == 0 or it == steps - 1))
+                                         r[idx].contiguous(), wts[idx].contiguous(), lr,
+                                         want_loss=(it % 100 == 0 or it == steps - 1))
         if loss is not None:
             losses.append(loss)
     cg.compton_mlp_calibrate(ctx, ut[:, :65536].contiguous(), kt[:, :65536].contiguous())
     torch.cuda.synchronize()
-    return {"steps": steps, "batch": batch, "lr": lr, "samples": n_samples, "loss_first": losses[0],
-            "loss_last": losses[-1]}
+    return {"steps": steps, "batch": batch, "lr": lr, "samples": n_samples, "balanced": "32 log bins of r",
+            "loss_first": losses[0], "loss_last": losses[-1]}
 
 
 def run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step0, peaks):

@@ -253,6 +253,17 @@ compton_status compton_mlp_train_step(struct compton_ctx* ctx, const float* ux_d
                                       const float* kz_dev, const float* y_dev, const float* w_dev, int64_t n,
                                       float lr, float* loss_out_host, compton_stream_t stream);
 
+/* Data-balancing weights (Sec. 3.2: events of every probability range
+ * should appear about equally often in training).  Sample i falls in bin
+ * b = number of edges_host[1 .. n_bins-1] that are <= r_dev[i] (values beyond
+ * the outer edges go to the outer bins); w_out_dev[i] = n / (count_b *
+ * number of non-empty bins), so the weights average to 1 and each non-empty
+ * bin carries equal total weight.  edges_host: n_bins + 1 strictly
+ * increasing floats (host), 1 <= n_bins <= 256. */
+compton_status compton_mlp_balance_weights(struct compton_ctx* ctx, const float* r_dev, int64_t n,
+                                           const float* edges_host, int32_t n_bins, float* w_out_dev,
+                                           compton_stream_t stream);
+
 /* The gradient dL/dtheta of the last compton_mlp_train_step (the loss
  * normalised by sum w), same layout as the parameters.  Synchronous. */
 compton_status compton_mlp_get_grad(struct compton_ctx* ctx, float* grad_host, int64_t n_params);
@@ -332,6 +343,16 @@ compton_status compton_poll(struct compton_ctx* ctx, uint64_t ticket, compton_re
 /* Pool bytes in use now, the peak since start, and the pool size. */
 compton_status compton_serve_info(struct compton_ctx* ctx, uint64_t* bytes_in_use, uint64_t* peak_bytes,
                                   uint64_t* pool_bytes);
+
+
+/* Self-test of the give-up path of the bounded device waits (every wait of
+ * the tensor-core kernels is limited in time; on expiry the kernel records a
+ * timeout, frees its tensor memory and returns instead of hanging): one
+ * thread waits on a barrier that nothing completes, for timeout_ns
+ * (<= 10 s).  compton_check then returns ETIMEOUT.  The paper has no
+ * counterpart; this exists so the failure path can be tested without a
+ * fault. */
+compton_status compton_selftest_wait(struct compton_ctx* ctx, uint64_t timeout_ns, compton_stream_t stream);
 
 /* The scattering-angle sampler of compton_scatter_step on its own, for
  * validation (the paper resolves each collision by sampling the scattered

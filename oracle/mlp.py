@@ -152,13 +152,20 @@ class Adam:
         return theta - self.lr * mh / (np.sqrt(vh) + self.eps)
 
 
-def balance_weights(r: np.ndarray, n_bins: int = 32, lo: float = 1e-8, hi: float = 1.0) -> np.ndarray:
-    """Per-sample weights that make every probability decade range count
-    equally (the data balancing of Sec. 3.2): histogram log10 r in n_bins
-    equal bins on [lo, hi], weight 1/count of the sample's bin, normalised
-    to mean 1."""
-    x = np.clip(np.log10(np.maximum(r, lo)), np.log10(lo), np.log10(hi))
-    b = np.minimum(((x - np.log10(lo)) / (np.log10(hi) - np.log10(lo)) * n_bins).astype(np.int64), n_bins - 1)
+def balance_edges(n_bins: int = 32, lo: float = 1e-8, hi: float = 1.0) -> np.ndarray:
+    """n_bins + 1 bin edges equally spaced in log r on [lo, hi], as float32."""
+    return (lo * (hi / lo) ** (np.arange(n_bins + 1) / n_bins)).astype(np.float32)
+
+
+def balance_weights(r: np.ndarray, edges: np.ndarray) -> np.ndarray:
+    """Per-sample weights that make every probability range count equally
+    (the data balancing of Sec. 3.2).  Sample i falls in bin b = (number of
+    edges[1:-1] <= r_i) (values beyond the outer edges go to the outer bins);
+    weight n / (count_b * number of non-empty bins), so the weights average
+    to 1 and every non-empty bin carries the same total weight."""
+    r32 = np.asarray(r, dtype=np.float32)
+    inner = np.asarray(edges, dtype=np.float32)[1:-1]
+    b = np.searchsorted(inner, r32, side="right")
+    n_bins = inner.shape[0] + 1
     cnt = np.bincount(b, minlength=n_bins).astype(np.float64)
-    wt = 1.0 / cnt[b]
-    return wt * (wt.shape[0] / wt.sum())
+    return r32.shape[0] / (cnt[b] * np.count_nonzero(cnt))

@@ -342,3 +342,22 @@ def compton_serve_info(ctx: int) -> dict:
     _check(lib().compton_serve_info(c_p(ctx), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
            "compton_serve_info", ctx)
     return dict(in_use=a.value, peak=b.value, pool=c.value)
+
+
+SIGNATURES["compton_mlp_balance_weights"] = (c_i32, [c_p, c_p, c_i64, c_p, c_i32, c_p, c_p])
+
+
+def compton_mlp_balance_weights(ctx: int, r, edges, w_out, stream=None) -> None:
+    """r: float32 CUDA tensor; edges: n_bins + 1 increasing host floats."""
+    import numpy as np
+    e = np.ascontiguousarray(edges, dtype=np.float32)
+    _check(lib().compton_mlp_balance_weights(c_p(ctx), _ptr(r), int(r.shape[0]), c_p(e.ctypes.data),
+                                             int(e.shape[0] - 1), _ptr(w_out), _stream_ptr(stream)),
+           "compton_mlp_balance_weights", ctx)
+
+
+SIGNATURES["compton_selftest_wait"] = (c_i32, [c_p, c_u64, c_p])
+
+
+def compton_selftest_wait(ctx: int, timeout_ns: int, stream=None) -> None:
+    _check(lib().compton_selftest_wait(c_p(ctx), int(timeout_ns), _stream_ptr(stream)), "compton_selftest_wait", ctx)

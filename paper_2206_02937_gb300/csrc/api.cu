@@ -114,7 +114,7 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     size_t o_wb = cv.take<uint8_t>(4 * 8192), o_w8 = cv.take<uint8_t>(4 * 8192), o_wt = cv.take<float>(4 * 4096);
     size_t o_bi = cv.take<float>(256), o_w4 = cv.take<float>(64), o_b4 = cv.take<float>(1);
     size_t o_sw = cv.take<float>(4), o_swi = cv.take<float>(4), o_sai = cv.take<float>(4), o_lo = cv.take<float>(2),
-           o_ax = cv.take<float>(4);
+           o_ax = cv.take<float>(4), o_ed = cv.take<float>(257), o_hi = cv.take<int>(256);
     if (cfg->max_train_batch < 0 || cfg->max_train_batch > (int64_t)1 << 31) {
         delete ctx;
         return COMPTON_EINVAL;
@@ -161,6 +161,8 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     m.scale_a_inv = reinterpret_cast<float*>(base + o_sai);
     m.loss = reinterpret_cast<float*>(base + o_lo);
     m.amax = reinterpret_cast<float*>(base + o_ax);
+    m.edges = reinterpret_cast<float*>(base + o_ed);
+    m.hist = reinterpret_cast<int*>(base + o_hi);
     ctx->train_scratch = base + o_tr;
     ctx->r_buf = reinterpret_cast<float*>(base + o_rb);
     m.fs[0] = 1.0f;   // s_u
@@ -197,7 +199,7 @@ compton_status compton_check(compton_ctx* ctx, compton_stream_t stream)
     COMPTON_CUDA_TRY(ctx, cudaMemcpy(&flags, &ctx->stats->error_flags, sizeof(flags), cudaMemcpyDeviceToHost));
     if (flags) {
         COMPTON_CUDA_TRY(ctx, cudaMemset(&ctx->stats->error_flags, 0, sizeof(flags)));
-        return COMPTON_ERANGE;
+        return (flags & compton::kErrTimeout) ? COMPTON_ETIMEOUT : COMPTON_ERANGE;
     }
     return COMPTON_OK;
 }
@@ -350,6 +352,15 @@ compton_status compton_mlp_train_step(compton_ctx* ctx, const float* ux, const f
     return COMPTON_OK;
 }
 
+compton_status compton_mlp_balance_weights(compton_ctx* ctx, const float* r, int64_t n, const float* edges,
+                                           int32_t n_bins, float* w_out, compton_stream_t stream)
+{
+    if (!ctx || !r || !edges || !w_out || n <= 0 || n_bins < 1 || n_bins > 256) return COMPTON_EINVAL;
+    for (int i = 0; i < n_bins; ++i)
+        if (!(edges[i] < edges[i + 1])) return COMPTON_EINVAL;
+    return compton::launch_balance_weights(ctx, r, n, edges, n_bins, w_out, stream);
+}
+
 compton_status compton_mlp_get_grad(compton_ctx* ctx, float* grad, int64_t n_params)
 {
     if (!ctx || !grad || n_params != compton::kMlpParams) return COMPTON_EINVAL;
@@ -468,6 +479,12 @@ compton_status compton_serve_info(compton_ctx* ctx, uint64_t* bytes_in_use, uint
 {
     if (!ctx || !bytes_in_use || !peak_bytes || !pool_bytes) return COMPTON_EINVAL;
     return compton::serve_info(ctx, bytes_in_use, peak_bytes, pool_bytes);
+}
+
+compton_status compton_selftest_wait(compton_ctx* ctx, uint64_t timeout_ns, compton_stream_t stream)
+{
+    if (!ctx || timeout_ns == 0 || timeout_ns > 10000000000ull) return COMPTON_EINVAL;
+    return compton::launch_selftest_wait(ctx, timeout_ns, stream);
 }
 
 compton_status compton_kn_sample_angle(compton_ctx* ctx, const float* x, const uint32_t* r, int64_t n,

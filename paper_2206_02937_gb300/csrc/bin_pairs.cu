@@ -419,7 +419,7 @@ __device__ __forceinline__ int count_below(const uint64_t* key64, int b, int m, 
 {
     int pos = 0;
 #pragma unroll
-    for (int step = 32; step > 0; step >>= 1) {
+    for (int step = 64; step > 0; step >>= 1) {  // m <= 64: all of a full chunk can count
         if (pos + step <= m) {
             const uint64_t v = key64[b + pos + step - 1];
             if (v < k || (or_equal && v == k)) pos += step;

@@ -61,6 +61,8 @@ struct MlpDev {
     float* scale_a_inv;  // 4: 1 / FP8 activation scale of each layer input
     float* loss;         // [2] weighted |error| sum and weight sum of the last step
     float* amax;         // [4] calibration: max |input| of each hidden layer
+    float* edges;        // [257] data-balancing bin edges
+    int* hist;           // [256] data-balancing counts
     float fs[4];         // feature scales s_u, n_u, s_k, n_k
 };
 
@@ -137,12 +139,15 @@ compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* 
                                 const float* kx, const float* ky, const float* kz, int64_t n, compton_mode mode,
                                 float* r_out, cudaStream_t stream, bool binned = false);
 size_t train_scratch_bytes(int64_t max_batch);
+compton_status launch_balance_weights(compton_ctx* ctx, const float* r, int64_t n, const float* edges_host,
+                                      int n_bins, float* w_out, cudaStream_t stream);
 compton_status launch_mlp_train_step(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                      const float* kx, const float* ky, const float* kz, const float* y,
                                      const float* w, int64_t n, float lr, cudaStream_t stream);
 compton_status launch_mlp_calibrate(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                     const float* kx, const float* ky, const float* kz, int64_t n,
                                     cudaStream_t stream);
+compton_status launch_selftest_wait(compton_ctx* ctx, uint64_t timeout_ns, cudaStream_t stream);
 compton_status serve_start(compton_ctx* ctx, uint64_t pool_bytes, int32_t max_active);
 compton_status serve_stop(compton_ctx* ctx);
 compton_status serve_submit(compton_ctx* ctx, const compton_request* r, uint64_t* ticket);

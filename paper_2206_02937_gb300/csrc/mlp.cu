@@ -476,6 +476,27 @@ compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* 
     return COMPTON_OK;
 }
 
+namespace {
+// The bounded mbarrier wait of the tensor-core kernels, on a barrier that no
+// one arrives at: it must give up after timeout_ns and record the timeout.
+__global__ void k_selftest_wait(uint64_t timeout_ns, DeviceStats* stats)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::fence_barrier_init();
+        if (!tc::mbar_wait(&bar, 0, timeout_ns)) atomicOr(&stats->error_flags, (unsigned long long)kErrTimeout);
+    }
+}
+}  // namespace
+
+compton_status launch_selftest_wait(compton_ctx* ctx, uint64_t timeout_ns, cudaStream_t stream)
+{
+    k_selftest_wait<<<1, 32, 0, stream>>>(timeout_ns, ctx->stats);
+    COMPTON_LAUNCH_CHECK(ctx, "k_selftest_wait");
+    return COMPTON_OK;
+}
+
 compton_status launch_mlp_calibrate(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                     const float* kx, const float* ky, const float* kz, int64_t n,
                                     cudaStream_t stream)

@@ -230,7 +230,76 @@ __global__ void k_train_adam(MlpDev m, float lr, float b1, float b2, float eps, 
     m.theta[i] -= lr * mh / (sqrtf(vh) + eps);
 }
 
+// Data balancing (Sec. 3.2: events of every probability range should appear
+// about equally often).  Sample i belongs to bin b = number of inner edges
+// <= r_i; its weight is n / (count_b * number of non-empty bins).
+constexpr int kMaxBalanceBins = 256;
+
+__device__ __forceinline__ int balance_bin(const float* inner, int n_inner, float r)
+{
+    int lo = 0, hi = n_inner;  // first inner edge > r
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (inner[mid] <= r) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_balance_hist(const float* __restrict__ r, int64_t n, const float* __restrict__ edges, int n_bins,
+                               int* __restrict__ count)
+{
+    __shared__ float inner[kMaxBalanceBins];
+    __shared__ int h[kMaxBalanceBins];
+    for (int i = threadIdx.x; i < n_bins; i += blockDim.x) {
+        h[i] = 0;
+        if (i < n_bins - 1) inner[i] = edges[i + 1];
+    }
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[balance_bin(inner, n_bins - 1, r[i])], 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_bins; i += blockDim.x)
+        if (h[i]) atomicAdd(&count[i], h[i]);
+}
+
+__global__ void k_balance_weights(const float* __restrict__ r, int64_t n, const float* __restrict__ edges,
+                                  int n_bins, const int* __restrict__ count, float* __restrict__ w)
+{
+    __shared__ float inner[kMaxBalanceBins];
+    __shared__ float inv[kMaxBalanceBins];
+    __shared__ int nonempty;
+    if (threadIdx.x == 0) {
+        int ne = 0;
+        for (int i = 0; i < n_bins; ++i) ne += count[i] > 0;
+        nonempty = ne;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_bins; i += blockDim.x) {
+        if (i < n_bins - 1) inner[i] = edges[i + 1];
+        inv[i] = count[i] > 0 ? (float)((double)n / ((double)count[i] * (double)nonempty)) : 0.0f;
+    }
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] = inv[balance_bin(inner, n_bins - 1, r[i])];
+}
+
 }  // namespace
+
+compton_status launch_balance_weights(compton_ctx* ctx, const float* r, int64_t n, const float* edges_host,
+                                      int n_bins, float* w_out, cudaStream_t stream)
+{
+    if (n_bins < 1 || n_bins > kMaxBalanceBins) return COMPTON_EINVAL;
+    COMPTON_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->mlp.edges, edges_host, sizeof(float) * (n_bins + 1),
+                                          cudaMemcpyHostToDevice, stream));
+    COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->mlp.hist, 0, sizeof(int) * n_bins, stream));
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_balance_hist<<<(unsigned)blocks, 256, 0, stream>>>(r, n, ctx->mlp.edges, n_bins, ctx->mlp.hist);
+    COMPTON_LAUNCH_CHECK(ctx, "k_balance_hist");
+    k_balance_weights<<<(unsigned)blocks, 256, 0, stream>>>(r, n, ctx->mlp.edges, n_bins, ctx->mlp.hist, w_out);
+    COMPTON_LAUNCH_CHECK(ctx, "k_balance_weights");
+    return COMPTON_OK;
+}
 
 size_t train_scratch_bytes(int64_t max_batch)
 {

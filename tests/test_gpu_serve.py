@@ -107,7 +107,7 @@ def test_budget_admission_and_errors():
             torch.cuda.synchronize()
             assert torch.equal(uo, ud) and torch.equal(ko, kd)
         # a request that can never fit
-        big_u, big_k = torch.zeros((3, 200000), device="cuda"), torch.zeros((3, 200000), device="cuda")
+        big_u, big_k = torch.zeros((3, 400000), device="cuda"), torch.zeros((3, 400000), device="cuda")
         with pytest.raises(cg.ComptonError) as e:
             cg.compton_submit(ctx, big_u, big_k, big_u, big_k, 1.0, 1)
         assert e.value.status == cg.COMPTON_ERANGE

@@ -120,10 +120,15 @@ def test_adam_matches_torch_and_first_step_closed_form():
 
 def test_balance_weights_equalise_bins():
     rng = np.random.default_rng(6)
-    r = 10 ** rng.uniform(-6, 0, 100000) ** 2  # skewed toward small r
-    w = mlp.balance_weights(r, n_bins=12, lo=1e-12, hi=1.0)
-    b = np.minimum(((np.log10(r) + 12) / 12 * 12).astype(int), 11)
-    per_bin = np.bincount(b, weights=w, minlength=12)
+    r = 10 ** (-12 * rng.uniform(0, 1, 100000) ** 2)  # skewed toward large r
+    edges = mlp.balance_edges(12, 1e-12, 1.0)
+    assert np.allclose(np.log10(edges.astype(np.float64)), np.linspace(-12, 0, 13), atol=1e-6)
+    w = mlp.balance_weights(r, edges)
+    # brute force: the bin of each sample by scanning the edges
+    b = np.array([sum(1 for e in edges[1:-1] if e <= np.float32(x)) for x in r[:2000]])
+    assert np.array_equal(b, np.searchsorted(edges[1:-1], r[:2000].astype(np.float32), side="right"))
+    full_b = np.searchsorted(edges[1:-1], r.astype(np.float32), side="right")
+    per_bin = np.bincount(full_b, weights=w, minlength=12)
     nz = per_bin[per_bin > 0]
     assert np.allclose(nz, nz[0])
     assert w.mean() == pytest.approx(1.0)
