@@ -344,6 +344,22 @@ compton_status compton_poll(struct compton_ctx* ctx, uint64_t ticket, compton_re
 compton_status compton_serve_info(struct compton_ctx* ctx, uint64_t* bytes_in_use, uint64_t* peak_bytes,
                                   uint64_t* pool_bytes);
 
+/* Per-cell offsets of one species with no device allocation at all (the
+ * paper has no counterpart: this serves callers that cannot allocate device
+ * memory when they need the offsets, such as a particle-in-cell code whose
+ * memory manager owns all device memory, or a time-step loop that must not
+ * allocate).  off_out_dev[c] = number of particles with a cell index below c
+ * (indices outside [0, n_cells) are not counted), off_out_dev[n_cells] = the
+ * number counted; the same values as compton_pairs.off_*_dev of
+ * compton_bin_pairs.  Needs no context.  The counts live in a library-owned
+ * static device array of 2^20 int32 (4 MiB, held on every GPU that loads the
+ * library until exit): n_cells above 1048576 is rejected with ERANGE.  The
+ * first call on a device looks up that array's device address, so make it
+ * before any stream capture.  Every call reuses the array and clears it
+ * first; calls whose work overlaps on the GPU race on it and must be ordered
+ * by the caller.  Asynchronous on `stream`. */
+compton_status compton_cell_offsets_noalloc(const int32_t* cell_dev, int64_t n, int64_t n_cells,
+                                            int32_t* off_out_dev, compton_stream_t stream);
 
 /* Self-test of the give-up path of the bounded device waits (every wait of
  * the tensor-core kernels is limited in time; on expiry the kernel records a

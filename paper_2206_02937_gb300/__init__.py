@@ -344,6 +344,16 @@ def compton_serve_info(ctx: int) -> dict:
     return dict(in_use=a.value, peak=b.value, pool=c.value)
 
 
+SIGNATURES["compton_cell_offsets_noalloc"] = (c_i32, [c_p, c_i64, c_i64, c_p, c_p])
+
+
+def compton_cell_offsets_noalloc(cell, n_cells: int, off_out, stream=None) -> None:
+    """Per-cell offsets of one species (cell: int32 CUDA tensor; off_out:
+    int32 CUDA tensor of n_cells + 1), with no device allocation."""
+    _check(lib().compton_cell_offsets_noalloc(_ptr(cell), int(cell.shape[0]), int(n_cells), _ptr(off_out),
+                                              _stream_ptr(stream)), "compton_cell_offsets_noalloc")
+
+
 SIGNATURES["compton_mlp_balance_weights"] = (c_i32, [c_p, c_p, c_i64, c_p, c_i32, c_p, c_p])
 
 
