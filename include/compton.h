@@ -25,7 +25,8 @@
  *     in a device word of the context; compton_check() synchronises the stream
  *     and reports them.
  *   - All library-owned device memory is allocated in compton_init, within
- *     compton_config.mem_budget_bytes; no entry point allocates afterwards.
+ *     compton_config.mem_budget_bytes, except the serving pool, allocated
+ *     once by compton_serve_start; no other entry point allocates.
  */
 #ifndef COMPTON_H
 #define COMPTON_H
@@ -117,7 +118,8 @@ typedef struct compton_stats {
 /* ---------------------------------------------------------------------- */
 
 /* Create a context on cfg->device: allocates the scratch for binning
- * (about 24 bytes per particle of capacity and 40 bytes per cell), the
+ * (about 68 bytes per particle of capacity: a 32-byte placement record per
+ * species and the 4-byte network output; and 40 bytes per cell), the
  * network buffers and the stats, all within cfg->mem_budget_bytes.
  * Synchronous.  EINVAL on bad sizes, ENOMEM if the budget or the device
  * cannot hold it. */

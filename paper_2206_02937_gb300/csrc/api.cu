@@ -100,9 +100,10 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     for (int s = 0; s < 2; ++s) {
         o_count[s] = cv.take<int32_t>(C);
         o_off[s] = cv.take<int32_t>(C + 1);
-        o_rec[s] = cv.take<uint2>(P > 0 ? P : 1);
+        o_rec[s] = cv.take<compton::SortRec>(P > 0 ? P : 1);
         o_stile[s] = cv.take<int32_t>(ctx->max_sort_tiles + 1);
     }
+    size_t o_uns = cv.take<int32_t>(2);
     size_t o_bs = cv.take<int64_t>(3 * ctx->max_scan_tiles);
     size_t o_ci = cv.take<CellInfo>(C);
     size_t o_tc = cv.take<int32_t>(ctx->max_pair_tiles + 1);
@@ -137,9 +138,10 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     for (int s = 0; s < 2; ++s) {
         ctx->count[s] = reinterpret_cast<int32_t*>(base + o_count[s]);
         ctx->off[s] = reinterpret_cast<int32_t*>(base + o_off[s]);
-        ctx->rec[s] = reinterpret_cast<uint2*>(base + o_rec[s]);
+        ctx->rec[s] = reinterpret_cast<compton::SortRec*>(base + o_rec[s]);
         ctx->stile[s] = reinterpret_cast<int32_t*>(base + o_stile[s]);
     }
+    ctx->unsorted = reinterpret_cast<int32_t*>(base + o_uns);
     ctx->block_sums = reinterpret_cast<int64_t*>(base + o_bs);
     ctx->cinfo = reinterpret_cast<CellInfo*>(base + o_ci);
     ctx->tile_cell = reinterpret_cast<int32_t*>(base + o_tc);

@@ -27,30 +27,66 @@ constexpr int kSortThreads = 512;
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // ---------------------------------------------------------------------------
-// Histogram.  A warp groups lanes with equal cells (__match_any_sync) and one
-// lane per group adds the group size: inputs already sorted by cell (every
-// step after the first) cost one atomic per run instead of one per particle.
+// Histogram and order check.  Each warp takes 128 consecutive particles (four
+// loads in flight per lane).  A group of 32 whose cells do not descend adds
+// one count per run of equal cells; any other group lets __match_any_sync
+// find the lanes with equal cells, and one lane per group adds the group
+// size.  unsorted[s] is set if a cell index descends or lies outside
+// [0, C): only then does the placement run.
 // ---------------------------------------------------------------------------
 __global__ void k_count(const int32_t* __restrict__ cell_e, int64_t n_e, const int32_t* __restrict__ cell_g,
                         int64_t n_g, int64_t C, int32_t* __restrict__ count_e, int32_t* __restrict__ count_g,
-                        DeviceStats* stats)
+                        int32_t* __restrict__ unsorted, DeviceStats* stats)
 {
     const int s = blockIdx.y;
-    const int32_t* cell = s == 0 ? cell_e : cell_g;
+    const int32_t* __restrict__ cell = s == 0 ? cell_e : cell_g;
     const int64_t n = s == 0 ? n_e : n_g;
-    int32_t* count = s == 0 ? count_e : count_g;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t n_round = (n + 31) / 32 * 32;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
-        int c = -1;
-        if (i < n) {
-            const int32_t ci = cell[i];
-            if (ci >= 0 && (int64_t)ci < C) c = ci;
-            else atomicOr(&stats->error_flags, (unsigned long long)kErrCellRange);
+    int32_t* __restrict__ count = s == 0 ? count_e : count_g;
+    const unsigned lane = lane_id();
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    bool disorder = false, bad = false;
+    for (int64_t base = warp * 128; base < n; base += n_warps * 128) {
+        int32_t v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = base + 32 * k + lane;
+            v[k] = i < n ? cell[i] : 0;
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, c);
-        if (c >= 0 && lane_id() == (unsigned)(__ffs(peers) - 1)) atomicAdd(&count[c], __popc(peers));
+        int32_t prev_last = 0;
+        if (lane == 0 && base > 0) prev_last = cell[base - 1];
+        prev_last = __shfl_sync(0xffffffffu, prev_last, 0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = base + 32 * k + lane;
+            const bool live = i < n;
+            const bool ok = live && v[k] >= 0 && (int64_t)v[k] < C;
+            bad |= live && !ok;
+            int32_t prev = __shfl_up_sync(0xffffffffu, v[k], 1);
+            if (lane == 0) prev = prev_last;
+            const bool desc = live && i > 0 && prev > v[k];
+            disorder |= desc;
+            prev_last = __shfl_sync(0xffffffffu, v[k], 31);
+            const int c = ok ? v[k] : -1;
+            if (__all_sync(0xffffffffu, !desc && (ok || !live))) {
+                // ordered group: runs of equal cells are runs of lanes
+                const unsigned head = __ballot_sync(0xffffffffu, ok && (lane == 0 || prev != v[k]));
+                if (ok && ((head >> lane) & 1u)) {
+                    const unsigned later = head & ~((2u << lane) - 1u);
+                    const int end = later ? __ffs(later) - 1 : 32;
+                    int len = end - (int)lane;
+                    const int64_t rem = n - (i - lane);  // live lanes in this group
+                    if (rem < 32 && end > rem) len = (int)rem - (int)lane;
+                    atomicAdd(&count[c], len);
+                }
+            } else {
+                const unsigned peers = __match_any_sync(0xffffffffu, c);
+                if (c >= 0 && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&count[c], __popc(peers));
+            }
+        }
     }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&stats->error_flags, (unsigned long long)kErrCellRange);
+    if (__any_sync(0xffffffffu, disorder || bad) && lane == 0) atomicOr(&unsorted[s], 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -246,40 +282,59 @@ __global__ void __launch_bounds__(256) k_scan_final(ScanFinalArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Keyed placement: record (key, input index) at off[c] + cursor.
+// Keyed placement of input not yet in cell order: each particle's record
+// (Philox key, id, momentum) goes to off[c] + cursor.  A record fills one
+// aligned 32-byte sector, written as two 16-byte stores, so the scattered
+// writes never leave partly written sectors behind.  Input already in cell
+// order (k_count found no descent and no bad index) skips this kernel: the
+// sort then reads the input arrays in place.
 // ---------------------------------------------------------------------------
-struct KeyScatterArgs {
+struct PlaceArgs {
     const int32_t* cell[2];
     const uint32_t* id[2];
+    const float* u[2][3];
     int64_t n[2];
     const int32_t* off[2];
     int32_t* cursor[2];
-    uint2* rec[2];
+    const int32_t* unsorted;
+    SortRec* rec[2];
     int64_t C;
     uint64_t seed, step;
 };
 
-__global__ void k_key_scatter(KeyScatterArgs a)
+__device__ __forceinline__ void store_rec(SortRec* r, uint32_t key, uint32_t pid, float ux, float uy, float uz)
 {
-    const bool e = blockIdx.y == 0;
-    const int64_t n = e ? a.n[0] : a.n[1];
-    const int32_t* __restrict__ cell = e ? a.cell[0] : a.cell[1];
-    const uint32_t* __restrict__ id = e ? a.id[0] : a.id[1];
-    const int32_t* __restrict__ off = e ? a.off[0] : a.off[1];
-    int32_t* __restrict__ cursor = e ? a.cursor[0] : a.cursor[1];
-    uint2* __restrict__ rec = e ? a.rec[0] : a.rec[1];
-    const uint32_t stream = e ? kStreamPairE : kStreamPairG;
+    uint4* q = reinterpret_cast<uint4*>(r);
+    q[0] = make_uint4(key, pid, __float_as_uint(ux), __float_as_uint(uy));
+    q[1] = make_uint4(__float_as_uint(uz), 0u, 0u, 0u);
+}
+
+__global__ void k_place(PlaceArgs a)
+{
+    const int s = blockIdx.y;
+    if (a.unsorted[s] == 0) return;
+    const int64_t n = a.n[s];
+    const int32_t* __restrict__ cell = a.cell[s];
+    const uint32_t* __restrict__ id = a.id[s];
+    const float* __restrict__ u0 = a.u[s][0];
+    const float* __restrict__ u1 = a.u[s][1];
+    const float* __restrict__ u2 = a.u[s][2];
+    const int32_t* __restrict__ off = a.off[s];
+    int32_t* __restrict__ cursor = a.cursor[s];
+    SortRec* __restrict__ rec = a.rec[s];
+    const uint32_t stream = s == 0 ? kStreamPairE : kStreamPairG;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t n_round = (n + 31) / 32 * 32;
     const unsigned lane = lane_id();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
         int c = -1;
-        uint32_t key = 0;
+        uint32_t key = 0, pid = 0;
         if (i < n) {
             const int32_t ci = cell[i];
             if (ci >= 0 && (int64_t)ci < a.C) {
                 c = ci;
-                key = draw(a.seed, a.step, stream, id[i]).r0;
+                pid = id[i];
+                key = draw(a.seed, a.step, stream, pid).r0;
             }
         }
         const unsigned peers = __match_any_sync(0xffffffffu, c);
@@ -288,236 +343,310 @@ __global__ void k_key_scatter(KeyScatterArgs a)
         if (c >= 0 && lane == (unsigned)leader) base = atomicAdd(&cursor[c], __popc(peers));
         base = __shfl_sync(peers, base, leader);
         if (c >= 0) {
-            const int rank = __popc(peers & ((1u << lane) - 1u));
-            rec[off[c] + base + rank] = make_uint2(key, (uint32_t)i);
+            const int64_t slot = (int64_t)off[c] + base + __popc(peers & ((1u << lane) - 1u));
+            store_rec(rec + slot, key, pid, u0[i], u1[i], u2[i]);
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// Per-cell sort by (key, id) and gather into sorted order.
+// Per-cell sort by (key, id) and copy into sorted order.
+//
+// Keys are uniform 32-bit Philox words, so within a cell of n particles the
+// bucket floor(key * n / 2^32) is monotone in the key and holds about one
+// particle.  A sort tile (whole cells, at most kSortCap particles) gives cell
+// c the buckets [a_c, a_c + n_c) at its own positions in the tile, so one
+// counting sort over all buckets of the tile sorts every cell at once: a
+// histogram in shared memory, one block-wide exclusive scan (its value at the
+// start of a cell's buckets is a_c), placement by bucket, and an exact rank
+// by (key, id) inside each bucket.  The sorted tile leaves through an inverse
+// permutation, so the global writes are coalesced.  O(1) work per particle,
+// every lane busy whatever the cell sizes.
 // ---------------------------------------------------------------------------
 struct SortGatherArgs {
     const float* in_u[2][3];
-    const int32_t* in_cell[2];
     const uint32_t* in_id[2];
     float* out_u[2][3];
     int32_t* out_cell[2];
     uint32_t* out_id[2];
-    const uint2* rec[2];
+    SortRec* rec[2];
     const int32_t* off[2];
     const int32_t* stile[2];
+    const int32_t* unsorted;
     int64_t nb_e;
+    uint64_t seed, step;
 };
 
-// Sort keys are (key << 32 | id) in 64 bits; the shared-memory position j
-// breaks ties between equal ids (invalid input), so every order is total and
-// every sort yields a permutation.
+// Where a species' particles are read from: the placed records, or (input in
+// cell order) the input arrays, with keys drawn from the ids.
+struct SortSrc {
+    const SortRec* rec;  // nullptr: read the input arrays in place
+    const uint32_t* id;
+    const float* u[3];
+    uint64_t seed, step;
+    uint32_t stream;
+};
+
+// Sort keys are (key << 32 | id) in 64 bits; the position j breaks ties
+// between equal ids (invalid input), so the order is total and every sort
+// yields a permutation.
 __device__ __forceinline__ int before64(uint64_t kj, int j, uint64_t ki, int i)
 {
     return (kj < ki) | ((kj == ki) & (j < i));
 }
 
-// Rank the elements base .. base + 32E - 1 of the segment [a, a+n) against the
-// whole segment with one warp: each lane holds E of them in registers and one
-// broadcast read of key64[j] serves all E comparisons.  perm[a + rank] = index.
-template <int E>
-__device__ __forceinline__ void warp_rank_chunk(const uint64_t* key64, int32_t* perm, int a, int n, int base)
+__device__ __forceinline__ int bucket_of(uint32_t key, int n) { return (int)__umulhi(key, (uint32_t)n); }
+
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src)
 {
-    const int lane = (int)lane_id();
-    uint64_t k[E];
-    int idx[E], rank[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        idx[e] = a + base + 32 * e + lane;
-        k[e] = base + 32 * e + lane < n ? key64[idx[e]] : 0ull;
-        rank[e] = 0;
-    }
-    for (int j = a; j < a + n; ++j) {
-        const uint64_t kj = key64[j];
-#pragma unroll
-        for (int e = 0; e < E; ++e) rank[e] += before64(kj, j, k[e], idx[e]);
-    }
-#pragma unroll
-    for (int e = 0; e < E; ++e)
-        if (base + 32 * e + lane < n) perm[a + rank[e]] = idx[e];
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
 
-// Sort the segment [a, a+n) (n <= 32 E) with one warp: a bitonic network over
-// 32 E slots held E per lane (slot i = 32 e + lane), ordered by (key64, index)
-// so the order is total and the network always yields a permutation.  Strides
-// below 32 exchange through shuffles, larger ones swap registers.
-template <int E>
-__device__ __forceinline__ void warp_bitonic_segment(uint64_t* key64, int32_t* perm, int a, int n)
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+struct SortSmem {
+    uint64_t* key64;  // [cap] (key << 32) | id
+    int32_t* cnt;     // [cap] bucket counts, then bucket starts, then ends
+    uint32_t* cmap;   // [cap] a_c | n_c << 16 of the element's cell
+    uint16_t* bidx;   // [cap] bucket of the element
+    uint16_t* ptmp;   // [cap] tile positions grouped by bucket
+    uint16_t* perm;   // [cap] sorted position -> tile position
+    float* us[3];     // [cap] momenta staged from global memory
+};
+
+// Element gi of the source to tile slot i: its 64-bit sort key and momentum
+// (by cp.async when read in place; wait before using us).
+__device__ __forceinline__ uint32_t fetch_elem(const SortSrc& t, const SortSmem& m, int64_t gi, int i)
 {
-    const int lane = (int)lane_id();
-    uint64_t k[E];
-    int32_t p[E];
+    uint32_t key, pid;
+    if (t.rec) {
+        const uint4* q = reinterpret_cast<const uint4*>(t.rec + gi);
+        const uint4 r0 = q[0], r1 = q[1];
+        key = r0.x;
+        pid = r0.y;
+        m.us[0][i] = __uint_as_float(r0.z);
+        m.us[1][i] = __uint_as_float(r0.w);
+        m.us[2][i] = __uint_as_float(r1.x);
+    } else {
+        cp_async4(&m.us[0][i], t.u[0] + gi);
+        cp_async4(&m.us[1][i], t.u[1] + gi);
+        cp_async4(&m.us[2][i], t.u[2] + gi);
+        pid = t.id[gi];
+        key = draw(t.seed, t.step, t.stream, pid).r0;
+    }
+    m.key64[i] = ((uint64_t)key << 32) | pid;
+    return key;
+}
+
+// Block-wide exclusive scan of cnt[0 .. R) in place (R <= kSortCap).
+__device__ __forceinline__ void block_scan_counts(int32_t* cnt, int R)
+{
+    constexpr int kPer = (kSortCap + kSortThreads - 1) / kSortThreads;
+    __shared__ int32_t warp_tot[kSortThreads / 32];
+    const int tid = threadIdx.x, lane = (int)lane_id(), w = tid >> 5;
+    const int b0 = tid * kPer;
+    int v[kPer];
+    int sum = 0;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = e * 32 + lane;
-        if (i < n) {
-            k[e] = key64[a + i];
-            p[e] = a + i;
-        } else {
-            k[e] = ~0ull;
-            p[e] = 0x40000000 + i;  // padding sorts last
+    for (int k = 0; k < kPer; ++k) {
+        v[k] = b0 + k < R ? cnt[b0 + k] : 0;
+        sum += v[k];
+    }
+    int inc = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < kSortThreads / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, t, d);
+            if (lane >= d) t += o;
+        }
+        if (lane < kSortThreads / 32) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    int run = (w > 0 ? warp_tot[w - 1] : 0) + inc - sum;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        if (b0 + k < R) cnt[b0 + k] = run;
+        run += v[k];
+    }
+}
+
+// Sort the tile of cells [c0, c1) (positions o0 .. o0 + R of species s) with
+// the whole block.
+__device__ __forceinline__ void sort_tile_block(const SortGatherArgs& g, int s, const SortSrc& t, const SortSmem& m,
+                                                int64_t c0, int64_t c1, int64_t o0, int R)
+{
+    const int tid = threadIdx.x, lane = (int)lane_id(), w = tid >> 5;
+    const int32_t* __restrict__ off = g.off[s];
+    // cell of every position (warp per cell) and the output cell indices
+    for (int64_t c = c0 + w; c < c1; c += kSortThreads / 32) {
+        const int a = off[c] - (int32_t)o0;
+        const int n = off[c + 1] - off[c];
+        for (int j = lane; j < n; j += 32) {
+            m.cmap[a + j] = (uint32_t)a | ((uint32_t)n << 16);
+            g.out_cell[s][o0 + a + j] = (int32_t)c;
         }
     }
-    constexpr int N = 32 * E;
-#pragma unroll
-    for (int kk = 2; kk <= N; kk <<= 1) {
-#pragma unroll
-        for (int j = kk >> 1; j > 0; j >>= 1) {
-            if (j >= 32) {
-                const int je = j >> 5;
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    if ((e & je) == 0) {
-                        const int e2 = e | je;
-                        const bool asc = ((e * 32 + lane) & kk) == 0;
-                        const bool gt = (k[e] > k[e2]) || (k[e] == k[e2] && p[e] > p[e2]);
-                        if (gt == asc) {
-                            const uint64_t tk = k[e];
-                            k[e] = k[e2];
-                            k[e2] = tk;
-                            const int32_t tp = p[e];
-                            p[e] = p[e2];
-                            p[e2] = tp;
-                        }
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const uint64_t ok = __shfl_xor_sync(0xffffffffu, k[e], j);
-                    const int32_t op = __shfl_xor_sync(0xffffffffu, p[e], j);
-                    const bool take_min = (((lane & j) == 0) == (((e * 32 + lane) & kk) == 0));
-                    const bool other_smaller = (ok < k[e]) || (ok == k[e] && op < p[e]);
-                    if (take_min == other_smaller) {
-                        k[e] = ok;
-                        p[e] = op;
-                    }
-                }
+    for (int i = tid; i < R; i += kSortThreads) m.cnt[i] = 0;
+    __syncthreads();
+    // keys, momenta, bucket histogram
+    for (int i = tid; i < R; i += kSortThreads) {
+        const uint32_t key = fetch_elem(t, m, o0 + i, i);
+        const uint32_t cm = m.cmap[i];
+        const int b = (int)(cm & 0xffffu) + bucket_of(key, (int)(cm >> 16));
+        m.bidx[i] = (uint16_t)b;
+        atomicAdd(&m.cnt[b], 1);
+    }
+    __syncthreads();
+    block_scan_counts(m.cnt, R);
+    __syncthreads();
+    // positions grouped by bucket; afterwards cnt[b] = end of bucket b
+    for (int i = tid; i < R; i += kSortThreads) {
+        const int pos = atomicAdd(&m.cnt[m.bidx[i]], 1);
+        m.ptmp[pos] = (uint16_t)i;
+    }
+    __syncthreads();
+    // exact rank inside each bucket (the end of bucket b - 1 is the start of
+    // bucket b, also across cells)
+    for (int i = tid; i < R; i += kSortThreads) {
+        const int b = m.bidx[i];
+        const int lo = b == 0 ? 0 : m.cnt[b - 1];
+        const int hi = m.cnt[b];
+        int fin = lo;
+        if (hi - lo > 1) {
+            const uint64_t ki = m.key64[i];
+            for (int q = lo; q < hi; ++q) {
+                const int jj = m.ptmp[q];
+                fin += before64(m.key64[jj], jj, ki, i);
             }
         }
+        m.perm[fin] = (uint16_t)i;
     }
-    __syncwarp();
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = e * 32 + lane;
-        if (i < n) {
-            perm[a + i] = p[e];
-            key64[a + i] = k[e];
-        }
+    cp_async_wait_all();
+    __syncthreads();
+    // coalesced write of the sorted tile
+    for (int q = tid; q < R; q += kSortThreads) {
+        const int i = m.perm[q];
+        const int64_t go = o0 + q;
+        g.out_u[s][0][go] = m.us[0][i];
+        g.out_u[s][1][go] = m.us[1][i];
+        g.out_u[s][2][go] = m.us[2][i];
+        g.out_id[s][go] = (uint32_t)m.key64[i];
     }
-    __syncwarp();
 }
 
-// Count of sorted keys in key64[b .. b+m) below k (strict) or not above k.
-__device__ __forceinline__ int count_below(const uint64_t* key64, int b, int m, uint64_t k, bool or_equal)
-{
-    int pos = 0;
-#pragma unroll
-    for (int step = 64; step > 0; step >>= 1) {  // m <= 64: all of a full chunk can count
-        if (pos + step <= m) {
-            const uint64_t v = key64[b + pos + step - 1];
-            if (v < k || (or_equal && v == k)) pos += step;
-        }
-    }
-    return pos;
-}
-
-// Segments of 65..256: each 64-element chunk sorted by the bitonic network
-// (keys written back in sorted order, source indices in perm), then every
-// element's final rank = its rank in its chunk + the number of elements
-// before it in each other sorted chunk (binary search; ties go to the lower
-// chunk, so ranks stay unique).  Results are written after all ranks are
-// known.
-__device__ __forceinline__ void warp_chunk_merge_segment(uint64_t* key64, int32_t* perm, int a, int n)
+// One cell of n <= kSortCap particles (tile positions [0, n), global o ...)
+// sorted by one warp with the same bucket method, written directly.
+__device__ __forceinline__ void sort_cell_warp(const SortGatherArgs& g, int s, const SortSrc& t, const SortSmem& m,
+                                               int64_t o, int n, int32_t c)
 {
     const int lane = (int)lane_id();
-    const int nc = (n + 63) >> 6;
-    for (int c = 0; c < nc; ++c) {
-        const int cn = n - 64 * c < 64 ? n - 64 * c : 64;
-        warp_bitonic_segment<2>(key64, perm, a + 64 * c, cn);
+    for (int j = lane; j < n; j += 32) m.cnt[j] = 0;
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) {
+        const uint32_t key = fetch_elem(t, m, o + j, j);
+        atomicAdd(&m.cnt[bucket_of(key, n)], 1);
+        g.out_cell[s][o + j] = c;
     }
-    uint64_t kk[8];
-    int32_t pp[8];
-    int rank[8];
+    __syncwarp();
+    int carry = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int j = base + lane;
+        const int v = j < n ? m.cnt[j] : 0;
+        int inc = v;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        const int idx = lane + 32 * t;
-        rank[t] = -1;
-        if (idx < n) {
-            const int c = idx >> 6;
-            kk[t] = key64[a + idx];
-            pp[t] = perm[a + idx];
-            int r = idx & 63;
-            for (int c2 = 0; c2 < nc; ++c2) {
-                if (c2 == c) continue;
-                const int cn2 = n - 64 * c2 < 64 ? n - 64 * c2 : 64;
-                r += count_below(key64, a + 64 * c2, cn2, kk[t], c2 < c);
+        for (int d = 1; d < 32; d <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += x;
+        }
+        if (j < n) m.cnt[j] = carry + inc - v;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) {
+        const int pos = atomicAdd(&m.cnt[bucket_of((uint32_t)(m.key64[j] >> 32), n)], 1);
+        m.ptmp[pos] = (uint16_t)j;
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) {
+        const uint64_t kj = m.key64[j];
+        const int b = bucket_of((uint32_t)(kj >> 32), n);
+        const int lo = b == 0 ? 0 : m.cnt[b - 1];
+        const int hi = m.cnt[b];
+        int fin = lo;
+        if (hi - lo > 1)
+            for (int q = lo; q < hi; ++q) {
+                const int jj = m.ptmp[q];
+                fin += before64(m.key64[jj], jj, kj, j);
             }
-            rank[t] = r;
-        }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        if (rank[t] >= 0) {
-            key64[a + rank[t]] = kk[t];
-            perm[a + rank[t]] = pp[t];
-        }
+        const int64_t go = o + fin;
+        g.out_u[s][0][go] = m.us[0][j];
+        g.out_u[s][1][go] = m.us[1][j];
+        g.out_u[s][2][go] = m.us[2][j];
+        g.out_id[s][go] = (uint32_t)kj;
     }
     __syncwarp();
 }
 
-// Cells of up to 64 particles: bitonic network in registers; up to 256:
-// sorted 64-element chunks merged by rank; larger: register-held ranking
-// against the whole cell.  Only perm is meaningful afterwards (key64 may hold
-// keys in sorted or in original order, depending on the path).
-__device__ __forceinline__ void sort_segment(uint64_t* key64, int32_t* perm, int a, int n)
+// A cell larger than the shared-memory capacity: records in global memory
+// (materialised from the input first when the placement was skipped), each
+// particle ranked against the whole cell by the block.
+__device__ void sort_giant_cell(const SortGatherArgs& g, int s, const SortSrc& t, int64_t o, int64_t n, int32_t c)
 {
-    if (n <= 32) warp_bitonic_segment<1>(key64, perm, a, n);
-    else if (n <= 64) warp_bitonic_segment<2>(key64, perm, a, n);
-    else if (n <= 256) warp_chunk_merge_segment(key64, perm, a, n);
-    else
-        for (int base = 0; base < n; base += 256) warp_rank_chunk<8>(key64, perm, a, n, base);
+    SortRec* rec = g.rec[s];
+    if (!t.rec) {
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t pid = t.id[o + i];
+            store_rec(rec + o + i, draw(t.seed, t.step, t.stream, pid).r0, pid, t.u[0][o + i], t.u[1][o + i],
+                      t.u[2][o + i]);
+        }
+        __syncthreads();
+    }
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const SortRec ri = rec[o + i];
+        int64_t rank = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            const uint32_t kj = rec[o + j].key, dj = rec[o + j].id;
+            rank += (kj < ri.key) | ((kj == ri.key) & ((dj < ri.id) | ((dj == ri.id) & (j < i))));
+        }
+        const int64_t p = o + rank;
+        g.out_u[s][0][p] = ri.ux;
+        g.out_u[s][1][p] = ri.uy;
+        g.out_u[s][2][p] = ri.uz;
+        g.out_cell[s][p] = c;
+        g.out_id[s][p] = ri.id;
+    }
+    __syncthreads();
 }
 
-__device__ __forceinline__ void gather_out(const SortGatherArgs& g, int s, const uint32_t* src, const int32_t* perm,
-                                           int64_t o0, int R)
-{
-    const uint32_t* __restrict__ iid = g.in_id[s];
-    const float* __restrict__ iu0 = g.in_u[s][0];
-    const float* __restrict__ iu1 = g.in_u[s][1];
-    const float* __restrict__ iu2 = g.in_u[s][2];
-    const int32_t* __restrict__ icell = g.in_cell[s];
-    for (int p = threadIdx.x; p < R; p += blockDim.x) {
-        const int i = perm[p];
-        const uint32_t sidx = src[i];
-        g.out_u[s][0][o0 + p] = iu0[sidx];
-        g.out_u[s][1][o0 + p] = iu1[sidx];
-        g.out_u[s][2][o0 + p] = iu2[sidx];
-        g.out_cell[s][o0 + p] = icell[sidx];
-        g.out_id[s][o0 + p] = iid[sidx];
-    }
-}
+constexpr size_t kSortSmem = (size_t)kSortCap * (8 + 4 + 4 + 2 + 2 + 2 + 12);
 
 __global__ void __launch_bounds__(kSortThreads, 2) k_sort_gather(SortGatherArgs g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t* key64 = reinterpret_cast<uint64_t*>(smem_raw);
-    uint32_t* src = reinterpret_cast<uint32_t*>(key64 + kSortCap);
-    int32_t* perm = reinterpret_cast<int32_t*>(src + kSortCap);
-    __shared__ int next_cell;
+    SortSmem m;
+    m.key64 = reinterpret_cast<uint64_t*>(smem_raw);
+    m.cnt = reinterpret_cast<int32_t*>(m.key64 + kSortCap);
+    m.cmap = reinterpret_cast<uint32_t*>(m.cnt + kSortCap);
+    m.us[0] = reinterpret_cast<float*>(m.cmap + kSortCap);
+    m.us[1] = m.us[0] + kSortCap;
+    m.us[2] = m.us[1] + kSortCap;
+    m.bidx = reinterpret_cast<uint16_t*>(m.us[2] + kSortCap);
+    m.ptmp = m.bidx + kSortCap;
+    m.perm = m.ptmp + kSortCap;
 
     const int s = (int64_t)blockIdx.x < g.nb_e ? 0 : 1;
     const int64_t b = s == 0 ? blockIdx.x : blockIdx.x - g.nb_e;
     const int32_t* __restrict__ off = g.off[s];
-    const uint2* __restrict__ rec = g.rec[s];
-    const uint32_t* __restrict__ in_id = g.in_id[s];
     const int64_t c0 = g.stile[s][b];
     const int64_t c1 = g.stile[s][b + 1];
     if (c1 <= c0) return;
@@ -525,68 +654,30 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort_gather(SortGatherArgs 
     const int64_t R = (int64_t)off[c1] - o0;
     if (R <= 0) return;
 
+    SortSrc t;
+    const bool placed = g.unsorted[s] != 0;
+    t.rec = placed ? g.rec[s] : nullptr;
+    t.id = g.in_id[s];
+    for (int k = 0; k < 3; ++k) t.u[k] = g.in_u[s][k];
+    t.seed = g.seed;
+    t.step = g.step;
+    t.stream = s == 0 ? kStreamPairE : kStreamPairG;
+
     if (R <= kSortCap) {
-        for (int i = threadIdx.x; i < R; i += blockDim.x) {
-            const uint2 r = rec[o0 + i];
-            key64[i] = ((uint64_t)r.x << 32) | in_id[r.y];
-            src[i] = r.y;
-        }
-        if (threadIdx.x == 0) next_cell = 0;
-        __syncthreads();
-        // warps take cells in order as they finish (balances uneven cell sizes)
-        for (;;) {
-            int c = 0;
-            if (lane_id() == 0) c = atomicAdd(&next_cell, 1);
-            c = __shfl_sync(0xffffffffu, c, 0) + (int)c0;
-            if (c >= c1) break;
-            const int a = off[c] - (int32_t)o0;
-            const int n = off[c + 1] - off[c];
-            if (n > 0) sort_segment(key64, perm, a, n);
-        }
-        __syncthreads();
-        gather_out(g, s, src, perm, o0, (int)R);
+        sort_tile_block(g, s, t, m, c0, c1, o0, (int)R);
         return;
     }
-
-    // A cell range larger than shared memory: cell by cell.
+    // A cell range larger than shared memory: cell by cell, each at the start
+    // of the shared buffers (warp 0), or in global memory (the block).
     for (int64_t c = c0; c < c1; ++c) {
         const int64_t o = off[c];
         const int64_t n = (int64_t)off[c + 1] - o;
         if (n <= 0) continue;
         if (n <= kSortCap) {
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const uint2 r = rec[o + i];
-                key64[i] = ((uint64_t)r.x << 32) | in_id[r.y];
-                src[i] = r.y;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const uint64_t ki = key64[i];
-                int rank = 0;
-                for (int j = 0; j < n; ++j) rank += before64(key64[j], j, ki, i);
-                perm[rank] = i;
-            }
-            __syncthreads();
-            gather_out(g, s, src, perm, o, (int)n);
-            __syncthreads();
+            if (threadIdx.x < 32) sort_cell_warp(g, s, t, m, o, (int)n, (int32_t)c);
         } else {
-            // Oversized cell: rank against the records in global memory.
-            for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-                const uint2 ri = rec[o + i];
-                const uint32_t di = in_id[ri.y];
-                int64_t rank = 0;
-                for (int64_t j = 0; j < n; ++j) {
-                    const uint2 rj = rec[o + j];
-                    const uint32_t dj = in_id[rj.y];
-                    rank += (rj.x < ri.x) | ((rj.x == ri.x) & ((dj < di) | ((dj == di) & (j < i))));
-                }
-                const int64_t p = o + rank;
-                g.out_u[s][0][p] = g.in_u[s][0][ri.y];
-                g.out_u[s][1][p] = g.in_u[s][1][ri.y];
-                g.out_u[s][2][p] = g.in_u[s][2][ri.y];
-                g.out_cell[s][p] = g.in_cell[s][ri.y];
-                g.out_id[s][p] = di;
-            }
+            __syncthreads();
+            sort_giant_cell(g, s, t, o, n, (int32_t)c);
         }
     }
 }
@@ -610,11 +701,12 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
     const int64_t n_tiles = (C + kScanTile - 1) / kScanTile;
     COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->count[0], 0, sizeof(int32_t) * C, stream));
     COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->count[1], 0, sizeof(int32_t) * C, stream));
+    COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->unsorted, 0, 2 * sizeof(int32_t), stream));
 
     const int64_t nmax = ne > ng ? ne : ng;
-    const dim3 pgrid(grid_for(nmax, 256, 152 * 16), 2);
-    k_count<<<pgrid, 256, 0, stream>>>(e_in->cell_dev, ne, g_in->cell_dev, ng, C, ctx->count[0], ctx->count[1],
-                                       ctx->stats);
+    const dim3 cgrid(grid_for((nmax + 127) / 128, 8, 152 * 8), 2);  // 8 warps per block, 128 particles per warp
+    k_count<<<cgrid, 256, 0, stream>>>(e_in->cell_dev, ne, g_in->cell_dev, ng, C, ctx->count[0], ctx->count[1],
+                                       ctx->unsorted, ctx->stats);
     COMPTON_LAUNCH_CHECK(ctx, "k_count");
     k_scan_reduce<<<(unsigned)n_tiles, 256, 0, stream>>>(ctx->count[0], ctx->count[1], C, ctx->block_sums,
                                                          n_tiles);
@@ -645,33 +737,34 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
     k_scan_final<<<(unsigned)n_tiles, 256, 0, stream>>>(sf);
     COMPTON_LAUNCH_CHECK(ctx, "k_scan_final");
 
-    KeyScatterArgs ks;
-    ks.cell[0] = e_in->cell_dev;
-    ks.cell[1] = g_in->cell_dev;
-    ks.id[0] = e_in->id_dev;
-    ks.id[1] = g_in->id_dev;
-    ks.n[0] = ne;
-    ks.n[1] = ng;
+    const dim3 pgrid(grid_for(nmax, 256, 152 * 16), 2);
+    PlaceArgs pa;
+    const compton_species* ins[2] = {e_in, g_in};
+    compton_species* outs[2] = {e_out, g_out};
     for (int s = 0; s < 2; ++s) {
-        ks.off[s] = ctx->off[s];
-        ks.cursor[s] = ctx->count[s];
-        ks.rec[s] = ctx->rec[s];
+        pa.cell[s] = ins[s]->cell_dev;
+        pa.id[s] = ins[s]->id_dev;
+        pa.u[s][0] = ins[s]->ux_dev;
+        pa.u[s][1] = ins[s]->uy_dev;
+        pa.u[s][2] = ins[s]->uz_dev;
+        pa.n[s] = ins[s]->n;
+        pa.off[s] = ctx->off[s];
+        pa.cursor[s] = ctx->count[s];
+        pa.rec[s] = ctx->rec[s];
     }
-    ks.C = C;
-    ks.seed = ctx->cfg.seed;
-    ks.step = step;
-    k_key_scatter<<<pgrid, 256, 0, stream>>>(ks);
-    COMPTON_LAUNCH_CHECK(ctx, "k_key_scatter");
+    pa.unsorted = ctx->unsorted;
+    pa.C = C;
+    pa.seed = ctx->cfg.seed;
+    pa.step = step;
+    k_place<<<pgrid, 256, 0, stream>>>(pa);
+    COMPTON_LAUNCH_CHECK(ctx, "k_place");
 
     if (nb_e + nb_g > 0) {
         SortGatherArgs sg;
-        const compton_species* ins[2] = {e_in, g_in};
-        compton_species* outs[2] = {e_out, g_out};
         for (int s = 0; s < 2; ++s) {
             sg.in_u[s][0] = ins[s]->ux_dev;
             sg.in_u[s][1] = ins[s]->uy_dev;
             sg.in_u[s][2] = ins[s]->uz_dev;
-            sg.in_cell[s] = ins[s]->cell_dev;
             sg.in_id[s] = ins[s]->id_dev;
             sg.out_u[s][0] = outs[s]->ux_dev;
             sg.out_u[s][1] = outs[s]->uy_dev;
@@ -682,8 +775,11 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
             sg.off[s] = ctx->off[s];
             sg.stile[s] = ctx->stile[s];
         }
+        sg.unsorted = ctx->unsorted;
+        sg.seed = ctx->cfg.seed;
+        sg.step = step;
         sg.nb_e = nb_e;
-        const int smem = kSortCap * 16;
+        const int smem = (int)kSortSmem;
         COMPTON_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sort_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    smem));
         k_sort_gather<<<(unsigned)(nb_e + nb_g), kSortThreads, smem, stream>>>(sg);

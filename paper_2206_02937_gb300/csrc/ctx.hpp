@@ -13,8 +13,8 @@ namespace compton {
 
 // Tiling constants shared by the binning and scattering kernels.
 constexpr int kScanTile = 2048;       // cells per scan tile (256 threads x 8)
-constexpr int kSortTile = 4096;       // particles per sort tile (by cell start offsets)
-constexpr int kSortCap = 6144;        // particles a sort CTA holds in shared memory
+constexpr int kSortTile = 2048;       // particles per sort tile (by cell start offsets)
+constexpr int kSortCap = 3072;        // particles a sort CTA holds in shared memory
 constexpr int kPairsPerTile = 1024;   // pairs per scatter CTA (256 threads x 4)
 constexpr int kCellWindow = 512;      // cells of a scatter tile staged in shared memory
 
@@ -24,6 +24,14 @@ struct __align__(16) CellInfo {
     int32_t e_start;   // first sorted electron
     int32_t g_start;   // first sorted photon
     float dens;        // pair density n_c = max(N_e, N_g) * w_over_v
+};
+
+// A particle placed in its cell's segment by the binning: Philox key, id,
+// momentum, padded to one aligned 32-byte sector.
+struct __align__(32) SortRec {
+    uint32_t key, id;
+    float ux, uy, uz;
+    uint32_t pad[3];
 };
 
 enum : unsigned { kErrCellRange = 1u, kErrCapacity = 2u, kErrTimeout = 4u };
@@ -79,7 +87,8 @@ struct compton_ctx {
     // binning scratch (index 0 = electrons, 1 = photons)
     int32_t* count[2] = {nullptr, nullptr};      // [C] histogram, then insertion cursor
     int32_t* off[2] = {nullptr, nullptr};        // [C+1]
-    uint2* rec[2] = {nullptr, nullptr};          // [max_particles] (key, source index)
+    compton::SortRec* rec[2] = {nullptr, nullptr};  // [max_particles] placed records
+    int32_t* unsorted = nullptr;                 // [2] set when a species' input is not in cell order
     int32_t* stile[2] = {nullptr, nullptr};      // [max_sort_tiles+1] first cell of each sort tile
     int64_t* block_sums = nullptr;               // [3 * max_scan_tiles]
     compton::CellInfo* cinfo = nullptr;          // [C]

@@ -91,34 +91,33 @@ struct Invariants {
 // sqrt(x) from the hardware reciprocal square root (a few ulp), 0 at 0.
 __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 
+// Straight-line form (no branch, so the pairs of a thread interleave): the
+// reciprocal square roots give 1/gamma, 1/|u| and 1/|k| directly, so
+// beta = |u|/gamma, 1 - beta = (1/gamma)/(gamma + |u|), cos psi = u.k/(|u||k|)
+// and sin^2 psi = |u x k|^2/(|u|^2 |k|^2) need two divisions in all.  An
+// electron at rest or a photon of zero energy gives v = 1 (x = gamma eps).
 __device__ __forceinline__ Invariants invariants_f32(float ux, float uy, float uz, float kx, float ky, float kz)
 {
     Invariants r;
     const float uu = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-    const float un = fast_sqrt(uu);
-    r.gamma = fast_sqrt(1.0f + uu);
-    r.eps = fast_sqrt(fmaf(kx, kx, fmaf(ky, ky, kz * kz)));
-    float v = 1.0f;
-    if (un > 0.0f && r.eps > 0.0f) {
-        const float beta = __fdividef(un, r.gamma);
-        const float omb = __fdividef(1.0f, r.gamma * (r.gamma + un));
-        const float uk = fmaf(ux, kx, fmaf(uy, ky, uz * kz));
-        const float ue = un * r.eps;
-        const float cosp = __fdividef(uk, ue);
-        float omc;
-        if (cosp > 0.0f) {
-            const float cx = diff_of_products(uy, kz, uz, ky);
-            const float cy = diff_of_products(uz, kx, ux, kz);
-            const float cz = diff_of_products(ux, ky, uy, kx);
-            const float sn = __fdividef(fast_sqrt(fmaf(cx, cx, fmaf(cy, cy, cz * cz))), ue);
-            omc = __fdividef(sn * sn, 1.0f + cosp);
-        } else {
-            omc = 1.0f - cosp;
-        }
-        v = fmaf(beta, omc, omb);
-    }
-    r.v = v;
-    r.x = r.gamma * r.eps * v;
+    const float kk = fmaf(kx, kx, fmaf(ky, ky, kz * kz));
+    const float ru = rsqrtf(uu), rk = rsqrtf(kk);
+    const float g2 = 1.0f + uu;
+    const float rg = rsqrtf(g2);  // 1/gamma
+    const bool moving = uu > 0.0f, lit = kk > 0.0f;
+    const float un = moving ? uu * ru : 0.0f;
+    r.gamma = g2 * rg;
+    r.eps = lit ? kk * rk : 0.0f;
+    const float rur = ru * rk;
+    const float cosp = fmaf(ux, kx, fmaf(uy, ky, uz * kz)) * rur;
+    const float cx = diff_of_products(uy, kz, uz, ky);
+    const float cy = diff_of_products(uz, kx, ux, kz);
+    const float cz = diff_of_products(ux, ky, uy, kx);
+    const float s2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz)) * rur * rur;  // sin^2 psi
+    const float omc = cosp > 0.0f ? __fdividef(s2, 1.0f + cosp) : 1.0f - cosp;
+    const float v = fmaf(un * rg, omc, __fdividef(rg, r.gamma + un));
+    r.v = moving && lit ? v : 1.0f;
+    r.x = r.gamma * r.eps * r.v;
     return r;
 }
 
@@ -248,24 +247,27 @@ __device__ __forceinline__ float kn_f_upper(float x, float s)
 
 // sigma_KN(x) / sigma_T
 // F(x, 2) = (8/3) sigma_KN(x)/sigma_T, the total of the angular cumulative.  At
-// t = 2: w = 2x, q = 1/(1+x), z = x/(1+x), A = 2(1+x)/(1+2x)^2; in the series
-// range (x < 1/2, z^2 < 1/9) eight terms of S1 suffice.
-__device__ __forceinline__ float kn_F2(float x)
+// t = 2: w = 2x, q = 1/(1+x), z = x/(1+x), and with r = 1/(1+2x) also
+// 1/(1+z) = (1+x) r, 1/(1-z^2) = (1+x)^2 r, A = 2(1+x) r^2: two reciprocals.
+// For x < 1 (z^2 < 1/4) twelve terms of S1 reach FP32 precision.
+__device__ __forceinline__ float kn_F2_series(float x)
 {
-    if (x < 0.5f) {
-        const float q = __fdividef(1.0f, 1.0f + x);
-        const float z = x * q;
-        const float z2 = z * z;
-        float S1, S2;
-        kn_series<8>(z2, S1, S2);
-        const float opw = fmaf(2.0f, x, 1.0f);
-        const float A = __fdividef(2.0f * (1.0f + x), opw * opw);
-        const float B = 2.0f * q * fmaf(z2, S1, 1.0f);
-        const float C = 4.0f * q * q * (fmaf(z, S1, __fdividef(1.0f, 1.0f + z)) - q * S2);
-        return A + B - C;
-    }
-    return kn_F(x, 2.0f);
+    const float opx = 1.0f + x;
+    const float q = __fdividef(1.0f, opx);
+    const float r = __fdividef(1.0f, fmaf(2.0f, x, 1.0f));
+    const float z = x * q;
+    const float z2 = z * z;
+    float S1 = 0.0f;
+#pragma unroll
+    for (int j = 12; j >= 1; --j) S1 = fmaf(S1, z2, 1.0f / (float)(2 * j + 1));
+    const float S2 = opx * opx * r - S1;
+    const float A = 2.0f * opx * r * r;
+    const float B = 2.0f * q * fmaf(z2, S1, 1.0f);
+    const float C = 4.0f * q * q * (fmaf(z, S1, opx * r) - q * S2);
+    return A + B - C;
 }
+
+__device__ __forceinline__ float kn_F2(float x) { return x < 1.0f ? kn_F2_series(x) : kn_F(x, 2.0f); }
 
 __device__ __forceinline__ float kn_sigma(float x) { return 0.375f * kn_F2(x); }
 
@@ -397,17 +399,15 @@ __device__ __forceinline__ void collide_f32(float& ux, float& uy, float& uz, flo
 // 1 - exp(-a) above it (where the result is >= 0.22).
 __device__ __forceinline__ float one_minus_exp_neg(float a)
 {
-    if (a < 0.25f) {
-        float s = 1.0f - a * (1.0f / 8.0f);
-        s = 1.0f - a * (1.0f / 7.0f) * s;
-        s = 1.0f - a * (1.0f / 6.0f) * s;
-        s = 1.0f - a * (1.0f / 5.0f) * s;
-        s = 1.0f - a * (1.0f / 4.0f) * s;
-        s = 1.0f - a * (1.0f / 3.0f) * s;
-        s = 1.0f - a * 0.5f * s;
-        return a * s;
-    }
-    return 1.0f - __expf(-a);
+    float s = 1.0f - a * (1.0f / 8.0f);
+    s = 1.0f - a * (1.0f / 7.0f) * s;
+    s = 1.0f - a * (1.0f / 6.0f) * s;
+    s = 1.0f - a * (1.0f / 5.0f) * s;
+    s = 1.0f - a * (1.0f / 4.0f) * s;
+    s = 1.0f - a * (1.0f / 3.0f) * s;
+    s = 1.0f - a * 0.5f * s;
+    const float e = 1.0f - __expf(-a);
+    return a < 0.25f ? a * s : e;  // both evaluated: no divergence
 }
 
 // ---------------------------------------------------------------------------

@@ -415,12 +415,33 @@ __global__ void k_mlp_set_act_scales(MlpDev m)
     }
 }
 
+// Persistent grid: as many CTAs as fit on every SM at once, counted from the
+// device's shared-memory limits (per SM, and reserved per CTA), the register
+// file and the thread limit, capped by the work.
 int grid_persistent(const void* kernel, int threads, int smem, int64_t work_items, int per_item)
 {
-    int dev = 0, n_sm = 0, per_sm = 0;
+    int dev = 0, n_sm = 1, smem_sm = 0, smem_rsv = 0, regs_sm = 65536, thr_sm = 2048;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    cudaFuncAttributes fa{};
+    int regs = 64;
+    if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) {
+        regs = fa.numRegs > 0 ? fa.numRegs : 64;
+        smem += (int)fa.sharedSizeBytes;
+    }
+    cudaGetLastError();
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    cudaGetLastError();
+    int per_sm = smem > 0 ? smem_sm / (smem + smem_rsv) : 32;
+    const int by_regs = regs_sm / (regs * threads);
+    const int by_thr = thr_sm / threads;
+    if (by_regs < per_sm) per_sm = by_regs;
+    if (by_thr < per_sm) per_sm = by_thr;
+    if (n_sm < 1) n_sm = 1;
     if (per_sm < 1) per_sm = 1;
     const int64_t need = (work_items + per_item - 1) / per_item;
     const int64_t full = (int64_t)per_sm * n_sm;

@@ -218,3 +218,39 @@ def test_explicit_pairs_and_ratio():
         assert flag.sum() > 100
     finally:
         cgl.compton_destroy(ctx)
+
+
+def _presorted(w):
+    """The same particles, stably ordered by cell: the binning then reads the
+    input in place instead of placing records first."""
+    out = wl.Workload(w.name + " presorted", w.n_cells, w.w_over_v, w.dt, w.seed, w.steps)
+    for name in ("e", "g"):
+        sp = getattr(w, name)
+        order = np.argsort(sp["cell"], kind="stable")
+        setattr(out, name, {k: np.ascontiguousarray(v[order]) for k, v in sp.items()})
+    return out
+
+
+@pytest.mark.parametrize("case", ["ragged", "big_cells", "one_sided"])
+def test_presorted_input(case):
+    if case == "ragged":
+        w = _random_workload(12, n_cells=601, ppc_e=45, ppc_g=38)
+    elif case == "big_cells":
+        w = _random_workload(13, 6, 3000, 2800, spread=0.05)  # tiles above shared memory, cells above it too
+    else:
+        rng = wl.rng_for(14)
+        e = wl._species(wl.isotropic(rng, 300), np.arange(300) % 30)
+        g = wl._species(0.1 * wl.isotropic(rng, 90), 3 * (np.arange(90) % 10))
+        w = wl.Workload("one-sided", 40, 0.1, 0.05, 5, 1, e, g)
+    compare_with_oracle(_presorted(w), step=3)
+
+
+def test_two_chained_steps():
+    # the sorted output of one step is the next step's input (the in-place
+    # path); the oracle's second step starts from the GPU's first-step output
+    w = _random_workload(15, n_cells=333, ppc_e=50, ppc_g=47)
+    g1, _, _ = compare_with_oracle(w, step=0)
+    w2 = wl.Workload("second step", w.n_cells, w.w_over_v, w.dt, w.seed, 1,
+                     {k: np.ascontiguousarray(v) for k, v in g1["after_e"].items()},
+                     {k: np.ascontiguousarray(v) for k, v in g1["after_g"].items()})
+    compare_with_oracle(w2, step=1)
