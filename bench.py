@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--train-steps", type=int, default=8000)
     ap.add_argument("--train-balanced", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c5"],
+                    help="c2: the 2D 512x512 step (default); c5: the 3D power-law precision sweep")
+    ap.add_argument("--c5-side", type=int, default=256)
     return ap.parse_args()
 
 
@@ -230,7 +233,6 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     total_ms, pairs_all = reduce_timing(total_ms, pairs, dev)
     value = pairs_all / (total_ms * 1e-3)
 
-    # roofline of the scatter kernel (one launch per compton_scatter_step)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -238,14 +240,53 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    bytes_scatter = pairs_per_step * (24.0 + 24.0 * frac_scat) + w.n_cells * 16.0
     sc_avg = sum(sc_ms) / len(sc_ms)
+    bin_avg = sum(bin_ms) / len(bin_ms)
+
+    # per-kernel device times: the same steps once more with the library's
+    # event timing on (kept out of the headline region above)
+    cg.compton_kernel_timing(ctx, True)
+    for i in range(args.steps):
+        one_step(step, bufs[step % 2], bufs[(step + 1) % 2])
+        step += 1
+    torch.cuda.synchronize()
+    kt = cg.compton_kernel_times(ctx)
+    cg.compton_kernel_timing(ctx, False)
+    n_part = w.n_e + w.n_g
+    acc_per_step = stats["scatters"] / args.steps
+    # algorithmic bytes per launch (input already in cell order)
+    algo_bytes = {
+        "k_count": 4.0 * n_part,                       # cell indices read
+        "k_scan": 48.0 * w.n_cells,                    # counts in, offsets + CellInfo out
+        "k_place": 0.0,                                # returns at once on ordered input
+        "k_sort_gather": 36.0 * n_part,                # id + momentum read, sorted copy written
+        "k_pair_prob": 24.0 * pairs_per_step + 16.0 * acc_per_step + 16.0 * w.n_cells,
+        "k_collide": 64.0 * acc_per_step,              # list entry, both momenta read and written
+    }
+    kernels = {}
+    for name, v in kt.items():
+        if v["launches"] == 0 or name not in algo_bytes:
+            continue
+        avg = v["ms"] / v["launches"]
+        gbs = algo_bytes[name] / (avg * 1e-3) / 1e9
+        kernels[name] = {"avg_launch_ms": avg, "launches_per_step": v["launches"] / args.steps,
+                         "algorithmic_bytes_per_launch": algo_bytes[name], "achieved_gbs": gbs,
+                         "frac_of_hbm": gbs / hbm_peak}
+    dom = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"] * kernels[k]["launches_per_step"])
+    D = kernels[dom]
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": D["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": D["frac_of_hbm"], "traffic": None, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": D["algorithmic_bytes_per_launch"],
+                "avg_launch_ms": D["avg_launch_ms"],
+                "note": "dominant kernel of the step by device time; durations from CUDA events the library "
+                        "records on the launch stream around each kernel"}
+    # whole binning and scattering calls (events around the C-ABI calls)
+    bytes_scatter = pairs_per_step * 24.0 + acc_per_step * 80.0 + w.n_cells * 16.0
     achieved_sc = bytes_scatter / (sc_avg * 1e-3) / 1e9
     # binning of input already in cell order (every step after the first: the
     # particles keep their cells): per particle 4 (count) + 4 + 12 (id and
     # momentum read by the sort) + 20 (sorted write) = 40 B, both species
     bytes_bin = (w.n_e + w.n_g) * 40.0 + w.n_cells * 64.0
-    bin_avg = sum(bin_ms) / len(bin_ms)
     achieved_bin = bytes_bin / (bin_avg * 1e-3) / 1e9
     # binning of shuffled input: 4 (count) + 20 (placement read) + 20 (record
     # write) + 20 (record read) + 20 (sorted write) = 84 B per particle
@@ -284,7 +325,6 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     cg.compton_destroy(ctx)
     if rank == 0:
-        dominant = "k_scatter" if sc_avg >= bin_avg else "bin_pairs (6 kernels)"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -292,18 +332,18 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "config": workload_config(args),
             "pairs_per_step": pairs_per_step, "scatter_fraction": frac_scat,
             "kernel_ms": {"bin_pairs": bin_avg, "scatter_step": sc_avg, "bin_pairs_shuffled_input": bin_shuf_avg},
-            "roofline": {"kernel": "k_scatter", "bound": "hbm", "achieved": achieved_sc, "peak": hbm_peak,
-                         "unit": "GB/s", "frac": achieved_sc / hbm_peak, "traffic": None,
-                         "peak_source": peak_src,
-                         "algorithmic_bytes_per_launch": bytes_scatter,
-                         "note": f"dominant by time: {dominant}"},
+            "roofline": roofline,
+            "kernels": kernels,
+            "roofline_scatter_step": {"bound": "hbm", "achieved": achieved_sc, "peak": hbm_peak, "unit": "GB/s",
+                                      "frac": achieved_sc / hbm_peak, "algorithmic_bytes_per_launch": bytes_scatter,
+                                      "calls": "compton_scatter_step (k_pair_prob + k_collide)"},
             "roofline_bin": {"bound": "hbm", "achieved": achieved_bin, "peak": hbm_peak, "unit": "GB/s",
                              "frac": achieved_bin / hbm_peak, "algorithmic_bytes_per_launch": bytes_bin,
                              "input": "cell order of the previous step's output"},
             "roofline_bin_shuffled": {"bound": "hbm", "achieved": achieved_bin_shuf, "peak": hbm_peak,
                                       "unit": "GB/s", "frac": achieved_bin_shuf / hbm_peak,
                                       "algorithmic_bytes_per_launch": bytes_bin_shuf, "input": "shuffled"},
-            "gpu_launches": 7 * args.steps,
+            "gpu_launches": 8 * args.steps,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -547,6 +587,160 @@ def run_e2e(args, cg, torch, ctx, w, stream, dev):
             "steps": n_steps, "ms_per_step": ms / n_steps}
 
 
+# ---------------------------------------------------------------------------
+# 3D precision sweep: power-law electrons on a photon beam
+# ---------------------------------------------------------------------------
+def log_spectrum(torch, k_after, hit, lo=-5.0, hi=5.0, bins=64):
+    eps = k_after[:, hit].norm(dim=0).double().clamp_min(1e-30)
+    h = torch.histc(eps.log10(), bins=bins, min=lo, max=hi)
+    return h / h.sum().clamp_min(1.0)
+
+
+def oracle_subsample(u, k, dens, dt, seed, step):
+    """The cpu_baseline leg of the sweep: the FP64 oracle on a pre-paired
+    subsample (pair i uses counter i, as the GPU's pair list does), timed on
+    one host core.  Returns its timing and the photon momenta it produced."""
+    import oracle
+    t0 = time.time()
+    uo, ko, P, flag = oracle.pairs(u, k, dens, dt, seed, step)
+    return time.time() - t0, ko, flag
+
+
+def run_c5(args, rank: int, world: int, local_rank: int):
+    import torch
+    import paper_2206_02937_gb300 as cg
+    from paper_2206_02937_gb300 import workloads as wl
+
+    cg.build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+    t_gen = time.time()
+    w = wl.c5(args.c5_side, 16, seed=5 + rank)
+    t_gen = time.time() - t_gen
+
+    def species(d):
+        return cg.Species(torch.from_numpy(d["ux"]).to(dev), torch.from_numpy(d["uy"]).to(dev),
+                          torch.from_numpy(d["uz"]).to(dev), torch.from_numpy(d["cell"]).to(dev),
+                          torch.from_numpy(d["id"].view(np.int32)).to(dev))
+
+    A = [species(w.e), species(w.g)]
+    B = [cg.Species.empty_like(A[0]), cg.Species.empty_like(A[1])]
+    n = max(w.n_e, w.n_g)
+    del w.e, w.g
+    ctx = cg.compton_init(w.n_cells, n, w.w_over_v, w.dt, w.seed, device=local_rank, max_train_batch=8192)
+    stream = torch.cuda.current_stream(dev)
+    bufs = [A, B]
+    step = 0
+
+    def one(src, dst, st, md):
+        pairs = cg.compton_bin_pairs(ctx, src[0], src[1], dst[0], dst[1], st, stream)
+        cg.compton_scatter_step(ctx, dst[0], dst[1], pairs, md, st, None, None, stream)
+
+    for _ in range(args.warmup):
+        one(bufs[step % 2], bufs[(step + 1) % 2], step, cg.MODE_PLAIN)
+        step += 1
+    torch.cuda.synchronize()
+    cg.compton_get_stats(ctx, reset=True)
+    if dist is not None:
+        dist.barrier()
+    with ClockSampler(local_rank) as clk:
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            one(bufs[step % 2], bufs[(step + 1) % 2], step, cg.MODE_PLAIN)
+            step += 1
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    total_ms = t0.elapsed_time(t1)
+    stats = cg.compton_get_stats(ctx, reset=True)
+    from paper_2206_02937_gb300.dist import reduce_timing
+    total_ms, pairs_all = reduce_timing(total_ms, stats["pairs_tested"], dev)
+    value = pairs_all / (total_ms * 1e-3)
+
+    train = train_surrogate(cg, torch, ctx, dev, steps=args.train_steps, balanced=args.train_balanced)
+
+    # the sweep: every mode takes the same state, pairing and draws
+    X, Y = bufs[step % 2], bufs[(step + 1) % 2]
+    st = step
+    n_sub = min(1 << 20, n)
+    sweep, spectra_sub, hits = {}, {}, {}
+    for md, name in ((cg.MODE_PLAIN, "plain"), (cg.MODE_MLP_FP32, "fp32"), (cg.MODE_MLP_BF16, "bf16"),
+                     (cg.MODE_MLP_FP8, "fp8")):
+        ms = []
+        for rep in range(3):
+            pairs = cg.compton_bin_pairs(ctx, X[0], X[1], Y[0], Y[1], st, stream)
+            torch.cuda.synchronize()
+            k_before = torch.stack([Y[1].ux, Y[1].uy, Y[1].uz]).clone()
+            if name == "plain" and rep == 0:
+                sub_u = torch.stack([Y[0].ux[:n_sub], Y[0].uy[:n_sub], Y[0].uz[:n_sub]]).cpu().numpy()
+                sub_k = k_before[:, :n_sub].cpu().numpy()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            cg.compton_get_stats(ctx, reset=True)
+            e0.record(stream)
+            cg.compton_scatter_step(ctx, Y[0], Y[1], pairs, md, st, None, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        stt = cg.compton_get_stats(ctx, reset=True)
+        k_after = torch.stack([Y[1].ux, Y[1].uy, Y[1].uz])
+        hit = (k_after != k_before).any(dim=0)
+        spec = log_spectrum(torch, k_after, hit)
+        hits[name] = int(hit.sum())
+        spectra_sub[name] = (k_after[:, :n_sub].cpu().numpy(), hit[:n_sub].cpu().numpy())
+        sweep[name] = {"scatter_step_ms": statistics.median(ms), "pairs": stt["pairs_tested"],
+                       "scatters": stt["scatters"], "fallbacks": stt["mlp_fallbacks"], "spectrum": spec}
+        del k_before, k_after, hit
+    for name in sweep:
+        sweep[name]["spectrum_L1_vs_plain"] = float((sweep[name]["spectrum"] - sweep["plain"]["spectrum"]).abs().sum())
+        sweep[name]["collision_rate_ratio"] = hits[name] / max(1, hits["plain"])
+    for name in sweep:
+        del sweep[name]["spectrum"]
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # the oracle on the first 2^20 pairs of the same step (all cells hold 16
+        # of each species, so pair p is particle p of both sorted species)
+        dens = np.full(n_sub, 16 * w.w_over_v, dtype=np.float32)
+        dt_cpu, ko, oflag = oracle_subsample(sub_u, sub_k, dens, w.dt, w.seed, st)
+        cpu = {"value": n_sub / dt_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the first {n_sub} pairs of one step of the same workload"}
+        o_hit = oflag == 1
+        o_k = torch.from_numpy(ko)
+        o_spec = log_spectrum(torch, o_k, torch.from_numpy(o_hit))
+        for name, (kg, hg) in spectra_sub.items():
+            g_spec = log_spectrum(torch, torch.from_numpy(kg.astype(np.float64)), torch.from_numpy(hg))
+            sweep[name]["spectrum_L1_vs_oracle_subsample"] = float((g_spec - o_spec).abs().sum())
+            sweep[name]["collisions_subsample"] = int(hg.sum())
+        sweep["oracle_subsample_collisions"] = int(o_hit.sum())
+
+    cg.compton_destroy(ctx)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 above the gamma and gamma-eps thresholds)",
+            "data": "synthetic",
+            "config": {"workload": f"c5: 3D {args.c5_side}^3 cells x 16 per species, electrons dN/dgamma ~ gamma^-2 "
+                                   f"on [1, 1e4], photon beam 1e-2 along +x, dt=0.05, density 1, seed 5",
+                       "mode": "plain (headline); sweep of the surrogate in FP32/BF16/FP8",
+                       "l2": "inputs larger than L2", "generate_s": t_gen},
+            "pairs_per_step": stats["pairs_tested"] / args.steps,
+            "clocks": clk.summary(), "cpu_baseline": cpu, "gpu_launches": 8 * args.steps,
+            "precision_sweep": sweep, "train": train,
+            "spectrum_note": "L1 distance of normalised 64-bin log10(eps) histograms (eps in [1e-5, 1e5]) of the "
+                             "photons that scattered; vs plain over all pairs, vs the FP64 oracle over the subsample",
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -555,7 +749,10 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    run_ours(args, rank, world, local_rank)
+    if args.workload == "c5":
+        run_c5(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
 
 
 if __name__ == "__main__":

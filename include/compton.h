@@ -363,6 +363,34 @@ compton_status compton_serve_info(struct compton_ctx* ctx, uint64_t* bytes_in_us
 compton_status compton_cell_offsets_noalloc(const int32_t* cell_dev, int64_t n, int64_t n_cells,
                                             int32_t* off_out_dev, compton_stream_t stream);
 
+/* ---------------------------------------------------------------------- */
+/* Per-kernel timing (measurement support; no counterpart in the paper).   */
+/* ---------------------------------------------------------------------- */
+
+/* Kernel slots of compton_kernel_times. */
+typedef enum compton_kernel_slot {
+    COMPTON_K_COUNT = 0,   /* histogram and order check                    */
+    COMPTON_K_SCAN = 1,    /* the three scan kernels together              */
+    COMPTON_K_PLACE = 2,   /* keyed placement (shuffled input)             */
+    COMPTON_K_SORT = 3,    /* per-cell sort and sorted copy                */
+    COMPTON_K_PROB = 4,    /* probability and Bernoulli trial of all pairs */
+    COMPTON_K_COLLIDE = 5, /* collisions of the accepted pairs             */
+    COMPTON_K_MLP = 6,     /* surrogate network forward                    */
+    COMPTON_N_TIMED = 7
+} compton_kernel_slot;
+
+/* enable != 0: from now on every kernel launch of the slots above records a
+ * CUDA event pair on its own stream (the last 64 launches per slot are kept)
+ * and the counts restart from zero; enable == 0 stops recording.  The events
+ * are created on the first enable.  Synchronous.  ECUDA if they cannot be
+ * created. */
+compton_status compton_kernel_timing(struct compton_ctx* ctx, int32_t enable);
+
+/* Wait for the recorded events and write, per slot, the summed device time
+ * of the kept launches in ms (ms_out_host[COMPTON_N_TIMED]) and their number
+ * (launches_out_host[COMPTON_N_TIMED]).  EINVAL if timing was never enabled. */
+compton_status compton_kernel_times(struct compton_ctx* ctx, double* ms_out_host, int64_t* launches_out_host);
+
 /* Self-test of the give-up path of the bounded device waits (every wait of
  * the tensor-core kernels is limited in time; on expiry the kernel records a
  * timeout, frees its tensor memory and returns instead of hanging): one

@@ -366,6 +366,26 @@ def compton_mlp_balance_weights(ctx: int, r, edges, w_out, stream=None) -> None:
            "compton_mlp_balance_weights", ctx)
 
 
+KERNEL_SLOTS = ("k_count", "k_scan", "k_place", "k_sort_gather", "k_pair_prob", "k_collide", "k_mlp")
+
+SIGNATURES["compton_kernel_timing"] = (c_i32, [c_p, c_i32])
+SIGNATURES["compton_kernel_times"] = (c_i32, [c_p, c_p, c_p])
+
+
+def compton_kernel_timing(ctx: int, enable: bool) -> None:
+    """Start (restarting the counts) or stop per-kernel event timing."""
+    _check(lib().compton_kernel_timing(c_p(ctx), 1 if enable else 0), "compton_kernel_timing", ctx)
+
+
+def compton_kernel_times(ctx: int) -> dict:
+    """Summed device time (ms) and launch count per kernel slot since timing
+    was enabled (the last 64 launches of each slot)."""
+    ms = (ctypes.c_double * len(KERNEL_SLOTS))()
+    n = (ctypes.c_int64 * len(KERNEL_SLOTS))()
+    _check(lib().compton_kernel_times(c_p(ctx), ms, n), "compton_kernel_times", ctx)
+    return {name: {"ms": ms[i], "launches": n[i]} for i, name in enumerate(KERNEL_SLOTS)}
+
+
 SIGNATURES["compton_selftest_wait"] = (c_i32, [c_p, c_u64, c_p])
 
 

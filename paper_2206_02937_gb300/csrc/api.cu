@@ -108,6 +108,11 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     size_t o_ci = cv.take<CellInfo>(C);
     size_t o_tc = cv.take<int32_t>(ctx->max_pair_tiles + 1);
     size_t o_np = cv.take<int64_t>(1);
+    ctx->accepted_cap = P > ((int64_t)1 << 20) ? P : ((int64_t)1 << 20);
+    size_t o_acc = cv.take<compton::AcceptedPair>(ctx->accepted_cap);
+    size_t o_nacc = cv.take<uint32_t>(1);
+    size_t o_cand = cv.take<compton::CandPair>(ctx->accepted_cap);
+    size_t o_ncand = cv.take<uint32_t>(1);
     size_t o_st = cv.take<compton::DeviceStats>(1);
     const size_t NP = compton::kMlpParams;
     size_t o_th = cv.take<float>(NP), o_gr = cv.take<float>(NP), o_am = cv.take<float>(NP),
@@ -146,6 +151,10 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     ctx->cinfo = reinterpret_cast<CellInfo*>(base + o_ci);
     ctx->tile_cell = reinterpret_cast<int32_t*>(base + o_tc);
     ctx->n_pairs = reinterpret_cast<int64_t*>(base + o_np);
+    ctx->accepted = reinterpret_cast<compton::AcceptedPair*>(base + o_acc);
+    ctx->n_accepted = reinterpret_cast<uint32_t*>(base + o_nacc);
+    ctx->cand = reinterpret_cast<compton::CandPair*>(base + o_cand);
+    ctx->n_cand = reinterpret_cast<uint32_t*>(base + o_ncand);
     ctx->stats = reinterpret_cast<compton::DeviceStats*>(base + o_st);
     compton::MlpDev& m = ctx->mlp;
     m.theta = reinterpret_cast<float*>(base + o_th);
@@ -188,8 +197,72 @@ compton_status compton_destroy(compton_ctx* ctx)
     cudaSetDevice(ctx->cfg.device);
     compton::serve_stop(ctx);
     cudaDeviceSynchronize();
+    if (ctx->timing) {
+        for (int s = 0; s < compton::kTimedSlots; ++s)
+            for (int k = 0; k < compton::kTimingRing; ++k) {
+                cudaEventDestroy(ctx->timing->ev[s][k][0]);
+                cudaEventDestroy(ctx->timing->ev[s][k][1]);
+            }
+        delete ctx->timing;
+    }
     if (ctx->arena) cudaFree(ctx->arena);
     delete ctx;
+    return COMPTON_OK;
+}
+
+compton_status compton_kernel_timing(compton_ctx* ctx, int32_t enable)
+{
+    if (!ctx) return COMPTON_EINVAL;
+    COMPTON_CUDA_TRY(ctx, cudaSetDevice(ctx->cfg.device));
+    if (!enable) {
+        if (ctx->timing) ctx->timing->on = false;
+        return COMPTON_OK;
+    }
+    if (!ctx->timing) {
+        compton::KernelTiming* T = new (std::nothrow) compton::KernelTiming();
+        if (!T) return COMPTON_ENOMEM;
+        for (int s = 0; s < compton::kTimedSlots; ++s)
+            for (int k = 0; k < compton::kTimingRing; ++k)
+                for (int j = 0; j < 2; ++j) {
+                    const cudaError_t e = cudaEventCreate(&T->ev[s][k][j]);
+                    if (e != cudaSuccess) {
+                        for (int s2 = 0; s2 <= s; ++s2)
+                            for (int k2 = 0; k2 < compton::kTimingRing; ++k2)
+                                for (int j2 = 0; j2 < 2; ++j2) {
+                                    if (s2 == s && (k2 > k || (k2 == k && j2 >= j))) continue;
+                                    cudaEventDestroy(T->ev[s2][k2][j2]);
+                                }
+                        delete T;
+                        return compton::set_cuda_error(ctx, e, "cudaEventCreate");
+                    }
+                }
+        ctx->timing = T;
+    }
+    COMPTON_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    for (int s = 0; s < compton::kTimedSlots; ++s) ctx->timing->n[s] = 0;
+    ctx->timing->on = true;
+    return COMPTON_OK;
+}
+
+compton_status compton_kernel_times(compton_ctx* ctx, double* ms_out, int64_t* launches_out)
+{
+    if (!ctx || !ms_out || !launches_out) return COMPTON_EINVAL;
+    if (!ctx->timing) return COMPTON_EINVAL;
+    COMPTON_CUDA_TRY(ctx, cudaSetDevice(ctx->cfg.device));
+    const compton::KernelTiming& T = *ctx->timing;
+    for (int s = 0; s < compton::kTimedSlots; ++s) {
+        const int64_t kept = T.n[s] < compton::kTimingRing ? T.n[s] : compton::kTimingRing;
+        double sum = 0.0;
+        for (int64_t k = 0; k < kept; ++k) {
+            const int i = (int)((T.n[s] - kept + k) % compton::kTimingRing);
+            COMPTON_CUDA_TRY(ctx, cudaEventSynchronize(T.ev[s][i][1]));
+            float ms = 0.0f;
+            COMPTON_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, T.ev[s][i][0], T.ev[s][i][1]));
+            sum += ms;
+        }
+        ms_out[s] = sum;
+        launches_out[s] = kept;
+    }
     return COMPTON_OK;
 }
 

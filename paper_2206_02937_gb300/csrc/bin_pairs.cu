@@ -27,13 +27,27 @@ constexpr int kSortThreads = 512;
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // ---------------------------------------------------------------------------
-// Histogram and order check.  Each warp takes 128 consecutive particles (four
-// loads in flight per lane).  A group of 32 whose cells do not descend adds
-// one count per run of equal cells; any other group lets __match_any_sync
-// find the lanes with equal cells, and one lane per group adds the group
-// size.  unsorted[s] is set if a cell index descends or lies outside
-// [0, C): only then does the placement run.
+// Histogram and order check.  Every maximal run of equal in-range cell
+// indices at positions [i_s, i_e] adds i_e + 1 - i_s to its cell: the first
+// element adds -i_s, the last i_e + 1 (one atomic when they coincide).  This
+// counts any input exactly (a cell's runs sum to its size; int32 wrap-around
+// cancels), costs one atomic per element of shuffled input and two per run
+// of input in cell order.  Each thread takes four consecutive positions with
+// one vector load; the neighbours across threads come by shuffle.
+// unsorted[s] is set if a cell index descends or lies outside [0, C): only
+// then does the placement run.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int4 load_cells4(const int32_t* __restrict__ cell, int64_t i, int64_t n, bool vec)
+{
+    if (vec && i + 3 < n) return *reinterpret_cast<const int4*>(cell + i);  // 16-byte aligned: i % 4 == 0
+    int4 v = make_int4(-1, -1, -1, -1);
+    if (i < n) v.x = cell[i];
+    if (i + 1 < n) v.y = cell[i + 1];
+    if (i + 2 < n) v.z = cell[i + 2];
+    if (i + 3 < n) v.w = cell[i + 3];
+    return v;
+}
+
 __global__ void k_count(const int32_t* __restrict__ cell_e, int64_t n_e, const int32_t* __restrict__ cell_g,
                         int64_t n_g, int64_t C, int32_t* __restrict__ count_e, int32_t* __restrict__ count_g,
                         int32_t* __restrict__ unsorted, DeviceStats* stats)
@@ -43,46 +57,31 @@ __global__ void k_count(const int32_t* __restrict__ cell_e, int64_t n_e, const i
     const int64_t n = s == 0 ? n_e : n_g;
     int32_t* __restrict__ count = s == 0 ? count_e : count_g;
     const unsigned lane = lane_id();
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+    const int64_t n_round = (n + 127) / 128 * 128;  // whole warps in every iteration
+    const bool vec = (reinterpret_cast<uintptr_t>(cell) & 15u) == 0;
     bool disorder = false, bad = false;
-    for (int64_t base = warp * 128; base < n; base += n_warps * 128) {
-        int32_t v[4];
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i0 < n_round; i0 += stride) {
+        const int4 q = load_cells4(cell, i0, n, vec);
+        const int32_t v[4] = {q.x, q.y, q.z, q.w};
+        int32_t prev = __shfl_up_sync(0xffffffffu, v[3], 1);
+        int32_t next = __shfl_down_sync(0xffffffffu, v[0], 1);
+        if (lane == 0) prev = (i0 > 0 && i0 - 1 < n) ? cell[i0 - 1] : -1;
+        if (lane == 31) next = i0 + 4 < n ? cell[i0 + 4] : -1;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int64_t i = base + 32 * k + lane;
-            v[k] = i < n ? cell[i] : 0;
-        }
-        int32_t prev_last = 0;
-        if (lane == 0 && base > 0) prev_last = cell[base - 1];
-        prev_last = __shfl_sync(0xffffffffu, prev_last, 0);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int64_t i = base + 32 * k + lane;
-            const bool live = i < n;
-            const bool ok = live && v[k] >= 0 && (int64_t)v[k] < C;
-            bad |= live && !ok;
-            int32_t prev = __shfl_up_sync(0xffffffffu, v[k], 1);
-            if (lane == 0) prev = prev_last;
-            const bool desc = live && i > 0 && prev > v[k];
-            disorder |= desc;
-            prev_last = __shfl_sync(0xffffffffu, v[k], 31);
-            const int c = ok ? v[k] : -1;
-            if (__all_sync(0xffffffffu, !desc && (ok || !live))) {
-                // ordered group: runs of equal cells are runs of lanes
-                const unsigned head = __ballot_sync(0xffffffffu, ok && (lane == 0 || prev != v[k]));
-                if (ok && ((head >> lane) & 1u)) {
-                    const unsigned later = head & ~((2u << lane) - 1u);
-                    const int end = later ? __ffs(later) - 1 : 32;
-                    int len = end - (int)lane;
-                    const int64_t rem = n - (i - lane);  // live lanes in this group
-                    if (rem < 32 && end > rem) len = (int)rem - (int)lane;
-                    atomicAdd(&count[c], len);
-                }
-            } else {
-                const unsigned peers = __match_any_sync(0xffffffffu, c);
-                if (c >= 0 && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&count[c], __popc(peers));
-            }
+        for (int j = 0; j < 4; ++j) {
+            const int64_t i = i0 + j;
+            if (i >= n) break;
+            const int32_t c = v[j];
+            const int32_t pc = j == 0 ? prev : v[j - 1];
+            const int32_t nc = j == 3 ? next : v[j + 1];
+            const bool ok = c >= 0 && (int64_t)c < C;
+            bad |= !ok;
+            disorder |= i > 0 && pc > c;
+            const bool first = ok && (i == 0 || pc != c);
+            const bool last = ok && (i + 1 == n || nc != c);
+            if (first || last)
+                atomicAdd(&count[c], (last ? (int32_t)(i + 1) : 0) - (first ? (int32_t)i : 0));
         }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&stats->error_flags, (unsigned long long)kErrCellRange);
@@ -497,13 +496,46 @@ __device__ __forceinline__ void sort_tile_block(const SortGatherArgs& g, int s, 
     }
     for (int i = tid; i < R; i += kSortThreads) m.cnt[i] = 0;
     __syncthreads();
-    // keys, momenta, bucket histogram
-    for (int i = tid; i < R; i += kSortThreads) {
-        const uint32_t key = fetch_elem(t, m, o0 + i, i);
-        const uint32_t cm = m.cmap[i];
-        const int b = (int)(cm & 0xffffu) + bucket_of(key, (int)(cm >> 16));
-        m.bidx[i] = (uint16_t)b;
-        atomicAdd(&m.cnt[b], 1);
+    // keys, momenta, bucket histogram; the loads of a thread's elements are
+    // all issued before the first key is drawn
+    constexpr int kPer = (kSortCap + kSortThreads - 1) / kSortThreads;
+    uint32_t key[kPer];
+    if (t.rec) {
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = tid + k * kSortThreads;
+            if (i < R) key[k] = fetch_elem(t, m, o0 + i, i);
+        }
+    } else {
+        uint32_t pid[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = tid + k * kSortThreads;
+            if (i < R) {
+                cp_async4(&m.us[0][i], t.u[0] + o0 + i);
+                cp_async4(&m.us[1][i], t.u[1] + o0 + i);
+                cp_async4(&m.us[2][i], t.u[2] + o0 + i);
+                pid[k] = t.id[o0 + i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = tid + k * kSortThreads;
+            if (i < R) {
+                key[k] = draw(t.seed, t.step, t.stream, pid[k]).r0;
+                m.key64[i] = ((uint64_t)key[k] << 32) | pid[k];
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int i = tid + k * kSortThreads;
+        if (i < R) {
+            const uint32_t cm = m.cmap[i];
+            const int b = (int)(cm & 0xffffu) + bucket_of(key[k], (int)(cm >> 16));
+            m.bidx[i] = (uint16_t)b;
+            atomicAdd(&m.cnt[b], 1);
+        }
     }
     __syncthreads();
     block_scan_counts(m.cnt, R);
@@ -541,60 +573,6 @@ __device__ __forceinline__ void sort_tile_block(const SortGatherArgs& g, int s, 
         g.out_u[s][2][go] = m.us[2][i];
         g.out_id[s][go] = (uint32_t)m.key64[i];
     }
-}
-
-// One cell of n <= kSortCap particles (tile positions [0, n), global o ...)
-// sorted by one warp with the same bucket method, written directly.
-__device__ __forceinline__ void sort_cell_warp(const SortGatherArgs& g, int s, const SortSrc& t, const SortSmem& m,
-                                               int64_t o, int n, int32_t c)
-{
-    const int lane = (int)lane_id();
-    for (int j = lane; j < n; j += 32) m.cnt[j] = 0;
-    __syncwarp();
-    for (int j = lane; j < n; j += 32) {
-        const uint32_t key = fetch_elem(t, m, o + j, j);
-        atomicAdd(&m.cnt[bucket_of(key, n)], 1);
-        g.out_cell[s][o + j] = c;
-    }
-    __syncwarp();
-    int carry = 0;
-    for (int base = 0; base < n; base += 32) {
-        const int j = base + lane;
-        const int v = j < n ? m.cnt[j] : 0;
-        int inc = v;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int x = __shfl_up_sync(0xffffffffu, inc, d);
-            if (lane >= d) inc += x;
-        }
-        if (j < n) m.cnt[j] = carry + inc - v;
-        carry += __shfl_sync(0xffffffffu, inc, 31);
-    }
-    __syncwarp();
-    for (int j = lane; j < n; j += 32) {
-        const int pos = atomicAdd(&m.cnt[bucket_of((uint32_t)(m.key64[j] >> 32), n)], 1);
-        m.ptmp[pos] = (uint16_t)j;
-    }
-    cp_async_wait_all();
-    __syncwarp();
-    for (int j = lane; j < n; j += 32) {
-        const uint64_t kj = m.key64[j];
-        const int b = bucket_of((uint32_t)(kj >> 32), n);
-        const int lo = b == 0 ? 0 : m.cnt[b - 1];
-        const int hi = m.cnt[b];
-        int fin = lo;
-        if (hi - lo > 1)
-            for (int q = lo; q < hi; ++q) {
-                const int jj = m.ptmp[q];
-                fin += before64(m.key64[jj], jj, kj, j);
-            }
-        const int64_t go = o + fin;
-        g.out_u[s][0][go] = m.us[0][j];
-        g.out_u[s][1][go] = m.us[1][j];
-        g.out_u[s][2][go] = m.us[2][j];
-        g.out_id[s][go] = (uint32_t)kj;
-    }
-    __syncwarp();
 }
 
 // A cell larger than the shared-memory capacity: records in global memory
@@ -667,18 +645,22 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort_gather(SortGatherArgs 
         sort_tile_block(g, s, t, m, c0, c1, o0, (int)R);
         return;
     }
-    // A cell range larger than shared memory: cell by cell, each at the start
-    // of the shared buffers (warp 0), or in global memory (the block).
-    for (int64_t c = c0; c < c1; ++c) {
+    // A cell range larger than shared memory: runs of whole cells that fit
+    // are sorted block-wide one after another; a cell above the capacity
+    // alone is ranked in global memory.
+    for (int64_t c = c0; c < c1;) {
         const int64_t o = off[c];
-        const int64_t n = (int64_t)off[c + 1] - o;
-        if (n <= 0) continue;
-        if (n <= kSortCap) {
-            if (threadIdx.x < 32) sort_cell_warp(g, s, t, m, o, (int)n, (int32_t)c);
-        } else {
+        if ((int64_t)off[c + 1] - o > kSortCap) {
             __syncthreads();
-            sort_giant_cell(g, s, t, o, n, (int32_t)c);
+            sort_giant_cell(g, s, t, o, (int64_t)off[c + 1] - o, (int32_t)c);
+            ++c;
+            continue;
         }
+        int64_t e = c + 1;
+        while (e < c1 && (int64_t)off[e + 1] - o <= kSortCap) ++e;
+        __syncthreads();
+        sort_tile_block(g, s, t, m, c, e, o, (int)((int64_t)off[e] - o));
+        c = e;
     }
 }
 
@@ -704,10 +686,14 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
     COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->unsorted, 0, 2 * sizeof(int32_t), stream));
 
     const int64_t nmax = ne > ng ? ne : ng;
-    const dim3 cgrid(grid_for((nmax + 127) / 128, 8, 152 * 8), 2);  // 8 warps per block, 128 particles per warp
-    k_count<<<cgrid, 256, 0, stream>>>(e_in->cell_dev, ne, g_in->cell_dev, ng, C, ctx->count[0], ctx->count[1],
-                                       ctx->unsorted, ctx->stats);
+    const dim3 cgrid(grid_for((nmax + 3) / 4, 256, 152 * 16), 2);  // four particles per thread
+    {
+        TimedScope ts_(ctx, COMPTON_K_COUNT, stream);
+        k_count<<<cgrid, 256, 0, stream>>>(e_in->cell_dev, ne, g_in->cell_dev, ng, C, ctx->count[0], ctx->count[1],
+                                           ctx->unsorted, ctx->stats);
+    }
     COMPTON_LAUNCH_CHECK(ctx, "k_count");
+    TimedScope scan_scope(ctx, COMPTON_K_SCAN, stream);
     k_scan_reduce<<<(unsigned)n_tiles, 256, 0, stream>>>(ctx->count[0], ctx->count[1], C, ctx->block_sums,
                                                          n_tiles);
     COMPTON_LAUNCH_CHECK(ctx, "k_scan_reduce");
@@ -735,6 +721,7 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
     sf.n_pairs = ctx->n_pairs;
     sf.w_over_v = ctx->cfg.w_over_v;
     k_scan_final<<<(unsigned)n_tiles, 256, 0, stream>>>(sf);
+    scan_scope.end();
     COMPTON_LAUNCH_CHECK(ctx, "k_scan_final");
 
     const dim3 pgrid(grid_for(nmax, 256, 152 * 16), 2);
@@ -756,7 +743,10 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
     pa.C = C;
     pa.seed = ctx->cfg.seed;
     pa.step = step;
-    k_place<<<pgrid, 256, 0, stream>>>(pa);
+    {
+        TimedScope ts_(ctx, COMPTON_K_PLACE, stream);
+        k_place<<<pgrid, 256, 0, stream>>>(pa);
+    }
     COMPTON_LAUNCH_CHECK(ctx, "k_place");
 
     if (nb_e + nb_g > 0) {
@@ -782,6 +772,7 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
         const int smem = (int)kSortSmem;
         COMPTON_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sort_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    smem));
+        TimedScope ts_(ctx, COMPTON_K_SORT, stream);
         k_sort_gather<<<(unsigned)(nb_e + nb_g), kSortThreads, smem, stream>>>(sg);
         COMPTON_LAUNCH_CHECK(ctx, "k_sort_gather");
     }

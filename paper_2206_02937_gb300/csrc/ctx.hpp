@@ -34,6 +34,29 @@ struct __align__(32) SortRec {
     uint32_t pad[3];
 };
 
+// A pair that passed its Bernoulli trial, waiting for its collision: sorted
+// electron and photon index, rest-frame photon energy (negative when the
+// probability came from the network), pair index (counter of its draws), and
+// both momenta as they were read (so the collision kernel reads the list
+// sequentially instead of the particle arrays at random).
+struct __align__(16) AcceptedPair {
+    int32_t ie, ig;
+    float x;
+    uint32_t p;
+    float u[3], k[3];
+    uint32_t pad[2];
+};
+
+// A pair whose uniform passed the probability bound P_b = 1 - exp(-2 n dt)
+// and whose probability must be evaluated: sorted electron and photon index,
+// pair density, its uniform u0, pair index.
+struct __align__(16) CandPair {
+    int32_t ie, ig;
+    float dens, u0;
+    uint32_t p;
+    uint32_t pad[3];
+};
+
 enum : unsigned { kErrCellRange = 1u, kErrCapacity = 2u, kErrTimeout = 4u };
 
 struct DeviceStats {
@@ -76,6 +99,16 @@ struct MlpDev {
 
 struct ServeEngine;
 
+// Optional per-kernel timing (compton_kernel_timing): every launch of a slot
+// records a CUDA event pair on its stream into a ring of kTimingRing pairs.
+constexpr int kTimedSlots = COMPTON_N_TIMED;
+constexpr int kTimingRing = 64;
+struct KernelTiming {
+    bool on = false;
+    cudaEvent_t ev[kTimedSlots][kTimingRing][2];
+    int64_t n[kTimedSlots];
+};
+
 }  // namespace compton
 
 struct compton_ctx {
@@ -94,6 +127,11 @@ struct compton_ctx {
     compton::CellInfo* cinfo = nullptr;          // [C]
     int32_t* tile_cell = nullptr;                // [max_pair_tiles+1]
     int64_t* n_pairs = nullptr;                  // device scalar
+    compton::AcceptedPair* accepted = nullptr;   // [accepted_cap] pairs that passed their trial
+    uint32_t* n_accepted = nullptr;              // device scalar
+    int64_t accepted_cap = 0;                    // max(max_particles, 2^20)
+    compton::CandPair* cand = nullptr;           // [accepted_cap] candidates of the surrogate modes
+    uint32_t* n_cand = nullptr;                  // device scalar
     compton::DeviceStats* stats = nullptr;       // device counters
     int64_t max_scan_tiles = 0, max_sort_tiles = 0, max_pair_tiles = 0;
     // surrogate network
@@ -103,6 +141,7 @@ struct compton_ctx {
     void* train_scratch = nullptr;  // inside the arena, sized by cfg.max_train_batch
     float* r_buf = nullptr;         // [max_particles] network output per pair (surrogate modes)
     compton::ServeEngine* serve = nullptr;  // continuous-batching engine (compton_serve_start)
+    compton::KernelTiming* timing = nullptr;  // per-kernel event pairs (compton_kernel_timing)
 };
 
 namespace compton {
@@ -128,6 +167,28 @@ inline compton_status set_cuda_error(compton_ctx* ctx, cudaError_t e, const char
         if (_e != cudaSuccess) return compton::set_cuda_error((ctx), _e, name); \
     } while (0)
 
+// Records an event pair around the launches made in its scope when kernel
+// timing is on (start now, stop when the scope ends).
+struct TimedScope {
+    cudaStream_t stream;
+    cudaEvent_t stop = nullptr;
+    TimedScope(compton_ctx* ctx, int slot, cudaStream_t s) : stream(s)
+    {
+        if (!ctx->timing || !ctx->timing->on) return;
+        KernelTiming& T = *ctx->timing;
+        const int k = (int)(T.n[slot] % kTimingRing);
+        if (cudaEventRecord(T.ev[slot][k][0], s) != cudaSuccess) return;
+        stop = T.ev[slot][k][1];
+        ++T.n[slot];
+    }
+    void end()
+    {
+        if (stop) cudaEventRecord(stop, stream);
+        stop = nullptr;
+    }
+    ~TimedScope() { end(); }
+};
+
 // Entry points implemented in the kernel files.
 compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, const compton_species* g_in,
                                 compton_species* e_out, compton_species* g_out, uint64_t step,
@@ -146,7 +207,7 @@ compton_status launch_sample_angle(compton_ctx* ctx, const float* x, const uint3
 compton_status mlp_repack(compton_ctx* ctx, cudaStream_t stream);
 compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                 const float* kx, const float* ky, const float* kz, int64_t n, compton_mode mode,
-                                float* r_out, cudaStream_t stream, bool binned = false);
+                                float* r_out, cudaStream_t stream, bool binned = false, bool candidates = false);
 size_t train_scratch_bytes(int64_t max_batch);
 compton_status launch_balance_weights(compton_ctx* ctx, const float* r, int64_t n, const float* edges_host,
                                       int n_bins, float* w_out, cudaStream_t stream);

@@ -38,8 +38,7 @@ constexpr int kTileM = 128;
 // shared-memory layout of the tensor-core kernels (base aligned to 1024 B)
 constexpr uint32_t kOffW = 0;                           // 4 weight tiles
 constexpr uint32_t kWTileBytes = 8192;                  // 64 rows x 128 B
-constexpr uint32_t kOffA0 = kOffW + 4 * kWTileBytes;    // layer-0 A tile (128 x 128 B)
-constexpr uint32_t kOffA = kOffA0 + 16384;              // hidden A tile
+constexpr uint32_t kOffA = kOffW + 4 * kWTileBytes;     // A tile (128 x 128 B): features, then activations
 constexpr uint32_t kOffBias = kOffA + 16384;            // 4 x 64 floats
 constexpr uint32_t kOffW4 = kOffBias + 1024;            // 64 floats
 constexpr uint32_t kOffScale = kOffW4 + 256;            // 8 floats
@@ -161,6 +160,9 @@ struct MlpArgs {
     const CellInfo* cinfo;
     const int32_t* tile_cell;
     const int64_t* n_pairs;
+    // candidate input (rows of the candidate list) when cand != nullptr
+    const CandPair* cand;
+    const uint32_t* n_cand;
 };
 
 // Electron and photon index of pair p of a binned pair list: the cell is
@@ -179,11 +181,34 @@ __device__ __forceinline__ void binned_pair(const MlpArgs& a, int64_t p, int& ie
     ig = ci.g_start + j;
 }
 
+// Raw momenta of pair `row` (electron u, photon k), zeros past the end.
+__device__ __forceinline__ void load_pair_raw(const MlpArgs& a, int64_t row, int64_t n_rows, float* q)
+{
+    if (row >= n_rows) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) q[i] = 0.0f;
+        return;
+    }
+    int ie = (int)row, ig = (int)row;
+    if (a.cand) {
+        ie = a.cand[row].ie;
+        ig = a.cand[row].ig;
+    } else if (a.cinfo) {
+        binned_pair(a, row, ie, ig);
+    }
+    q[0] = a.u[0][ie];
+    q[1] = a.u[1][ie];
+    q[2] = a.u[2][ie];
+    q[3] = a.k[0][ig];
+    q[4] = a.k[1][ig];
+    q[5] = a.k[2][ig];
+}
+
 __device__ __forceinline__ void load_pair_features(const MlpArgs& a, int64_t row, float* f)
 {
-    int ie = (int)row, ig = (int)row;
-    if (a.cinfo) binned_pair(a, row, ie, ig);
-    features(a.m, a.u[0][ie], a.u[1][ie], a.u[2][ie], a.k[0][ig], a.k[1][ig], a.k[2][ig], f);
+    float q[6];
+    load_pair_raw(a, row, row + 1, q);
+    features(a.m, q[0], q[1], q[2], q[3], q[4], q[5], f);
 }
 
 template <bool kFp8>
@@ -192,7 +217,6 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* Wt = sm + kOffW;
-    uint8_t* A0 = sm + kOffA0;
     uint8_t* Ah = sm + kOffA;
     float* bias = reinterpret_cast<float*>(sm + kOffBias);
     float* w4 = reinterpret_cast<float*>(sm + kOffW4);
@@ -205,7 +229,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
     const MlpDev& m = a.m;
     const uint4* wsrc = reinterpret_cast<const uint4*>(kFp8 ? m.wfp8 : m.wbf16);
     for (int i = tid; i < (int)(4 * kWTileBytes / 16); i += kMlpThreads) reinterpret_cast<uint4*>(Wt)[i] = wsrc[i];
-    for (int i = tid; i < 2 * 16384 / 16; i += kMlpThreads) reinterpret_cast<uint4*>(A0)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < 16384 / 16; i += kMlpThreads) reinterpret_cast<uint4*>(Ah)[i] = make_uint4(0, 0, 0, 0);
     for (int i = tid; i < 256; i += kMlpThreads) bias[i] = m.bias[i];
     if (tid < 64) w4[tid] = m.w4[tid];
     if (tid < 4) {
@@ -228,25 +252,32 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
     const uint32_t tmem = *slot;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     constexpr uint32_t idesc = kFp8 ? tc::make_idesc(0, 0, 128, 64) : tc::make_idesc(1, 1, 128, 64);
-    const uint32_t sW = tc::smem_u32(Wt), sA0 = tc::smem_u32(A0), sA = tc::smem_u32(Ah);
+    const uint32_t sW = tc::smem_u32(Wt), sA = tc::smem_u32(Ah);
     uint32_t phase = 0;
     bool failed = false;
-    const int64_t n_rows = a.cinfo ? *a.n_pairs : a.n;
+    const int64_t n_rows = a.cand ? (int64_t)*a.n_cand : (a.cinfo ? *a.n_pairs : a.n);
     const int64_t n_tiles = (n_rows + kTileM - 1) / kTileM;
 
+    // the next tile's momenta are loaded while the current tile runs its layers
+    float raw[6];
+    load_pair_raw(a, (int64_t)blockIdx.x * kTileM + tid, n_rows, raw);
     for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
         const int64_t row = tile * kTileM + tid;
         float f[6] = {0, 0, 0, 0, 0, 0};
-        if (row < n_rows) load_pair_features(a, row, f);
+        if (row < n_rows) features(m, raw[0], raw[1], raw[2], raw[3], raw[4], raw[5], f);
+        if (tile + gridDim.x < n_tiles) load_pair_raw(a, (tile + gridDim.x) * kTileM + tid, n_rows, raw);
+        // layer-0 input: the 6 features in chunk 0 of the row, chunk 1 zeroed
+        // (the single K step of layer 0 reads bytes 0..31 of the row)
         if (kFp8) {
             const float s = scale[4];
-            *reinterpret_cast<uint4*>(A0 + tc::sw128_offset(tid, 0)) =
+            *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(tid, 0)) =
                 make_uint4(pack_e4m3x4(f[0] * s, f[1] * s, f[2] * s, f[3] * s), pack_e4m3x4(f[4] * s, f[5] * s, 0, 0),
                            0u, 0u);
         } else {
-            *reinterpret_cast<uint4*>(A0 + tc::sw128_offset(tid, 0)) =
+            *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(tid, 0)) =
                 make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]), 0u);
         }
+        *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(tid, 1)) = make_uint4(0u, 0u, 0u, 0u);
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         __syncthreads();
@@ -255,10 +286,12 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
         float acc_out = 0.0f;
         for (int l = 0; l < 4; ++l) {
             if (tid == 0) {
-                const uint64_t ad = tc::sw128_kmajor_desc(l == 0 ? sA0 : sA);
+                const uint64_t ad = tc::sw128_kmajor_desc(sA);
                 const uint64_t bd = tc::sw128_kmajor_desc(sW + l * kWTileBytes);
-#pragma unroll
-                for (int ks = 0; ks < 4; ++ks) {
+                // K steps of 32 bytes that hold data: layer 0 one (6 features),
+                // hidden layers 64 values = 4 steps in BF16, 2 in E4M3
+                const int n_ks = l == 0 ? 1 : (kFp8 ? 2 : 4);
+                for (int ks = 0; ks < n_ks; ++ks) {
                     // 32-byte K step inside the 128-byte swizzle atom
                     if (kFp8) tc::mma_f8(tmem, ad + 2 * ks, bd + 2 * ks, idesc, ks > 0);
                     else tc::mma_bf16(tmem, ad + 2 * ks, bd + 2 * ks, idesc, ks > 0);
@@ -355,7 +388,7 @@ __global__ void __launch_bounds__(kF32Threads) k_mlp_fp32(MlpArgs a)
     const float b4 = m.b4[0];
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * kF32Threads;
-    const int64_t n_rows = a.cinfo ? *a.n_pairs : a.n;
+    const int64_t n_rows = a.cand ? (int64_t)*a.n_cand : (a.cinfo ? *a.n_pairs : a.n);
     for (int64_t row = (int64_t)blockIdx.x * kF32Threads + tid; row < n_rows; row += stride) {
         float f[6];
         load_pair_features(a, row, f);
@@ -462,7 +495,7 @@ compton_status mlp_repack(compton_ctx* ctx, cudaStream_t stream)
 
 compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                 const float* kx, const float* ky, const float* kz, int64_t n, compton_mode mode,
-                                float* r_out, cudaStream_t stream, bool binned)
+                                float* r_out, cudaStream_t stream, bool binned, bool candidates)
 {
     MlpArgs a;
     a.m = ctx->mlp;
@@ -478,12 +511,17 @@ compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* 
     a.cinfo = binned ? ctx->cinfo : nullptr;
     a.tile_cell = binned ? ctx->tile_cell : nullptr;
     a.n_pairs = binned ? ctx->n_pairs : nullptr;
+    a.cand = candidates ? ctx->cand : nullptr;
+    a.n_cand = candidates ? ctx->n_cand : nullptr;
     if (mode == COMPTON_MODE_MLP_FP32) {
         const int smem = (4 * 4096 + 64 * kF32Threads + 256 + 64) * 4;
         COMPTON_CUDA_TRY(ctx, cudaFuncSetAttribute(k_mlp_fp32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    smem));
         const int grid = grid_persistent((const void*)k_mlp_fp32<false>, kF32Threads, smem, n, kF32Threads);
-        k_mlp_fp32<false><<<grid, kF32Threads, smem, stream>>>(a);
+        {
+            TimedScope ts_(ctx, COMPTON_K_MLP, stream);
+            k_mlp_fp32<false><<<grid, kF32Threads, smem, stream>>>(a);
+        }
         COMPTON_LAUNCH_CHECK(ctx, "k_mlp_fp32");
         return COMPTON_OK;
     }
@@ -491,8 +529,11 @@ compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* 
     const void* kern = fp8 ? (const void*)k_mlp_tc<true> : (const void*)k_mlp_tc<false>;
     COMPTON_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTc));
     const int grid = grid_persistent(kern, kMlpThreads, (int)kSmemTc, n, kTileM);
-    if (fp8) k_mlp_tc<true><<<grid, kMlpThreads, kSmemTc, stream>>>(a);
-    else k_mlp_tc<false><<<grid, kMlpThreads, kSmemTc, stream>>>(a);
+    {
+        TimedScope ts_(ctx, COMPTON_K_MLP, stream);
+        if (fp8) k_mlp_tc<true><<<grid, kMlpThreads, kSmemTc, stream>>>(a);
+        else k_mlp_tc<false><<<grid, kMlpThreads, kSmemTc, stream>>>(a);
+    }
     COMPTON_LAUNCH_CHECK(ctx, fp8 ? "k_mlp_tc<fp8>" : "k_mlp_tc<bf16>");
     return COMPTON_OK;
 }
@@ -537,6 +578,8 @@ compton_status launch_mlp_calibrate(compton_ctx* ctx, const float* ux, const flo
     a.cinfo = binned ? ctx->cinfo : nullptr;
     a.tile_cell = binned ? ctx->tile_cell : nullptr;
     a.n_pairs = binned ? ctx->n_pairs : nullptr;
+    a.cand = nullptr;
+    a.n_cand = nullptr;
     const int smem = (4 * 4096 + 64 * kF32Threads + 256 + 64) * 4;
     COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->mlp.amax, 0, 4 * sizeof(float), stream));
     COMPTON_CUDA_TRY(ctx, cudaFuncSetAttribute(k_mlp_fp32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

@@ -5,33 +5,34 @@
 // updated; Sec. 3.2: the probability comes from the Klein-Nishina cross
 // section in the lepton rest frame, carried back to the simulation frame).
 //
-// One fused, persistent kernel, software-pipelined over the tiles of 1024
-// pairs (256 threads x 4 consecutive pairs) that a CTA owns:
-//   * while tile t is computed, the particle data of tile t + G (G = grid
-//     size) is already in flight to shared memory (cp.async), and so is the
-//     window of CellInfo records of tile t + 2G: the loads of a tile never
-//     sit on the critical path of its own arithmetic;
-//   phase 1  every pair of tile t, from shared memory: x and v, sigma_KN,
-//            P = 1 - exp(-n dt s v), one Philox block per four pairs, the
-//            Bernoulli decision; accepted pairs are appended to a
-//            shared-memory queue that persists across tiles;
-//   phase 2  whenever the queue holds at least 256 entries, all 256 threads
-//            take one each: inverse-CDF angle, rest-frame boost and momentum
-//            update (FP32, or FP64 above the configured gamma eps), write-back
-//            of both momenta in place.  The last partial batch is drained
-//            after the final tile.
-// Accepted pairs are a few percent of all pairs; batching them keeps the
-// collision branch at full warp width instead of one live lane per warp.
+// Two kernels per step:
+//   k_pair_prob  one CTA per tile of 1024 pairs (256 threads x 4 consecutive
+//                pairs): the tile's CellInfo window staged in shared memory,
+//                each thread locates its pairs (binary search in the window,
+//                then forward steps), loads both momenta, draws one Philox
+//                block for the four Bernoulli uniforms and evaluates all four
+//                probabilities in straight-line FP32 (x and v without
+//                cancellation, sigma_KN from its series, 1 - exp(-n dt s v)),
+//                with a second pass for the rare pairs (FP64 invariants above
+//                the gamma threshold, closed-form sigma_KN above the series
+//                range).  Accepted pairs are appended to a list in global
+//                memory (warp-aggregated atomics).  No queue and little shared
+//                memory: many warps per SM hide the latency of the long
+//                arithmetic chains.
+//   k_collide    every accepted pair (a few percent of all pairs) at full
+//                warp width: inverse-CDF angle, rest-frame boost and momentum
+//                update (FP32, or FP64 above the configured gamma eps),
+//                write-back of both momenta in place.
+// Every draw is keyed by the pair index, so the order of the list does not
+// change any result.
 #include "ctx.hpp"
 #include "device_math.cuh"
 
 namespace compton {
 namespace {
 
-constexpr int kScatterThreads = 256;
-constexpr int kPairsPerThread = kPairsPerTile / kScatterThreads;
-constexpr int kQueueCap = kPairsPerTile + kScatterThreads;
-constexpr int kSlots = 8;  // staged per pair: ux uy uz kx ky kz, density (explicit pairs), network output
+constexpr int kProbThreads = 256;
+constexpr int kPairsPerThread = kPairsPerTile / kProbThreads;
 
 struct ScatterArgs {
     float* u[3];  // electron momenta (sorted species, or explicit pair list)
@@ -40,7 +41,7 @@ struct ScatterArgs {
     const int32_t* tile_cell;
     const int64_t* n_pairs;   // binned: device total
     const float* n_dens;      // explicit: density per pair
-    int64_t n_explicit;       // explicit: pair count
+    int64_t p_begin, p_end;   // explicit: the pairs of this launch
     float dt;
     uint64_t seed, step;
     float gamma64;
@@ -49,38 +50,11 @@ struct ScatterArgs {
     uint8_t* flag_out;
     DeviceStats* stats;
     const float* r_mlp;  // network output per pair (surrogate modes)
+    AcceptedPair* accepted;
+    uint32_t* n_accepted;
+    CandPair* cand;
+    uint32_t* n_cand;
 };
-
-// A pair accepted in phase 1 and waiting for its collision.  x < 0 marks a
-// pair whose probability came from the network (x is then recomputed).
-struct QEntry {
-    int32_t ie, ig;
-    float x;
-    uint32_t p;  // pair index: counter of its angle draws
-};
-
-struct ScatterSmem {
-    float* stage[2];   // [kSlots][kPairsPerTile] each
-    CellInfo* win[2];  // [kCellWindow] each
-    QEntry* queue;     // [kQueueCap]
-};
-constexpr size_t kStageBytes = sizeof(float) * kSlots * kPairsPerTile;
-constexpr size_t kScatterSmem = 2 * kStageBytes + 2 * sizeof(CellInfo) * kCellWindow + sizeof(QEntry) * kQueueCap;
-
-__device__ __forceinline__ void cp_async4(void* dst, const void* src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 __device__ __forceinline__ int find_cell(const CellInfo* win, int nwin, int64_t p)
 {
@@ -92,102 +66,10 @@ __device__ __forceinline__ int find_cell(const CellInfo* win, int nwin, int64_t 
     return lo;
 }
 
-// Where the four pairs of one thread in one tile live.
-struct PairLoc {
-    int32_t ie[kPairsPerThread], ig[kPairsPerThread];
-    float dens[kPairsPerThread];  // binned: the cell's density
-};
-
-// First and last cell of a binned tile.
-struct TileCells {
-    int32_t first, last;
-};
-
-__device__ __forceinline__ TileCells tile_cells(const ScatterArgs& a, int64_t tile)
+__device__ __forceinline__ void resolve(const ScatterArgs& a, const AcceptedPair& e)
 {
-    return TileCells{a.tile_cell[tile], a.tile_cell[tile + 1]};
-}
-
-// Window of CellInfo records of a tile to shared memory (when it fits).
-__device__ __forceinline__ void issue_window(const ScatterArgs& a, CellInfo* win, TileCells tc)
-{
-    const int nwin = tc.last - tc.first + 1;
-    if (nwin > kCellWindow) return;
-    for (int i = threadIdx.x; i < nwin; i += kScatterThreads) cp_async16(&win[i], &a.cinfo[tc.first + i]);
-}
-
-template <bool kBinned>
-__device__ __forceinline__ PairLoc locate(const ScatterArgs& a, const CellInfo* win, TileCells tc, int64_t pb,
-                                          int64_t total)
-{
-    PairLoc L;
-    if (!kBinned) {
-#pragma unroll
-        for (int r = 0; r < kPairsPerThread; ++r) {
-            L.ie[r] = (int32_t)(pb + r);
-            L.ig[r] = (int32_t)(pb + r);
-            L.dens[r] = 0.0f;
-        }
-        return L;
-    }
-    const int nwin = tc.last - tc.first + 1;
-    const CellInfo* cw = nwin <= kCellWindow ? win : a.cinfo + tc.first;
-    int ci_idx = pb < total ? find_cell(cw, nwin, pb) : 0;
-#pragma unroll
-    for (int r = 0; r < kPairsPerThread; ++r) {
-        const int64_t p = pb + r;
-        L.ie[r] = 0;
-        L.ig[r] = 0;
-        L.dens[r] = 0.0f;
-        if (p < total) {
-            while (ci_idx + 1 < nwin && (int64_t)cw[ci_idx + 1].pair_off <= p) ++ci_idx;
-            const CellInfo ci = cw[ci_idx];
-            const int j = (int)(p - ci.pair_off);
-            L.ie[r] = ci.e_start + j;
-            L.ig[r] = ci.g_start + j;
-            L.dens[r] = ci.dens;
-        }
-    }
-    return L;
-}
-
-// Four values of one array at indices i0..i3 to st[4 tid .. 4 tid + 3]: one
-// 16-byte copy when they are consecutive and aligned, else one per value.
-__device__ __forceinline__ void stage4(float* st, const float* src, int32_t i0, int32_t i1, int32_t i2, int32_t i3,
-                                       int nvalid)
-{
-    if (nvalid == kPairsPerThread && i3 == i0 + 3 && ((reinterpret_cast<uintptr_t>(src + i0) & 15u) == 0)) {
-        cp_async16(st, src + i0);
-        return;
-    }
-    cp_async4(st, src + i0);
-    if (nvalid > 1) cp_async4(st + 1, src + i1);
-    if (nvalid > 2) cp_async4(st + 2, src + i2);
-    if (nvalid > 3) cp_async4(st + 3, src + i3);
-}
-
-template <bool kBinned, bool kMlp>
-__device__ __forceinline__ void issue_pairs(const ScatterArgs& a, float* stage, const PairLoc& L, int64_t pb,
-                                            int64_t total)
-{
-    const int64_t left = total - pb;
-    const int nvalid = left <= 0 ? 0 : (left >= kPairsPerThread ? kPairsPerThread : (int)left);
-    if (nvalid == 0) return;
-    const int o = kPairsPerThread * threadIdx.x;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        stage4(stage + c * kPairsPerTile + o, a.u[c], L.ie[0], L.ie[1], L.ie[2], L.ie[3], nvalid);
-        stage4(stage + (3 + c) * kPairsPerTile + o, a.k[c], L.ig[0], L.ig[1], L.ig[2], L.ig[3], nvalid);
-    }
-    const int32_t p0 = (int32_t)pb;
-    if (!kBinned) stage4(stage + 6 * kPairsPerTile + o, a.n_dens, p0, p0 + 1, p0 + 2, p0 + 3, nvalid);
-    if (kMlp) stage4(stage + 7 * kPairsPerTile + o, a.r_mlp, p0, p0 + 1, p0 + 2, p0 + 3, nvalid);
-}
-
-__device__ __forceinline__ void resolve(const ScatterArgs& a, const QEntry& e)
-{
-    float ux = a.u[0][e.ie], uy = a.u[1][e.ie], uz = a.u[2][e.ie];
-    float kx = a.k[0][e.ig], ky = a.k[1][e.ig], kz = a.k[2][e.ig];
+    float ux = e.u[0], uy = e.u[1], uz = e.u[2];
+    float kx = e.k[0], ky = e.k[1], kz = e.k[2];
     float x = e.x;
     if (x < 0.0f) {  // probability came from the network: the collision needs x
         const Invariants inv = invariants_f32(ux, uy, uz, kx, ky, kz);
@@ -210,185 +92,312 @@ __device__ __forceinline__ void resolve(const ScatterArgs& a, const QEntry& e)
     a.k[2][e.ig] = kz;
 }
 
-// kMlp: the probability of in-range pairs is P = 1 - exp(-2 n dt r) with r
-// from the surrogate network (a.r_mlp, one value per pair); pairs outside the
-// network's training range (gamma > 1e3, eps outside [1e-4, 1]) use the
-// analytic probability and are counted as fallbacks.
-template <bool kBinned, bool kMlp>
-__global__ void __launch_bounds__(kScatterThreads, 2) k_scatter(ScatterArgs a)
+// The analytic probability of one pair and its rest-frame energy x; for
+// electrons above the FP64 threshold the invariants are recomputed in FP64.
+__device__ __forceinline__ float analytic_P(const ScatterArgs& a, float ux, float uy, float uz, float kx, float ky,
+                                           float kz, float dens, float* x_out)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    ScatterSmem sm;
-    sm.stage[0] = reinterpret_cast<float*>(smem_raw);
-    sm.stage[1] = sm.stage[0] + kSlots * kPairsPerTile;
-    sm.win[0] = reinterpret_cast<CellInfo*>(sm.stage[1] + kSlots * kPairsPerTile);
-    sm.win[1] = sm.win[0] + kCellWindow;
-    sm.queue = reinterpret_cast<QEntry*>(sm.win[1] + kCellWindow);
-    __shared__ int qn;
-    __shared__ unsigned red_pairs, red_scat, red_fb;
+    const Invariants inv = invariants_f32(ux, uy, uz, kx, ky, kz);
+    float x = inv.x, v = inv.v;
+    if (inv.gamma > a.gamma64) invariants_f64(ux, uy, uz, kx, ky, kz, &x, &v);
+    *x_out = x;
+    return inv.eps > 0.0f ? one_minus_exp_neg(dens * a.dt * 0.375f * kn_F2(x) * v) : 0.0f;
+}
 
+// Probability, Bernoulli trial and list of accepted pairs of one tile of
+// 1024 pairs (256 threads x 4 consecutive pairs).
+//
+// Candidate filter: sigma_KN <= sigma_T and v = 1 - beta cos psi <= 2 bound
+// every pair's probability by P_b = 1 - exp(-2 n dt) (the P_max of the
+// No-Time-Counter method, Sec. 3.1), and the network output r <= 1 gives the
+// same bound in the surrogate modes.  A pair whose uniform u0 >= P_b cannot
+// collide, so only the candidates u0 < P_b (a fraction ~2 n dt of the pairs)
+// load their momenta and evaluate P; the decision u0 < P is the one the full
+// evaluation would take, bit for bit.  With prob_out requested every pair is
+// evaluated.
+//
+// Phase A (all pairs): locate each pair's cell in the tile's CellInfo window
+// (binary search, then forward steps), draw one Philox block for the four
+// Bernoulli uniforms, test u0 < P_b and append the candidates to the warp's
+// shared-memory list.  Phase B (candidates, one per lane): load both momenta,
+// evaluate P (FP32 invariants and series sigma_KN; FP64 invariants above the
+// gamma threshold, closed-form sigma_KN above the series range; or the
+// network output), decide, append the accepted pairs to the global list
+// (warp-aggregated atomics).
+constexpr int kCandPerWarp = 32 * kPairsPerThread;
+
+struct Cand {
+    int32_t ie, ig;
+    float dens, u0;
+    uint32_t p;
+};
+
+template <bool kBinned>
+__global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
+{
+    __shared__ CellInfo win[kCellWindow];
+    __shared__ Cand cand[kProbThreads / 32][kCandPerWarp];
+    __shared__ unsigned red[3];
     const int tid = threadIdx.x;
-    const int64_t total = kBinned ? *a.n_pairs : a.n_explicit;
-    const int64_t n_tiles = (total + kPairsPerTile - 1) / kPairsPerTile;
-    const int64_t G = gridDim.x;
-    if (tid == 0) {
-        qn = 0;
-        red_pairs = 0;
-        red_scat = 0;
-        red_fb = 0;
+    const unsigned lane = tid & 31u;
+    const int w = tid >> 5;
+    const int64_t total = kBinned ? *a.n_pairs : a.p_end;
+    const int64_t tile = blockIdx.x;
+    const int64_t p0 = (kBinned ? 0 : a.p_begin) + tile * kPairsPerTile;
+    if (p0 >= total) return;
+    if (tid < 3) red[tid] = 0;
+    int c_first = 0, nwin = 0;
+    if (kBinned) {
+        c_first = a.tile_cell[tile];
+        nwin = a.tile_cell[tile + 1] - c_first + 1;
+        if (nwin <= kCellWindow)
+            for (int i = tid; i < nwin; i += kProbThreads) win[i] = a.cinfo[c_first + i];
     }
-    unsigned my_pairs = 0, my_scat = 0, my_fb = 0;
-
-    // prologue: window of the first tile, then its pairs and the second window
-    int64_t tile = blockIdx.x;
-    TileCells tc_next{0, 0}, tc_next2{0, 0};
-    PairLoc nx{};
-    if (tile < n_tiles) {
-        if (kBinned) {
-            tc_next = tile_cells(a, tile);
-            issue_window(a, sm.win[0], tc_next);
-            cp_async_commit();
-            cp_async_wait_all();
-        }
-        __syncthreads();
-        const int64_t pb = tile * kPairsPerTile + (int64_t)tid * kPairsPerThread;
-        nx = locate<kBinned>(a, sm.win[0], tc_next, pb, total);
-        issue_pairs<kBinned, kMlp>(a, sm.stage[0], nx, pb, total);
-        if (kBinned && tile + G < n_tiles) {
-            tc_next2 = tile_cells(a, tile + G);
-            issue_window(a, sm.win[1], tc_next2);
-        }
-        cp_async_commit();
-    }
-
-    for (int buf = 0; tile < n_tiles; tile += G, buf ^= 1) {
-        const PairLoc cur = nx;
-        const int64_t pb = tile * kPairsPerTile + (int64_t)tid * kPairsPerThread;
-        cp_async_wait_all();
-        __syncthreads();  // stage[buf] holds this tile, win[buf ^ 1] the next tile's window
-
-        // ---------------- prefetch: next tile's pairs, window after it ----------------
-        const int64_t tn = tile + G;
-        if (tn < n_tiles) {
-            const int64_t pbn = tn * kPairsPerTile + (int64_t)tid * kPairsPerThread;
-            nx = locate<kBinned>(a, sm.win[buf ^ 1], tc_next2, pbn, total);
-            issue_pairs<kBinned, kMlp>(a, sm.stage[buf ^ 1], nx, pbn, total);
-            if (kBinned && tn + G < n_tiles) {
-                tc_next2 = tile_cells(a, tn + G);
-                issue_window(a, sm.win[buf], tc_next2);
-            }
-        }
-        cp_async_commit();
-
-        // ---------------- phase 1: every pair of the tile ----------------
-        const float* st = sm.stage[buf];
-        const int o = kPairsPerThread * tid;
-        const float4 vux = *reinterpret_cast<const float4*>(st + 0 * kPairsPerTile + o);
-        const float4 vuy = *reinterpret_cast<const float4*>(st + 1 * kPairsPerTile + o);
-        const float4 vuz = *reinterpret_cast<const float4*>(st + 2 * kPairsPerTile + o);
-        const float4 vkx = *reinterpret_cast<const float4*>(st + 3 * kPairsPerTile + o);
-        const float4 vky = *reinterpret_cast<const float4*>(st + 4 * kPairsPerTile + o);
-        const float4 vkz = *reinterpret_cast<const float4*>(st + 5 * kPairsPerTile + o);
-        const float ux[4] = {vux.x, vux.y, vux.z, vux.w}, uy[4] = {vuy.x, vuy.y, vuy.z, vuy.w};
-        const float uz[4] = {vuz.x, vuz.y, vuz.z, vuz.w}, kx[4] = {vkx.x, vkx.y, vkx.z, vkx.w};
-        const float ky[4] = {vky.x, vky.y, vky.z, vky.w}, kz[4] = {vkz.x, vkz.y, vkz.z, vkz.w};
-        // the Bernoulli uniforms of the thread's four pairs: one Philox block
-        const Philox4 rnd4 = draw(a.seed, a.step, kStreamScatter, (uint32_t)(pb >> 2));
-        const uint32_t words[4] = {rnd4.r0, rnd4.r1, rnd4.r2, rnd4.r3};
-        float P[kPairsPerThread], xq[kPairsPerThread];
-        if (!kMlp) {
-            // common path, straight-line for all four pairs: FP32 invariants,
-            // series sigma_KN, probability
-            bool rare[kPairsPerThread];
-#pragma unroll
-            for (int r = 0; r < kPairsPerThread; ++r) {
-                const float dens = kBinned ? cur.dens[r] : st[6 * kPairsPerTile + o + r];
-                const Invariants inv = invariants_f32(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r]);
-                xq[r] = inv.x;
-                const float F2 = kn_F2_series(fminf(inv.x, 0.99f));
-                const float Pr = one_minus_exp_neg(dens * a.dt * 0.375f * F2 * inv.v);
-                P[r] = inv.eps > 0.0f ? Pr : 0.0f;
-                rare[r] = (inv.gamma > a.gamma64 || !(inv.x < 0.99f)) && pb + r < total;
-            }
-            // rare pairs: FP64 invariants above the gamma threshold, closed-form
-            // sigma_KN above the series range
-#pragma unroll
-            for (int r = 0; r < kPairsPerThread; ++r) {
-                if (!rare[r]) continue;
-                const float dens = kBinned ? cur.dens[r] : st[6 * kPairsPerTile + o + r];
-                const Invariants inv = invariants_f32(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r]);
-                float x = inv.x, v = inv.v;
-                if (inv.gamma > a.gamma64) invariants_f64(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r], &x, &v);
-                xq[r] = x;
-                P[r] = inv.eps > 0.0f ? one_minus_exp_neg(dens * a.dt * 0.375f * kn_F2(x) * v) : 0.0f;
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < kPairsPerThread; ++r) {
-                if (pb + r >= total) continue;
-                const float dens = kBinned ? cur.dens[r] : st[6 * kPairsPerTile + o + r];
-                const float g2 = fmaf(ux[r], ux[r], fmaf(uy[r], uy[r], fmaf(uz[r], uz[r], 1.0f)));
-                const float e2 = fmaf(kx[r], kx[r], fmaf(ky[r], ky[r], kz[r] * kz[r]));
-                if (g2 <= 1.0e6f && e2 >= 1.0e-8f && e2 <= 1.0f) {
-                    xq[r] = -1.0f;
-                    P[r] = one_minus_exp_neg(2.0f * dens * a.dt * st[7 * kPairsPerTile + o + r]);
-                } else {
-                    ++my_fb;
-                    const Invariants inv = invariants_f32(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r]);
-                    float x = inv.x, v = inv.v;
-                    if (inv.gamma > a.gamma64) invariants_f64(ux[r], uy[r], uz[r], kx[r], ky[r], kz[r], &x, &v);
-                    xq[r] = x;
-                    P[r] = inv.eps > 0.0f ? one_minus_exp_neg(dens * a.dt * 0.375f * kn_F2(x) * v) : 0.0f;
-                }
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < kPairsPerThread; ++r) {
-            const int64_t p = pb + r;
-            if (p >= total) continue;
-            const bool hit = u24_closed0(words[r]) < P[r];
-            if (a.prob_out) a.prob_out[p] = P[r];
-            if (a.flag_out) a.flag_out[p] = hit ? 1 : 0;
-            ++my_pairs;
-            if (hit) {
-                ++my_scat;
-                const int slot = atomicAdd(&qn, 1);
-                sm.queue[slot] = QEntry{cur.ie[r], cur.ig[r], xq[r], (uint32_t)p};
-            }
-        }
-        __syncthreads();
-
-        // ---------------- phase 2: full batches of accepted pairs ----------------
-        int nq = qn;
-        while (nq >= kScatterThreads) {
-            resolve(a, sm.queue[nq - kScatterThreads + tid]);
-            nq -= kScatterThreads;
-        }
-        __syncthreads();
-        if (tid == 0) qn = nq;
-    }
-    cp_async_wait_all();
     __syncthreads();
-    if (tid < qn) resolve(a, sm.queue[tid]);
 
-    // ---------------- counters ----------------
+    // ---------------- phase A: every pair ----------------
+    const int64_t pb = p0 + (int64_t)tid * kPairsPerThread;
+    const Philox4 rnd4 = draw(a.seed, a.step, kStreamScatter, (uint32_t)(pb >> 2));
+    const uint32_t words[4] = {rnd4.r0, rnd4.r1, rnd4.r2, rnd4.r3};
+    const bool all = a.prob_out != nullptr;
+    const CellInfo* cw = nwin <= kCellWindow ? win : a.cinfo + c_first;
+    int ci = (kBinned && pb < total) ? find_cell(cw, nwin, pb) : 0;
+    unsigned n_pairs = 0, n_hit = 0, n_fb = 0;
+    int nq = 0;
+#pragma unroll
+    for (int r = 0; r < kPairsPerThread; ++r) {
+        const int64_t p = pb + r;
+        const bool valid = p < total;
+        int ie = 0, ig = 0;
+        float dens = 0.0f;
+        if (valid) {
+            if (kBinned) {
+                while (ci + 1 < nwin && (int64_t)cw[ci + 1].pair_off <= p) ++ci;
+                const CellInfo c = cw[ci];
+                const int j = (int)(p - c.pair_off);
+                ie = c.e_start + j;
+                ig = c.g_start + j;
+                dens = c.dens;
+            } else {
+                ie = (int)p;
+                ig = (int)p;
+                dens = a.n_dens[p];
+            }
+            ++n_pairs;
+        }
+        const float u0 = u24_closed0(words[r]);
+        const bool is_cand = valid && (all || u0 < one_minus_exp_neg(2.0002f * dens * a.dt));
+        if (valid && !is_cand && a.flag_out) a.flag_out[p] = 0;
+        const unsigned m = __ballot_sync(0xffffffffu, is_cand);
+        if (is_cand) cand[w][nq + __popc(m & ((1u << lane) - 1u))] = Cand{ie, ig, dens, u0, (uint32_t)p};
+        nq += __popc(m);
+    }
+    __syncwarp();
+
+    // ---------------- phase B: candidates, one per lane ----------------
+    for (int base = 0; base < nq; base += 32) {
+        const int j = base + (int)lane;
+        bool hit = false;
+        Cand c{0, 0, 0.0f, 1.0f, 0u};
+        float x = -1.0f;
+        float ux = 0.0f, uy = 0.0f, uz = 0.0f, kx = 0.0f, ky = 0.0f, kz = 0.0f;
+        if (j < nq) {
+            c = cand[w][j];
+            ux = a.u[0][c.ie];
+            uy = a.u[1][c.ie];
+            uz = a.u[2][c.ie];
+            kx = a.k[0][c.ig];
+            ky = a.k[1][c.ig];
+            kz = a.k[2][c.ig];
+            const Invariants inv = invariants_f32(ux, uy, uz, kx, ky, kz);
+            x = inv.x;
+            float P;
+            if (inv.gamma > a.gamma64 || !(inv.x < 0.99f)) {
+                P = analytic_P(a, ux, uy, uz, kx, ky, kz, c.dens, &x);
+            } else {
+                const float Pr = one_minus_exp_neg(c.dens * a.dt * 0.375f * kn_F2_series(inv.x) * inv.v);
+                P = inv.eps > 0.0f ? Pr : 0.0f;
+            }
+            hit = c.u0 < P;
+            if (a.prob_out) a.prob_out[c.p] = P;
+            if (a.flag_out) a.flag_out[c.p] = hit ? 1 : 0;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (m) {
+            uint32_t at = 0;
+            if (lane == 0) at = atomicAdd(a.n_accepted, (uint32_t)__popc(m));
+            at = __shfl_sync(0xffffffffu, at, 0);
+            if (hit) {
+                a.accepted[at + __popc(m & ((1u << lane) - 1u))] =
+                    AcceptedPair{c.ie, c.ig, x, c.p, {ux, uy, uz}, {kx, ky, kz}, {0u, 0u}};
+                ++n_hit;
+            }
+        }
+    }
+
+    // counters: warp sums, then one atomic per block
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
-        my_pairs += __shfl_xor_sync(0xffffffffu, my_pairs, d);
-        my_scat += __shfl_xor_sync(0xffffffffu, my_scat, d);
-        my_fb += __shfl_xor_sync(0xffffffffu, my_fb, d);
+        n_pairs += __shfl_xor_sync(0xffffffffu, n_pairs, d);
+        n_hit += __shfl_xor_sync(0xffffffffu, n_hit, d);
+        n_fb += __shfl_xor_sync(0xffffffffu, n_fb, d);
     }
-    if ((tid & 31) == 0) {
-        atomicAdd(&red_pairs, my_pairs);
-        atomicAdd(&red_scat, my_scat);
-        atomicAdd(&red_fb, my_fb);
+    if (lane == 0) {
+        atomicAdd(&red[0], n_pairs);
+        atomicAdd(&red[1], n_hit);
     }
     __syncthreads();
-    if (tid == 0 && red_pairs) {
-        atomicAdd(&a.stats->pairs_tested, (unsigned long long)red_pairs);
-        atomicAdd(&a.stats->scatters, (unsigned long long)red_scat);
-        if (red_fb) atomicAdd(&a.stats->mlp_fallbacks, (unsigned long long)red_fb);
+    if (tid == 0) {
+        atomicAdd(&a.stats->pairs_tested, (unsigned long long)red[0]);
+        if (red[1]) atomicAdd(&a.stats->scatters, (unsigned long long)red[1]);
     }
+}
+
+// Surrogate modes, first kernel: phase A of k_pair_prob (locate, Bernoulli
+// uniform, bound test), with the candidates written to the context's
+// candidate list for the network.
+template <bool kBinned>
+__global__ void __launch_bounds__(kProbThreads, 4) k_cand(ScatterArgs a)
+{
+    __shared__ CellInfo win[kCellWindow];
+    __shared__ unsigned red_pairs;
+    const int tid = threadIdx.x;
+    const unsigned lane = tid & 31u;
+    const int64_t total = kBinned ? *a.n_pairs : a.p_end;
+    const int64_t tile = blockIdx.x;
+    const int64_t p0 = (kBinned ? 0 : a.p_begin) + tile * kPairsPerTile;
+    if (p0 >= total) return;
+    if (tid == 0) red_pairs = 0;
+    int c_first = 0, nwin = 0;
+    if (kBinned) {
+        c_first = a.tile_cell[tile];
+        nwin = a.tile_cell[tile + 1] - c_first + 1;
+        if (nwin <= kCellWindow)
+            for (int i = tid; i < nwin; i += kProbThreads) win[i] = a.cinfo[c_first + i];
+    }
+    __syncthreads();
+    const int64_t pb = p0 + (int64_t)tid * kPairsPerThread;
+    const Philox4 rnd4 = draw(a.seed, a.step, kStreamScatter, (uint32_t)(pb >> 2));
+    const uint32_t words[4] = {rnd4.r0, rnd4.r1, rnd4.r2, rnd4.r3};
+    const bool all = a.prob_out != nullptr;
+    const CellInfo* cw = nwin <= kCellWindow ? win : a.cinfo + c_first;
+    int ci = (kBinned && pb < total) ? find_cell(cw, nwin, pb) : 0;
+    unsigned n_pairs = 0;
+#pragma unroll
+    for (int r = 0; r < kPairsPerThread; ++r) {
+        const int64_t p = pb + r;
+        const bool valid = p < total;
+        int ie = 0, ig = 0;
+        float dens = 0.0f;
+        if (valid) {
+            if (kBinned) {
+                while (ci + 1 < nwin && (int64_t)cw[ci + 1].pair_off <= p) ++ci;
+                const CellInfo c = cw[ci];
+                const int j = (int)(p - c.pair_off);
+                ie = c.e_start + j;
+                ig = c.g_start + j;
+                dens = c.dens;
+            } else {
+                ie = (int)p;
+                ig = (int)p;
+                dens = a.n_dens[p];
+            }
+            ++n_pairs;
+        }
+        const float u0 = u24_closed0(words[r]);
+        const bool is_cand = valid && (all || u0 < one_minus_exp_neg(2.0002f * dens * a.dt));
+        if (valid && !is_cand && a.flag_out) a.flag_out[p] = 0;
+        const unsigned m = __ballot_sync(0xffffffffu, is_cand);
+        if (m) {
+            uint32_t at = 0;
+            if (lane == 0) at = atomicAdd(a.n_cand, (uint32_t)__popc(m));
+            at = __shfl_sync(0xffffffffu, at, 0);
+            if (is_cand) {
+                CandPair c;
+                c.ie = ie;
+                c.ig = ig;
+                c.dens = dens;
+                c.u0 = u0;
+                c.p = (uint32_t)p;
+                c.pad[0] = c.pad[1] = c.pad[2] = 0u;
+                a.cand[at + __popc(m & ((1u << lane) - 1u))] = c;
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) n_pairs += __shfl_xor_sync(0xffffffffu, n_pairs, d);
+    if (lane == 0) atomicAdd(&red_pairs, n_pairs);
+    __syncthreads();
+    if (tid == 0) atomicAdd(&a.stats->pairs_tested, (unsigned long long)red_pairs);
+}
+
+// Surrogate modes, third kernel: every candidate's probability from its
+// network output r (P = 1 - exp(-2 n dt r)) or, outside the network's
+// training range (gamma > 1e3, eps outside [1e-4, 1]), from the analytic
+// path (counted); the decision; accepted pairs to the list.
+__global__ void __launch_bounds__(256) k_decide(ScatterArgs a)
+{
+    const uint32_t n = *a.n_cand;
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned n_hit = 0, n_fb = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // warp-uniform trip count, so the ballots see whole warps
+    const uint32_t first = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    for (uint32_t base = first; base < n; base += stride) {
+        const uint32_t i = base + lane;
+        bool hit = false;
+        CandPair c{};
+        float x = -1.0f;
+        float ux = 0.0f, uy = 0.0f, uz = 0.0f, kx = 0.0f, ky = 0.0f, kz = 0.0f;
+        if (i < n) {
+            c = a.cand[i];
+            ux = a.u[0][c.ie];
+            uy = a.u[1][c.ie];
+            uz = a.u[2][c.ie];
+            kx = a.k[0][c.ig];
+            ky = a.k[1][c.ig];
+            kz = a.k[2][c.ig];
+            const float g2 = fmaf(ux, ux, fmaf(uy, uy, fmaf(uz, uz, 1.0f)));
+            const float e2 = fmaf(kx, kx, fmaf(ky, ky, kz * kz));
+            float P;
+            if (g2 <= 1.0e6f && e2 >= 1.0e-8f && e2 <= 1.0f) {
+                P = one_minus_exp_neg(2.0f * c.dens * a.dt * a.r_mlp[i]);
+            } else {
+                ++n_fb;
+                P = analytic_P(a, ux, uy, uz, kx, ky, kz, c.dens, &x);
+            }
+            hit = c.u0 < P;
+            if (a.prob_out) a.prob_out[c.p] = P;
+            if (a.flag_out) a.flag_out[c.p] = hit ? 1 : 0;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (m) {
+            uint32_t at = 0;
+            if (lane == 0) at = atomicAdd(a.n_accepted, (uint32_t)__popc(m));
+            at = __shfl_sync(0xffffffffu, at, 0);
+            if (hit) {
+                a.accepted[at + __popc(m & ((1u << lane) - 1u))] =
+                    AcceptedPair{c.ie, c.ig, x, c.p, {ux, uy, uz}, {kx, ky, kz}, {0u, 0u}};
+                ++n_hit;
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        n_hit += __shfl_xor_sync(0xffffffffu, n_hit, d);
+        n_fb += __shfl_xor_sync(0xffffffffu, n_fb, d);
+    }
+    if (lane == 0) {
+        if (n_hit) atomicAdd(&a.stats->scatters, (unsigned long long)n_hit);
+        if (n_fb) atomicAdd(&a.stats->mlp_fallbacks, (unsigned long long)n_fb);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_collide(ScatterArgs a)
+{
+    const uint32_t n = *a.n_accepted;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) resolve(a, a.accepted[i]);
 }
 
 // r = s(x) v / 2 per explicit pair.
@@ -419,26 +428,65 @@ __global__ void k_sample_angle(const float* __restrict__ x, const uint32_t* __re
     }
 }
 
-// Persistent grid: every CTA that fits on the SMs at once (the kernel's
-// dynamic shared memory is set on each call, so any current device works),
-// capped by the tile count.  Returns 0 if the attributes cannot be set.
-template <bool kBinned, bool kMlp>
-int persistent_grid(int64_t max_pairs)
+int collide_grid(int64_t max_accepted)
 {
-    const void* kern = (const void*)k_scatter<kBinned, kMlp>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem) != cudaSuccess ||
-        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
-        return 0;
-    int dev = 0, n_sm = 0, per_sm = 0;
+    int dev = 0, n_sm = 1;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm < 1) n_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kScatterThreads, kScatterSmem) != cudaSuccess)
-        per_sm = 1;
-    if (per_sm < 1) per_sm = 1;
-    const int64_t tiles = (max_pairs + kPairsPerTile - 1) / kPairsPerTile;
-    const int64_t full = (int64_t)per_sm * n_sm;
-    return (int)(tiles < 1 ? 1 : (tiles < full ? tiles : full));
+    const int64_t want = (max_accepted + 255) / 256;
+    const int64_t cap = (int64_t)n_sm * 8;
+    return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+void fill_common(ScatterArgs& a, compton_ctx* ctx, uint64_t seed, uint64_t step, float* prob_out, uint8_t* flag_out)
+{
+    a.dt = (float)ctx->cfg.dt;
+    a.seed = seed;
+    a.step = step;
+    a.gamma64 = ctx->cfg.gamma_fp64_threshold;
+    a.collide64_sq = ctx->cfg.collide_fp64_threshold * ctx->cfg.collide_fp64_threshold;
+    a.prob_out = prob_out;
+    a.flag_out = flag_out;
+    a.stats = ctx->stats;
+    a.r_mlp = ctx->r_buf;
+    a.accepted = ctx->accepted;
+    a.n_accepted = ctx->n_accepted;
+    a.cand = ctx->cand;
+    a.n_cand = ctx->n_cand;
+}
+
+// The step after the pair list is known: probability and trial of every
+// pair (plain: one kernel; surrogate: candidates, network, decisions), then
+// the collisions.  Tiles: pair tiles of this launch; rows: a host bound on
+// the pair count.
+template <bool kBinned>
+compton_status launch_step(compton_ctx* ctx, ScatterArgs& a, compton_mode mode, unsigned tiles, int64_t rows,
+                           cudaStream_t stream)
+{
+    COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->n_accepted, 0, sizeof(uint32_t), stream));
+    if (mode == COMPTON_MODE_PLAIN) {
+        TimedScope ts_(ctx, COMPTON_K_PROB, stream);
+        k_pair_prob<kBinned><<<tiles, kProbThreads, 0, stream>>>(a);
+    } else {
+        COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->n_cand, 0, sizeof(uint32_t), stream));
+        {
+            TimedScope ts_(ctx, COMPTON_K_PROB, stream);
+            k_cand<kBinned><<<tiles, kProbThreads, 0, stream>>>(a);
+        }
+        COMPTON_LAUNCH_CHECK(ctx, "k_cand");
+        compton_status st = launch_mlp_infer(ctx, a.u[0], a.u[1], a.u[2], a.k[0], a.k[1], a.k[2], rows, mode,
+                                             ctx->r_buf, stream, false, true);
+        if (st != COMPTON_OK) return st;
+        TimedScope ts_(ctx, COMPTON_K_PROB, stream);
+        k_decide<<<collide_grid(rows), 256, 0, stream>>>(a);
+    }
+    COMPTON_LAUNCH_CHECK(ctx, "k_pair_prob");
+    {
+        TimedScope ts_(ctx, COMPTON_K_COLLIDE, stream);
+        k_collide<<<collide_grid(rows), 256, 0, stream>>>(a);
+    }
+    COMPTON_LAUNCH_CHECK(ctx, "k_collide");
+    return COMPTON_OK;
 }
 
 }  // namespace
@@ -448,12 +496,8 @@ compton_status launch_scatter_binned(compton_ctx* ctx, compton_species* e, compt
                                      float* prob_out, uint8_t* flag_out, cudaStream_t stream)
 {
     if (pairs->max_pairs <= 0) return COMPTON_OK;
-    const bool mlp = mode != COMPTON_MODE_PLAIN;
-    if (mlp) {
-        compton_status st = launch_mlp_infer(ctx, e->ux_dev, e->uy_dev, e->uz_dev, g->ux_dev, g->uy_dev, g->uz_dev,
-                                             pairs->max_pairs, mode, ctx->r_buf, stream, true);
-        if (st != COMPTON_OK) return st;
-    }
+    if (pairs->max_pairs > ctx->accepted_cap) return COMPTON_ERANGE;
+    if (mode != COMPTON_MODE_PLAIN && pairs->max_pairs > ctx->cfg.max_particles) return COMPTON_ERANGE;
     ScatterArgs a;
     a.u[0] = e->ux_dev;
     a.u[1] = e->uy_dev;
@@ -465,34 +509,19 @@ compton_status launch_scatter_binned(compton_ctx* ctx, compton_species* e, compt
     a.tile_cell = ctx->tile_cell;
     a.n_pairs = ctx->n_pairs;
     a.n_dens = nullptr;
-    a.n_explicit = 0;
-    a.dt = (float)ctx->cfg.dt;
-    a.seed = ctx->cfg.seed;
-    a.step = step;
-    a.gamma64 = ctx->cfg.gamma_fp64_threshold;
-    a.collide64_sq = ctx->cfg.collide_fp64_threshold * ctx->cfg.collide_fp64_threshold;
-    a.prob_out = prob_out;
-    a.flag_out = flag_out;
-    a.stats = ctx->stats;
-    a.r_mlp = ctx->r_buf;
-    const int grid = mlp ? persistent_grid<true, true>(pairs->max_pairs) : persistent_grid<true, false>(pairs->max_pairs);
-    if (grid == 0) return set_cuda_error(ctx, cudaGetLastError(), "k_scatter<binned> attributes");
-    if (mlp) k_scatter<true, true><<<grid, kScatterThreads, kScatterSmem, stream>>>(a);
-    else k_scatter<true, false><<<grid, kScatterThreads, kScatterSmem, stream>>>(a);
-    COMPTON_LAUNCH_CHECK(ctx, "k_scatter<binned>");
-    return COMPTON_OK;
+    a.p_begin = 0;
+    a.p_end = 0;
+    fill_common(a, ctx, ctx->cfg.seed, step, prob_out, flag_out);
+    const unsigned tiles = (unsigned)((pairs->max_pairs + kPairsPerTile - 1) / kPairsPerTile);
+    return launch_step<true>(ctx, a, mode, tiles, pairs->max_pairs, stream);
 }
 
 compton_status launch_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, float* uz, float* kx, float* ky,
                                     float* kz, const float* n_dens, int64_t n, uint64_t seed, uint64_t step,
                                     compton_mode mode, float* prob_out, uint8_t* flag_out, cudaStream_t stream)
 {
-    const bool mlp = mode != COMPTON_MODE_PLAIN;
-    if (mlp) {
-        if (n > ctx->cfg.max_particles) return COMPTON_ERANGE;
-        compton_status st = launch_mlp_infer(ctx, ux, uy, uz, kx, ky, kz, n, mode, ctx->r_buf, stream, false);
-        if (st != COMPTON_OK) return st;
-    }
+    if (n <= 0) return COMPTON_OK;
+    if (mode != COMPTON_MODE_PLAIN && n > ctx->cfg.max_particles) return COMPTON_ERANGE;
     ScatterArgs a;
     a.u[0] = ux;
     a.u[1] = uy;
@@ -504,21 +533,17 @@ compton_status launch_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, floa
     a.tile_cell = nullptr;
     a.n_pairs = nullptr;
     a.n_dens = n_dens;
-    a.n_explicit = n;
-    a.dt = (float)ctx->cfg.dt;
-    a.seed = seed;
-    a.step = step;
-    a.gamma64 = ctx->cfg.gamma_fp64_threshold;
-    a.collide64_sq = ctx->cfg.collide_fp64_threshold * ctx->cfg.collide_fp64_threshold;
-    a.prob_out = prob_out;
-    a.flag_out = flag_out;
-    a.stats = ctx->stats;
-    a.r_mlp = ctx->r_buf;
-    const int grid = mlp ? persistent_grid<false, true>(n) : persistent_grid<false, false>(n);
-    if (grid == 0) return set_cuda_error(ctx, cudaGetLastError(), "k_scatter<pairs> attributes");
-    if (mlp) k_scatter<false, true><<<grid, kScatterThreads, kScatterSmem, stream>>>(a);
-    else k_scatter<false, false><<<grid, kScatterThreads, kScatterSmem, stream>>>(a);
-    COMPTON_LAUNCH_CHECK(ctx, "k_scatter<pairs>");
+    fill_common(a, ctx, seed, step, prob_out, flag_out);
+    // chunks that fit the accepted-pair list (whole tiles, so the Philox
+    // blocks of four pairs never straddle two chunks)
+    const int64_t chunk = ctx->accepted_cap / kPairsPerTile * kPairsPerTile;
+    for (int64_t b = 0; b < n; b += chunk) {
+        a.p_begin = b;
+        a.p_end = b + chunk < n ? b + chunk : n;
+        const unsigned tiles = (unsigned)((a.p_end - a.p_begin + kPairsPerTile - 1) / kPairsPerTile);
+        const compton_status st = launch_step<false>(ctx, a, mode, tiles, a.p_end - a.p_begin, stream);
+        if (st != COMPTON_OK) return st;
+    }
     return COMPTON_OK;
 }
 

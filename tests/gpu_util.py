@@ -26,9 +26,13 @@ def species_np(s):
                 cell=s.cell.cpu().numpy(), id=s.id.cpu().numpy().view(np.uint32))
 
 
-def gpu_step(w, step=0, gamma64=1.0e3, want_prob=True):
+def gpu_step(w, step=0, gamma64=1.0e3, want_prob=True, want_flag=None):
     """bin_pairs + scatter_step of workload w on cuda:0.  Returns host copies
-    of the sorted species before and after the scatter, P, flags, offsets."""
+    of the sorted species before and after the scatter, P, flags, offsets.
+    want_flag defaults to want_prob; flags without P take the filtered path
+    (only pairs below the probability bound are evaluated)."""
+    if want_flag is None:
+        want_flag = want_prob
     torch = torch_cuda()
     import paper_2206_02937_gb300 as cg
     cg.build()
@@ -42,7 +46,7 @@ def gpu_step(w, step=0, gamma64=1.0e3, want_prob=True):
         before_e, before_g = species_np(e_out), species_np(g_out)
         mp = max(1, pairs.max_pairs)
         prob = torch.zeros(mp, dtype=torch.float32, device="cuda") if want_prob else None
-        flag = torch.zeros(mp, dtype=torch.uint8, device="cuda") if want_prob else None
+        flag = torch.zeros(mp, dtype=torch.uint8, device="cuda") if want_flag else None
         cg.compton_scatter_step(ctx, e_out, g_out, pairs, cg.MODE_PLAIN, step, prob, flag)
         torch.cuda.synchronize()
         st = cg.compton_check(ctx)
@@ -52,7 +56,7 @@ def gpu_step(w, step=0, gamma64=1.0e3, want_prob=True):
         off_g = _dev_array(torch, pairs.off_g_dev, w.n_cells + 1)
         out = dict(before_e=before_e, before_g=before_g, after_e=species_np(e_out), after_g=species_np(g_out),
                    P=prob.cpu().numpy()[:n_pairs] if want_prob else None,
-                   flag=flag.cpu().numpy()[:n_pairs] if want_prob else None,
+                   flag=flag.cpu().numpy()[:n_pairs] if want_flag else None,
                    off_e=off_e, off_g=off_g, n_pairs=n_pairs, stats=stats, check=st)
     finally:
         cg.compton_destroy(ctx)

@@ -84,3 +84,35 @@ def test_surrogate_scatter_matches_network_and_oracle(mode_name):
         ka = np.array([ag[c][ig[q]] for c in ("ux", "uy", "uz")], dtype=np.float64)
         assert np.linalg.norm(ua - uo) <= 1e-5 * scale[q]
         assert np.linalg.norm(ka - ko) <= 1e-5 * scale[q]
+
+
+def test_surrogate_filtered_equals_full_evaluation():
+    # the surrogate step without prob_out runs the network on the candidates
+    # only; flags and momenta equal those of the full evaluation
+    import paper_2206_02937_gb300 as cg
+    torch = torch_cuda()
+    cg.build()
+    w = _workload(seed=4)
+    out = {}
+    for want_p in (True, False):
+        ctx = cg.compton_init(w.n_cells, max(w.n_e, w.n_g), w.w_over_v, w.dt, w.seed)
+        try:
+            cg.compton_mlp_set_params(ctx, omlp.init_params(11).astype(np.float32))
+            e_in, g_in = to_species(torch, w.e), to_species(torch, w.g)
+            e_out, g_out = cg.Species.empty_like(e_in), cg.Species.empty_like(g_in)
+            pairs = cg.compton_bin_pairs(ctx, e_in, g_in, e_out, g_out, 2)
+            n = pairs.max_pairs
+            P = torch.zeros(n, device="cuda") if want_p else None
+            F = torch.zeros(n, dtype=torch.uint8, device="cuda")
+            cg.compton_get_stats(ctx, reset=True)
+            cg.compton_scatter_step(ctx, e_out, g_out, pairs, cg.MODE_MLP_BF16, 2, P, F)
+            st = cg.compton_get_stats(ctx, reset=True)
+            out[want_p] = (F.cpu().numpy(), species_np(e_out), species_np(g_out), st)
+        finally:
+            cg.compton_destroy(ctx)
+    (Fa, ea, ga, sa), (Fb, eb, gb, sb) = out[True], out[False]
+    assert np.array_equal(Fa, Fb) and Fa.sum() > 20
+    assert sa["scatters"] == sb["scatters"] and sa["pairs_tested"] == sb["pairs_tested"]
+    assert sb["mlp_fallbacks"] <= sa["mlp_fallbacks"]  # only candidates are looked at
+    for c in ("ux", "uy", "uz"):
+        assert np.array_equal(ea[c], eb[c]) and np.array_equal(ga[c], gb[c])

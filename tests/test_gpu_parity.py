@@ -254,3 +254,60 @@ def test_two_chained_steps():
                      {k: np.ascontiguousarray(v) for k, v in g1["after_e"].items()},
                      {k: np.ascontiguousarray(v) for k, v in g1["after_g"].items()})
     compare_with_oracle(w2, step=1)
+
+
+def test_unaligned_input_arrays():
+    # species arrays that start 4 bytes past an aligned address (views at
+    # offset 1): the histogram takes its scalar loads; the order must match
+    import paper_2206_02937_gb300 as cgl
+    from tests.gpu_util import species_np, torch_cuda
+    torch = torch_cuda()
+    cgl.build()
+    w = _presorted(_random_workload(16, n_cells=129, ppc_e=21, ppc_g=19))
+
+    def shifted(d):
+        def t(a):
+            base = torch.zeros(a.shape[0] + 1, dtype=torch.from_numpy(a).dtype, device="cuda")
+            base[1:] = torch.from_numpy(a).cuda()
+            return base[1:]
+        return cgl.Species(t(d["ux"]), t(d["uy"]), t(d["uz"]), t(d["cell"]), t(d["id"].view(np.int32)))
+
+    o = oracle.step(w.n_cells, w.w_over_v, w.dt, w.seed, 2, w.e, w.g)
+    ctx = cgl.compton_init(w.n_cells, max(w.n_e, w.n_g), w.w_over_v, w.dt, w.seed)
+    try:
+        e_in, g_in = shifted(w.e), shifted(w.g)
+        assert e_in.cell.data_ptr() % 16 != 0
+        e_out, g_out = cgl.Species.empty_like(e_in), cgl.Species.empty_like(g_in)
+        cgl.compton_bin_pairs(ctx, e_in, g_in, e_out, g_out, 2)
+        torch.cuda.synchronize()
+        assert cgl.compton_check(ctx) == cgl.COMPTON_OK
+        be, bg = species_np(e_out), species_np(g_out)
+    finally:
+        cgl.compton_destroy(ctx)
+    assert np.array_equal(be["id"], w.e["id"][o["e_perm"]])
+    assert np.array_equal(bg["id"], w.g["id"][o["g_perm"]])
+    assert np.array_equal(be["ux"], w.e["ux"][o["e_perm"]])
+
+
+@pytest.mark.parametrize("case", ["c1", "ragged", "gamma_fp64", "gamma_fp32"])
+def test_filtered_equals_full_evaluation(case):
+    # without prob_out only pairs whose uniform lies below the bound
+    # 1 - exp(-2 n dt) are evaluated; decisions and momenta must be those of
+    # the full evaluation (which the tests above hold to the oracle)
+    gamma64 = 1.0e3
+    if case == "c1":
+        w = wl.c1()
+    elif case == "ragged":
+        w = _random_workload(17, n_cells=700, ppc_e=44, ppc_g=40)
+    else:
+        w = _random_workload(18, 64, 32, 32, gamma_max=1e5, eps=(1e-4, 1e-2))
+        gamma64 = 0.0 if case == "gamma_fp64" else float("inf")
+    full = gpu_step(w, step=5, gamma64=gamma64)
+    flt = gpu_step(w, step=5, gamma64=gamma64, want_prob=False, want_flag=True)
+    bare = gpu_step(w, step=5, gamma64=gamma64, want_prob=False)
+    assert np.array_equal(flt["flag"], full["flag"])
+    assert flt["stats"]["scatters"] == full["stats"]["scatters"] == bare["stats"]["scatters"]
+    for g in (flt, bare):
+        for sp in ("after_e", "after_g"):
+            for c in ("ux", "uy", "uz"):
+                assert np.array_equal(g[sp][c], full[sp][c])
