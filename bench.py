@@ -288,6 +288,32 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # momentum read by the sort) + 20 (sorted write) = 40 B, both species
     bytes_bin = (w.n_e + w.n_g) * 40.0 + w.n_cells * 64.0
     achieved_bin = bytes_bin / (bin_avg * 1e-3) / 1e9
+    # No-Time-Counter collisions on the same binned particles (Sec. 3.1)
+    for _ in range(args.warmup):
+        pr = cg.compton_bin_pairs(ctx, bufs[step % 2][0], bufs[step % 2][1], bufs[(step + 1) % 2][0],
+                                  bufs[(step + 1) % 2][1], step, stream)
+        cg.compton_scatter_step_ntc(ctx, bufs[(step + 1) % 2][0], bufs[(step + 1) % 2][1], pr, step, stream)
+        step += 1
+    torch.cuda.synchronize()
+    cg.compton_get_stats(ctx, reset=True)
+    n0, n1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0.record(stream)
+    for _ in range(args.steps):
+        pr = cg.compton_bin_pairs(ctx, bufs[step % 2][0], bufs[step % 2][1], bufs[(step + 1) % 2][0],
+                                  bufs[(step + 1) % 2][1], step, stream)
+        cg.compton_scatter_step_ntc(ctx, bufs[(step + 1) % 2][0], bufs[(step + 1) % 2][1], pr, step, stream)
+        step += 1
+    n1.record(stream)
+    torch.cuda.synchronize()
+    ntc_ms = n0.elapsed_time(n1) / args.steps
+    st_ntc = cg.compton_get_stats(ctx, reset=True)
+    ntc = {"ms_per_step": ntc_ms, "candidates_per_step": st_ntc["pairs_tested"] / args.steps,
+           "collisions_per_step": st_ntc["scatters"] / args.steps,
+           "collisions_per_step_pairing": stats["scatters"] / args.steps,
+           "pairs_per_s_equivalent": pairs_per_step / (ntc_ms * 1e-3),
+           "note": "bin + NTC candidates per cell (one thread per cell, sequential in-cell updates); "
+                   "pairs_per_s_equivalent = the pairing method's pairs per step / NTC step time"}
+
     # binning of shuffled input: 4 (count) + 20 (placement read) + 20 (record
     # write) + 20 (record read) + 20 (sorted write) = 84 B per particle
     S = [species(w.e), species(w.g)]
@@ -348,6 +374,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "mlp": mlp,
+            "ntc": ntc,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
@@ -486,13 +513,41 @@ def run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step0, peaks):
     # sampling noise of the spectrum distance: two plain runs with other draws
     h_pl2, _ = scattered_spectrum(cg.MODE_PLAIN, torch.empty(n, device=dev), st=778)
     err["spectrum_L1_plain_vs_plain_other_draws"] = float((h_pl2 - h_pl).abs().sum())
+
+    # ablation: the same network trained on invariant inputs (ln x, ln v)
+    # instead of momenta; the momentum network is restored afterwards
+    blob = cg.compton_mlp_save(ctx)
+    cg.compton_mlp_set_features(ctx, cg.FEATURES_INVARIANTS)
+    train_inv = train_surrogate(cg, torch, ctx, dev, steps=args.train_steps, balanced=args.train_balanced)
+    P_iv = torch.empty(n, device=dev)
+    h_iv, n_iv = scattered_spectrum(mode, P_iv)
+    iv = P_iv[:np_pairs].double()
+    rel_iv = ((iv - pl).abs() / pl.clamp_min(1e-30))
+    for _ in range(args.warmup):
+        one(bufs[step % 2], bufs[(step + 1) % 2], step, mode)
+        step += 1
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one(bufs[step % 2], bufs[(step + 1) % 2], step, mode)
+        step += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    invariant = {"features": "ln(x)/8, ln(v)/8 from the FP32 invariants", "mode": "bf16",
+                 "ms_per_step": e0.elapsed_time(e1) / args.steps,
+                 "mean_rel_P": float(rel_iv.mean()), "median_rel_P": float(rel_iv.median()),
+                 "p99_rel_P": float(rel_iv[::4].float().quantile(0.99)),
+                 "collision_rate_ratio": n_iv / max(1, n_pl),
+                 "spectrum_L1": float((h_iv - h_pl).abs().sum()), "train": train_inv}
+    cg.compton_mlp_load(ctx, blob)
     return {"mode": "bf16", "metric": METRIC, "value": st["pairs_tested"] / (ms * 1e-3), "unit": UNIT,
             "ms_per_step": ms / args.steps, "fallback_fraction": st["mlp_fallbacks"] / max(1, st["pairs_tested"]),
             "network_kernel_ms": kern, "network_samples": n,
             "roofline": {"kernel": "k_mlp_tc<bf16>", "bound": "tensor", "achieved": achieved, "peak": peak_bf16,
                          "unit": "TFLOP/s", "frac": achieved / peak_bf16,
                          "note": "algorithmic FLOPs 2(6*64+3*64*64+64) per sample; peak: measured bf16 burst"},
-            "error_vs_plain": err, "train": train}
+            "error_vs_plain": err, "train": train, "invariant_features": invariant}
 
 
 def run_serving(args, cg, torch, ctx, src, dev):

@@ -60,6 +60,12 @@ typedef enum compton_mode {
     COMPTON_MODE_MLP_FP8 = 3   /* surrogate network, FP8 E4M3 operands      */
 } compton_mode;
 
+/* Inputs of the surrogate network (compton_mlp_set_features). */
+typedef enum compton_features {
+    COMPTON_FEATURES_MOMENTA = 0,   /* the particles' momenta (Sec. 3.2), sgnlog-scaled */
+    COMPTON_FEATURES_INVARIANTS = 1 /* ln(x)/8, ln(v)/8 of the pair, zeros elsewhere    */
+} compton_features;
+
 typedef struct compton_config {
     int64_t n_cells;             /* number of collision cells C (> 0)                          */
     int64_t max_particles;       /* capacity per species (sizes the sort scratch)              */
@@ -117,9 +123,10 @@ typedef struct compton_stats {
 /* Context                                                                 */
 /* ---------------------------------------------------------------------- */
 
-/* Create a context on cfg->device: allocates the scratch for binning
- * (about 68 bytes per particle of capacity: a 32-byte placement record per
- * species and the 4-byte network output; and 40 bytes per cell), the
+/* Create a context on cfg->device: allocates the scratch for binning and
+ * scattering (about 164 bytes per particle of capacity: a 32-byte placement
+ * record per species, a 48-byte entry each in the accepted-pair and the
+ * candidate lists, the 4-byte network output; and 40 bytes per cell), the
  * network buffers and the stats, all within cfg->mem_budget_bytes.
  * Synchronous.  EINVAL on bad sizes, ENOMEM if the budget or the device
  * cannot hold it. */
@@ -170,11 +177,15 @@ compton_status compton_bin_pairs(struct compton_ctx* ctx, const compton_species*
  * Per pair p (cell c, density n_c = max(N_e,c, N_g,c) * w_over_v):
  *   x = gamma eps - u.k, v = 1 - beta cos(psi) (rest-frame photon energy and
  *   flux factor), s = sigma_KN(x)/sigma_T, P = 1 - exp(-n_c dt s v);
- *   (r0, r1, r2, r3) = Philox4x32-10 at counter (p, step lo, 3, step hi);
- *   collide iff (r0 >> 8) 2^-24 < P; then t = 1 - cos(theta') from the
- *   Klein-Nishina angular distribution at u1 = ((r1 >> 8) + 1/2) 2^-24,
- *   phi = 2 pi (r2 >> 8) 2^-24, and the photon/electron momenta are replaced
- *   so that energy and momentum are conserved (update in FP64).
+ *   u0 = (w >> 8) 2^-24 with w word p mod 4 of Philox4x32-10 at counter
+ *   (p / 4, step lo, 3, step hi); collide iff u0 < P; then, from the block at
+ *   (p, step lo, 4, step hi), t = 1 - cos(theta') from the Klein-Nishina
+ *   angular distribution at u1 = ((r0 >> 8) + 1/2) 2^-24 and
+ *   phi = 2 pi (r1 >> 8) 2^-24, and both momenta are replaced so that energy
+ *   and momentum are conserved (FP64 where gamma eps exceeds the threshold).
+ * Only pairs with u0 < 1 - exp(-2 n_c dt), the bound of every pair's P, are
+ * evaluated (the decisions are those of evaluating all pairs); with
+ * prob_out_dev given, every pair is evaluated.
  * mode selects the analytic probability or the surrogate network.
  * prob_out_dev (nullable, float[max_pairs]) receives P per pair;
  * flag_out_dev (nullable, uint8[max_pairs]) receives the decision.
@@ -194,6 +205,21 @@ compton_status compton_scatter_pairs(struct compton_ctx* ctx, float* ux_dev, flo
                                      const float* n_dens_dev, int64_t n, uint64_t seed,
                                      uint64_t step, compton_mode mode, float* prob_out_dev,
                                      uint8_t* flag_out_dev, compton_stream_t stream);
+
+/* No-Time-Counter collisions (Sec. 3.1, second step; Bird 1989) of the
+ * binned species e, g (the e_out/g_out of the compton_bin_pairs call that
+ * produced `pairs`; only its cell offsets are used), in place.  Cell c with
+ * N_e, N_g > 0 draws N = floor(E + U) candidate pairs, E = N_e N_g w_over_v
+ * 2 dt (2 sigma_T c bounds sigma v), U from Philox at (c, step lo, 5,
+ * step hi); candidate j draws the block (c, step lo, 6 | j << 8, step hi):
+ * word 0 picks the electron e_start + floor(w0 N_e / 2^32), word 1 the
+ * photon, and the pair collides iff (w2 >> 8) 2^-24 < r = sigma_KN(x) v /
+ * (2 sigma_T); the collision uses word 3 for the angle and word 0 of block
+ * (c, step lo, 7 | j << 8, step hi) for the azimuth, and later candidates of
+ * the cell see the updated momenta.  The stats count candidates as pairs
+ * tested.  Analytic probability only. */
+compton_status compton_scatter_step_ntc(struct compton_ctx* ctx, compton_species* e, compton_species* g,
+                                        const compton_pairs* pairs, uint64_t step, compton_stream_t stream);
 
 /* Analytic target of the surrogate: r = s(x) (1 - beta cos psi) / 2 in [0, 1]
  * per pair, the probability normalised by its per-cell maximum
@@ -270,9 +296,19 @@ compton_status compton_mlp_balance_weights(struct compton_ctx* ctx, const float*
  * normalised by sum w), same layout as the parameters.  Synchronous. */
 compton_status compton_mlp_get_grad(struct compton_ctx* ctx, float* grad_host, int64_t n_params);
 
-/* Serialise the network (format "CMLP" version 1: header with the Adam step,
- * feature and activation scales, then parameters and both Adam moments) to
- * buf.  With buf NULL, *len receives the size needed; ERANGE if *len is too
+/* Select the network's inputs for every later inference, calibration and
+ * training step.  COMPTON_FEATURES_MOMENTA (the default) feeds the six
+ * sgnlog-scaled momentum components, as the paper feeds momenta (Sec. 3.2).
+ * COMPTON_FEATURES_INVARIANTS (no counterpart in the paper: an ablation of
+ * that choice) feeds f0 = ln(x)/8 and f1 = ln(v)/8, with x the photon energy
+ * in the electron rest frame and v = 1 - beta cos psi from the FP32
+ * invariants, and zeros in the other four inputs; the network must then be
+ * trained in that mode.  EINVAL for another value. */
+compton_status compton_mlp_set_features(struct compton_ctx* ctx, int32_t features);
+
+/* Serialise the network (format "CMLP" version 2: header with the Adam step,
+ * feature scales and mode, activation scales, then parameters and both Adam
+ * moments; version 1 blobs, without the mode, still load) to buf.  With buf NULL, *len receives the size needed; ERANGE if *len is too
  * small.  Synchronous. */
 compton_status compton_mlp_save(struct compton_ctx* ctx, void* buf, size_t* len);
 
@@ -376,7 +412,8 @@ typedef enum compton_kernel_slot {
     COMPTON_K_PROB = 4,    /* probability and Bernoulli trial of all pairs */
     COMPTON_K_COLLIDE = 5, /* collisions of the accepted pairs             */
     COMPTON_K_MLP = 6,     /* surrogate network forward                    */
-    COMPTON_N_TIMED = 7
+    COMPTON_K_NTC = 7,     /* No-Time-Counter candidates and collisions    */
+    COMPTON_N_TIMED = 8
 } compton_kernel_slot;
 
 /* enable != 0: from now on every kernel launch of the slots above records a

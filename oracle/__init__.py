@@ -87,6 +87,11 @@ def lib():
         L.or_pairs.restype = None
         L.or_ratio.argtypes = [i64, P, P, P, P, P, P, P]
         L.or_ratio.restype = None
+        L.or_ntc_step.argtypes = [i64, d, d, u64, u64,
+                                  i64, P, P, P, P, P,
+                                  i64, P, P, P, P, P,
+                                  P, P, P, P, P, P, P, P, P]
+        L.or_ntc_step.restype = i64
         _ = (i32,)
         _lib = L
     return _lib
@@ -250,6 +255,37 @@ def step(n_cells, w_over_v, dt, seed, step_idx, e, g):
     for key in ("P", "flag", "x"):
         out[key] = out[key][:npairs]
     out["n_pairs"] = int(npairs)
+    return out
+
+
+def ntc_step(n_cells, w_over_v, dt, seed, step_idx, e, g):
+    """One step with No-Time-Counter candidate selection (Sec. 3.1) on the
+    same species dicts as step().  Returns FP64 momenta in sorted order, the
+    sort permutations and offsets, and per cell the candidate and collision
+    counts and a flag for decisions within 1e-6 of their ratio."""
+    def arr(s, key, dt_):
+        return np.ascontiguousarray(s[key], dtype=dt_)
+
+    ex, ey, ez = (arr(e, c, np.float32) for c in ("ux", "uy", "uz"))
+    gx, gy, gz = (arr(g, c, np.float32) for c in ("ux", "uy", "uz"))
+    ec, gc = arr(e, "cell", np.int32), arr(g, "cell", np.int32)
+    ei, gi = arr(e, "id", np.uint32), arr(g, "id", np.uint32)
+    ne, ng = ex.shape[0], gx.shape[0]
+    out = dict(
+        e_out=np.zeros((3, ne)), g_out=np.zeros((3, ng)),
+        e_perm=np.zeros(ne, dtype=np.int64), g_perm=np.zeros(ng, dtype=np.int64),
+        e_off=np.zeros(n_cells + 1, dtype=np.int64), g_off=np.zeros(n_cells + 1, dtype=np.int64),
+        n_cand=np.zeros(n_cells, dtype=np.int64), n_coll=np.zeros(n_cells, dtype=np.int64),
+        near=np.zeros(n_cells, dtype=np.int32))
+    total = lib().or_ntc_step(int(n_cells), float(w_over_v), float(dt), int(seed), int(step_idx),
+                              ne, _p(ex), _p(ey), _p(ez), _p(ec), _p(ei),
+                              ng, _p(gx), _p(gy), _p(gz), _p(gc), _p(gi),
+                              _p(out["e_out"]), _p(out["g_out"]), _p(out["e_perm"]), _p(out["g_perm"]),
+                              _p(out["e_off"]), _p(out["g_off"]), _p(out["n_cand"]), _p(out["n_coll"]),
+                              _p(out["near"]))
+    if total < 0:
+        raise ValueError("oracle: bad input")
+    out["total_candidates"] = int(total)
     return out
 
 

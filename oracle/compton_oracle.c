@@ -285,17 +285,15 @@ double or_bernoulli_u0(uint64_t seed, uint64_t step, uint32_t p)
  * incoming rest-frame direction, azimuth about it in the Duff et al. basis),
  * boosted back, and the electron given the momentum the photon lost:
  * u <- u + k - k1. */
-void or_collide(const double u[3], const double k[3], uint64_t seed, uint64_t step, uint32_t ctr_id,
-                double u_out[3], double k_out[3])
+static void collide_words(const double u[3], const double k[3], uint32_t w_angle, uint32_t w_phi,
+                          double u_out[3], double k_out[3])
 {
     double inv[2];
     or_invariants(u, k, inv);
     double x = inv[0];
     double eps = norm3(k);
-    uint32_t r[4];
-    draw(seed, step, 4u, ctr_id, r);
-    double u1 = unif_open(r[0]);
-    double u2 = unif_closed0(r[1]);
+    double u1 = unif_open(w_angle);
+    double u2 = unif_closed0(w_phi);
     double t = or_kn_sample_t(x, u1);
     double phi = 2.0 * OR_PI * u2;
     double eps_r, kr[3];
@@ -318,6 +316,14 @@ void or_collide(const double u[3], const double k[3], uint64_t seed, uint64_t st
         u_out[i] = u[i] + k[i] - k1[i];
         k_out[i] = k1[i];
     }
+}
+
+void or_collide(const double u[3], const double k[3], uint64_t seed, uint64_t step, uint32_t ctr_id,
+                double u_out[3], double k_out[3])
+{
+    uint32_t r[4];
+    draw(seed, step, 4u, ctr_id, r);
+    collide_words(u, k, r[0], r[1], u_out, k_out);
 }
 
 /* One pair event (Sec. 3.1, Sec. 3.2).
@@ -496,4 +502,86 @@ void or_ratio(int64_t n, const float* ux, const float* uy, const float* uz,
         double eps = norm3(k);
         r[i] = eps > 0.0 ? 0.5 * or_kn_sigma(inv[0]) * inv[1] : 0.0;
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* No-Time-Counter candidate selection (Sec. 3.1, second step; Bird 1989).   */
+/* The paper gives no formula (its module paper is not available); the      */
+/* reading built here:                                                      */
+/*   - the particles are binned and ordered as or_step does;                */
+/*   - cell c draws N = floor(E + U) candidate pairs, E = N_e N_g (w/V)      */
+/*     sigma_max v_max dt with sigma_max v_max = 2 sigma_T c (sigma <=       */
+/*     sigma_T, v <= 2), U = word 0 of draw(seed, step, 5, c);              */
+/*   - candidate j takes the block draw(seed, step, 6 | j << 8, c): word 0   */
+/*     picks the electron (e_off + floor(w0 N_e / 2^32)), word 1 the photon, */
+/*     and the pair collides iff the uniform of word 2 is below              */
+/*     r = sigma_KN(x) v / (2 sigma_T), the acceptance ratio of the method;  */
+/*   - an accepted candidate collides at once (angle from word 3, azimuth   */
+/*     from word 0 of draw(seed, step, 7 | j << 8, c)) and later candidates */
+/*     of the cell see the updated momenta.                                 */
+/* Outputs e_out, g_out as or_step; per cell the candidate and collision    */
+/* counts and near[c] = 1 if some candidate's uniform lay within 1e-6 of its */
+/* ratio (a decision FP32 arithmetic may take the other way).               */
+/* ------------------------------------------------------------------------ */
+static int64_t pick(uint32_t w, int64_t n) { return (int64_t)(((uint64_t)w * (uint64_t)n) >> 32); }
+
+int64_t or_ntc_step(int64_t n_cells, double w_over_v, double dt, uint64_t seed, uint64_t step,
+                    int64_t n_e, const float* eux, const float* euy, const float* euz,
+                    const int32_t* ecell, const uint32_t* eid,
+                    int64_t n_g, const float* gkx, const float* gky, const float* gkz,
+                    const int32_t* gcell, const uint32_t* gid,
+                    double* e_out, double* g_out, int64_t* e_perm, int64_t* g_perm,
+                    int64_t* e_off, int64_t* g_off, int64_t* n_cand, int64_t* n_coll, int32_t* near)
+{
+    if (or_sort_species(n_e, ecell, eid, n_cells, seed, step, 1u, e_perm, e_off)) return -1;
+    if (or_sort_species(n_g, gcell, gid, n_cells, seed, step, 2u, g_perm, g_off)) return -1;
+    for (int64_t j = 0; j < n_e; ++j) {
+        int64_t i = e_perm[j];
+        e_out[j] = eux[i]; e_out[n_e + j] = euy[i]; e_out[2 * n_e + j] = euz[i];
+    }
+    for (int64_t j = 0; j < n_g; ++j) {
+        int64_t i = g_perm[j];
+        g_out[j] = gkx[i]; g_out[n_g + j] = gky[i]; g_out[2 * n_g + j] = gkz[i];
+    }
+    int64_t total = 0;
+    for (int64_t c = 0; c < n_cells; ++c) {
+        int64_t ne = e_off[c + 1] - e_off[c];
+        int64_t ng = g_off[c + 1] - g_off[c];
+        n_cand[c] = 0;
+        n_coll[c] = 0;
+        near[c] = 0;
+        if (ne == 0 || ng == 0) continue;
+        uint32_t r[4];
+        draw(seed, step, 5u, (uint32_t)c, r);
+        double expect = (double)ne * (double)ng * w_over_v * 2.0 * dt;
+        int64_t nc = (int64_t)floor(expect + unif_closed0(r[0]));
+        n_cand[c] = nc;
+        for (int64_t j = 0; j < nc; ++j) {
+            uint32_t q[4];
+            draw(seed, step, 6u | ((uint32_t)j << 8), (uint32_t)c, q);
+            int64_t je = e_off[c] + pick(q[0], ne);
+            int64_t jg = g_off[c] + pick(q[1], ng);
+            double u[3] = {e_out[je], e_out[n_e + je], e_out[2 * n_e + je]};
+            double k[3] = {g_out[jg], g_out[n_g + jg], g_out[2 * n_g + jg]};
+            double ratio = 0.0;
+            if (norm3(k) > 0.0) {
+                double inv[2];
+                or_invariants(u, k, inv);
+                ratio = 0.5 * or_kn_sigma(inv[0]) * inv[1];
+            }
+            double ua = unif_closed0(q[2]);
+            if (fabs(ua - ratio) < 1e-6) near[c] = 1;
+            if (ua < ratio) {
+                uint32_t z[4];
+                draw(seed, step, 7u | ((uint32_t)j << 8), (uint32_t)c, z);
+                double uo[3], ko[3];
+                collide_words(u, k, q[3], z[0], uo, ko);
+                e_out[je] = uo[0]; e_out[n_e + je] = uo[1]; e_out[2 * n_e + je] = uo[2];
+                g_out[jg] = ko[0]; g_out[n_g + jg] = ko[1]; g_out[2 * n_g + jg] = ko[2];
+                ++n_coll[c];
+            }
+        }
+        total += nc;
+    }
+    return total;
 }

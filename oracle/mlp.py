@@ -64,10 +64,32 @@ def sgnlog(z):
     return np.sign(z) * np.log1p(np.abs(z))
 
 
-def features(u: np.ndarray, k: np.ndarray, scales=FEATURE_SCALES) -> np.ndarray:
-    """(6, n) network inputs from (3, n) momenta."""
+def pair_invariants(u: np.ndarray, k: np.ndarray):
+    """(x, v) per pair from (3, n) momenta, in FP64: gamma = sqrt(1 + |u|^2),
+    eps = |k|, x = gamma eps - u.k (the photon energy in the electron rest
+    frame), v = x / (gamma eps) = 1 - beta cos psi (1 for eps = 0)."""
     u = np.asarray(u, dtype=np.float64)
     k = np.asarray(k, dtype=np.float64)
+    gamma = np.sqrt(1.0 + (u * u).sum(0))
+    eps = np.sqrt((k * k).sum(0))
+    x = gamma * eps - (u * k).sum(0)
+    ge = gamma * eps
+    v = np.where(ge > 0, x / np.where(ge > 0, ge, 1.0), 1.0)
+    return x, v
+
+
+def features(u: np.ndarray, k: np.ndarray, scales=FEATURE_SCALES, mode: str = "momenta") -> np.ndarray:
+    """(6, n) network inputs from (3, n) momenta.  mode "momenta": the six
+    sgnlog-scaled components; mode "invariants": [ln(x)/8, ln(v)/8, 0, 0, 0, 0]
+    (x, v floored at 1e-30)."""
+    u = np.asarray(u, dtype=np.float64)
+    k = np.asarray(k, dtype=np.float64)
+    if mode == "invariants":
+        x, v = pair_invariants(u, k)
+        f = np.zeros((6, u.shape[1]))
+        f[0] = np.log(np.maximum(x, 1e-30)) / 8.0
+        f[1] = np.log(np.maximum(v, 1e-30)) / 8.0
+        return f
     return np.concatenate([sgnlog(u / scales["s_u"]) / scales["n_u"],
                            sgnlog(k / scales["s_k"]) / scales["n_k"]])
 

@@ -23,6 +23,7 @@ c_i32, c_i64, c_u32, c_u64, c_f32, c_f64, c_p = (ctypes.c_int32, ctypes.c_int64,
 COMPTON_OK, COMPTON_EINVAL, COMPTON_ENOMEM, COMPTON_EBUSY, COMPTON_ETIMEOUT, COMPTON_ERANGE, \
     COMPTON_ENOTREADY, COMPTON_ECUDA, COMPTON_ENOMODEL = range(9)
 MODE_PLAIN, MODE_MLP_FP32, MODE_MLP_BF16, MODE_MLP_FP8 = range(4)
+FEATURES_MOMENTA, FEATURES_INVARIANTS = 0, 1
 
 
 class compton_config(ctypes.Structure):
@@ -180,6 +181,19 @@ def compton_scatter_step(ctx: int, e: Species, g: Species, pairs: compton_pairs,
     _check(lib().compton_scatter_step(c_p(ctx), ctypes.byref(ec), ctypes.byref(gc), ctypes.byref(pairs),
                                       int(mode), int(step), _ptr(prob_out), _ptr(flag_out),
                                       _stream_ptr(stream)), "compton_scatter_step", ctx)
+
+
+SIGNATURES["compton_scatter_step_ntc"] = (c_i32, [c_p, ctypes.POINTER(compton_species),
+                                                  ctypes.POINTER(compton_species), ctypes.POINTER(compton_pairs),
+                                                  c_u64, c_p])
+
+
+def compton_scatter_step_ntc(ctx: int, e: Species, g: Species, pairs: compton_pairs, step: int,
+                             stream=None) -> None:
+    """No-Time-Counter collisions of the binned species, in place."""
+    ec, gc = e.c(), g.c()
+    _check(lib().compton_scatter_step_ntc(c_p(ctx), ctypes.byref(ec), ctypes.byref(gc), ctypes.byref(pairs),
+                                          int(step), _stream_ptr(stream)), "compton_scatter_step_ntc", ctx)
 
 
 def compton_scatter_pairs(ctx: int, u, k, n_dens, seed: int, step: int, mode: int = MODE_PLAIN,
@@ -366,7 +380,15 @@ def compton_mlp_balance_weights(ctx: int, r, edges, w_out, stream=None) -> None:
            "compton_mlp_balance_weights", ctx)
 
 
-KERNEL_SLOTS = ("k_count", "k_scan", "k_place", "k_sort_gather", "k_pair_prob", "k_collide", "k_mlp")
+SIGNATURES["compton_mlp_set_features"] = (c_i32, [c_p, c_i32])
+
+
+def compton_mlp_set_features(ctx: int, features: int) -> None:
+    """Network inputs: FEATURES_MOMENTA (default) or FEATURES_INVARIANTS."""
+    _check(lib().compton_mlp_set_features(c_p(ctx), int(features)), "compton_mlp_set_features", ctx)
+
+
+KERNEL_SLOTS = ("k_count", "k_scan", "k_place", "k_sort_gather", "k_pair_prob", "k_collide", "k_mlp", "k_ntc")
 
 SIGNATURES["compton_kernel_timing"] = (c_i32, [c_p, c_i32])
 SIGNATURES["compton_kernel_times"] = (c_i32, [c_p, c_p, c_p])

@@ -180,6 +180,7 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     m.fs[1] = 7.0f;   // n_u
     m.fs[2] = 1e-4f;  // s_k
     m.fs[3] = 10.0f;  // n_k
+    m.feat_mode = COMPTON_FEATURES_MOMENTA;
     e = cudaMemset(ctx->arena, 0, total);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -327,6 +328,14 @@ compton_status compton_scatter_step(compton_ctx* ctx, compton_species* e, compto
     return compton::launch_scatter_binned(ctx, e, g, pairs, mode, step, prob_out, flag_out, stream);
 }
 
+compton_status compton_scatter_step_ntc(compton_ctx* ctx, compton_species* e, compton_species* g,
+                                        const compton_pairs* pairs, uint64_t step, compton_stream_t stream)
+{
+    if (!ctx || !pairs || !species_ok(e) || !species_ok(g)) return COMPTON_EINVAL;
+    if (pairs->cell_info_dev != ctx->cinfo || pairs->n_cells != ctx->cfg.n_cells) return COMPTON_EINVAL;
+    return compton::launch_scatter_ntc(ctx, e, g, pairs, step, stream);
+}
+
 compton_status compton_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, float* uz, float* kx, float* ky,
                                      float* kz, const float* n_dens, int64_t n, uint64_t seed, uint64_t step,
                                      compton_mode mode, float* prob_out, uint8_t* flag_out,
@@ -450,13 +459,18 @@ compton_status compton_mlp_get_grad(compton_ctx* ctx, float* grad, int64_t n_par
 }
 
 namespace {
-struct MlpBlobHeader {
+struct MlpBlobHeaderV1 {
     char magic[4];
     uint32_t version;
     int64_t n_params;
     int64_t adam_step;
     float fs[4];
     float scale_a_inv[4];
+};
+struct MlpBlobHeader {
+    MlpBlobHeaderV1 v1;
+    int32_t feat_mode;
+    int32_t reserved;
 };
 }  // namespace
 
@@ -472,12 +486,14 @@ compton_status compton_mlp_save(compton_ctx* ctx, void* buf, size_t* len)
     }
     COMPTON_CUDA_TRY(ctx, cudaDeviceSynchronize());
     MlpBlobHeader h;
-    std::memcpy(h.magic, "CMLP", 4);
-    h.version = 1;
-    h.n_params = (int64_t)NP;
-    h.adam_step = ctx->adam_step;
-    for (int i = 0; i < 4; ++i) h.fs[i] = ctx->mlp.fs[i];
-    COMPTON_CUDA_TRY(ctx, cudaMemcpy(h.scale_a_inv, ctx->mlp.scale_a_inv, sizeof(h.scale_a_inv),
+    std::memcpy(h.v1.magic, "CMLP", 4);
+    h.v1.version = 2;
+    h.v1.n_params = (int64_t)NP;
+    h.v1.adam_step = ctx->adam_step;
+    for (int i = 0; i < 4; ++i) h.v1.fs[i] = ctx->mlp.fs[i];
+    h.feat_mode = ctx->mlp.feat_mode;
+    h.reserved = 0;
+    COMPTON_CUDA_TRY(ctx, cudaMemcpy(h.v1.scale_a_inv, ctx->mlp.scale_a_inv, sizeof(h.v1.scale_a_inv),
                                      cudaMemcpyDeviceToHost));
     char* p = static_cast<char*>(buf);
     std::memcpy(p, &h, sizeof(h));
@@ -493,16 +509,25 @@ compton_status compton_mlp_save(compton_ctx* ctx, void* buf, size_t* len)
 
 compton_status compton_mlp_load(compton_ctx* ctx, const void* buf, size_t len)
 {
-    if (!ctx || !buf || len < sizeof(MlpBlobHeader)) return COMPTON_EINVAL;
-    MlpBlobHeader h;
+    if (!ctx || !buf || len < sizeof(MlpBlobHeaderV1)) return COMPTON_EINVAL;
+    MlpBlobHeaderV1 h;
     std::memcpy(&h, buf, sizeof(h));
     const size_t NP = compton::kMlpParams;
-    if (std::memcmp(h.magic, "CMLP", 4) != 0 || h.version != 1 || h.n_params != (int64_t)NP ||
-        len != sizeof(h) + 3 * NP * sizeof(float))
+    if (std::memcmp(h.magic, "CMLP", 4) != 0 || (h.version != 1 && h.version != 2) || h.n_params != (int64_t)NP)
         return COMPTON_EINVAL;
-    const char* p = static_cast<const char*>(buf) + sizeof(h);
+    const size_t head = h.version == 1 ? sizeof(MlpBlobHeaderV1) : sizeof(MlpBlobHeader);
+    if (len != head + 3 * NP * sizeof(float)) return COMPTON_EINVAL;
+    int32_t mode = COMPTON_FEATURES_MOMENTA;
+    if (h.version == 2) {
+        MlpBlobHeader h2;
+        std::memcpy(&h2, buf, sizeof(h2));
+        mode = h2.feat_mode;
+        if (mode != COMPTON_FEATURES_MOMENTA && mode != COMPTON_FEATURES_INVARIANTS) return COMPTON_EINVAL;
+    }
+    const char* p = static_cast<const char*>(buf) + head;
     compton_status st = compton_mlp_set_params(ctx, reinterpret_cast<const float*>(p), (int64_t)NP, h.fs);
     if (st != COMPTON_OK) return st;
+    ctx->mlp.feat_mode = mode;
     p += NP * sizeof(float);
     COMPTON_CUDA_TRY(ctx, cudaMemcpy(ctx->mlp.adam_m, p, NP * sizeof(float), cudaMemcpyHostToDevice));
     p += NP * sizeof(float);
@@ -510,6 +535,14 @@ compton_status compton_mlp_load(compton_ctx* ctx, const void* buf, size_t len)
     COMPTON_CUDA_TRY(ctx, cudaMemcpy(ctx->mlp.scale_a_inv, h.scale_a_inv, sizeof(h.scale_a_inv),
                                      cudaMemcpyHostToDevice));
     ctx->adam_step = h.adam_step;
+    return COMPTON_OK;
+}
+
+compton_status compton_mlp_set_features(compton_ctx* ctx, int32_t features)
+{
+    if (!ctx) return COMPTON_EINVAL;
+    if (features != COMPTON_FEATURES_MOMENTA && features != COMPTON_FEATURES_INVARIANTS) return COMPTON_EINVAL;
+    ctx->mlp.feat_mode = features;
     return COMPTON_OK;
 }
 

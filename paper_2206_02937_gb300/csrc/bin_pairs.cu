@@ -22,7 +22,7 @@
 namespace compton {
 namespace {
 
-constexpr int kSortThreads = 512;
+constexpr int kSortThreads = 256;
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
@@ -608,7 +608,7 @@ __device__ void sort_giant_cell(const SortGatherArgs& g, int s, const SortSrc& t
 
 constexpr size_t kSortSmem = (size_t)kSortCap * (8 + 4 + 4 + 2 + 2 + 2 + 12);
 
-__global__ void __launch_bounds__(kSortThreads, 2) k_sort_gather(SortGatherArgs g)
+__global__ void __launch_bounds__(kSortThreads, 4) k_sort_gather(SortGatherArgs g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem m;

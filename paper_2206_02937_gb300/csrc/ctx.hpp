@@ -13,8 +13,8 @@ namespace compton {
 
 // Tiling constants shared by the binning and scattering kernels.
 constexpr int kScanTile = 2048;       // cells per scan tile (256 threads x 8)
-constexpr int kSortTile = 2048;       // particles per sort tile (by cell start offsets)
-constexpr int kSortCap = 3072;        // particles a sort CTA holds in shared memory
+constexpr int kSortTile = 1024;       // particles per sort tile (by cell start offsets)
+constexpr int kSortCap = 1536;        // particles a sort CTA holds in shared memory
 constexpr int kPairsPerTile = 1024;   // pairs per scatter CTA (256 threads x 4)
 constexpr int kCellWindow = 512;      // cells of a scatter tile staged in shared memory
 
@@ -49,12 +49,24 @@ struct __align__(16) AcceptedPair {
 
 // A pair whose uniform passed the probability bound P_b = 1 - exp(-2 n dt)
 // and whose probability must be evaluated: sorted electron and photon index,
-// pair density, its uniform u0, pair index.
+// pair density, its uniform u0, pair index, and both momenta (read once,
+// while the pair's tile is being filtered, so the later kernels read the
+// list sequentially).
 struct __align__(16) CandPair {
     int32_t ie, ig;
     float dens, u0;
     uint32_t p;
-    uint32_t pad[3];
+    float u[3], k[3];
+    uint32_t pad;
+};
+
+// The Bernoulli decision made inside the network kernel (surrogate modes on
+// tensor cores): time step, FP64 threshold of the analytic fallback, optional
+// per-pair outputs.
+struct MlpDecide {
+    float dt, gamma64;
+    float* prob_out;
+    uint8_t* flag_out;
 };
 
 enum : unsigned { kErrCellRange = 1u, kErrCapacity = 2u, kErrTimeout = 4u };
@@ -95,6 +107,7 @@ struct MlpDev {
     float* edges;        // [257] data-balancing bin edges
     int* hist;           // [256] data-balancing counts
     float fs[4];         // feature scales s_u, n_u, s_k, n_k
+    int32_t feat_mode;   // compton_features: momenta or invariants
 };
 
 struct ServeEngine;
@@ -199,6 +212,8 @@ compton_status launch_scatter_binned(compton_ctx* ctx, compton_species* e, compt
 compton_status launch_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, float* uz, float* kx, float* ky,
                                     float* kz, const float* n_dens, int64_t n, uint64_t seed, uint64_t step,
                                     compton_mode mode, float* prob_out, uint8_t* flag_out, cudaStream_t stream);
+compton_status launch_scatter_ntc(compton_ctx* ctx, compton_species* e, compton_species* g,
+                                  const compton_pairs* pairs, uint64_t step, cudaStream_t stream);
 compton_status launch_kn_ratio(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                const float* kx, const float* ky, const float* kz, int64_t n, float* r_out,
                                cudaStream_t stream);
@@ -207,7 +222,8 @@ compton_status launch_sample_angle(compton_ctx* ctx, const float* x, const uint3
 compton_status mlp_repack(compton_ctx* ctx, cudaStream_t stream);
 compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                 const float* kx, const float* ky, const float* kz, int64_t n, compton_mode mode,
-                                float* r_out, cudaStream_t stream, bool binned = false, bool candidates = false);
+                                float* r_out, cudaStream_t stream, bool binned = false, bool candidates = false,
+                                const MlpDecide* decide = nullptr);
 size_t train_scratch_bytes(int64_t max_batch);
 compton_status launch_balance_weights(compton_ctx* ctx, const float* r, int64_t n, const float* edges_host,
                                       int n_bins, float* w_out, cudaStream_t stream);

@@ -455,4 +455,19 @@ __device__ __forceinline__ void collide_f64(float& ux, float& uy, float& uz, flo
     kz = (float)k12;
 }
 
+// ---------------------------------------------------------------------------
+// The analytic probability of one pair, P = 1 - exp(-n dt sigma_KN(x)/sigma_T
+// v), and its rest-frame photon energy x; FP64 invariants for electrons above
+// gamma64, the series or closed-form sigma_KN as x requires.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float analytic_prob(float ux, float uy, float uz, float kx, float ky, float kz, float dens,
+                                              float dt, float gamma64, float* x_out)
+{
+    const Invariants inv = invariants_f32(ux, uy, uz, kx, ky, kz);
+    float x = inv.x, v = inv.v;
+    if (inv.gamma > gamma64) invariants_f64(ux, uy, uz, kx, ky, kz, &x, &v);
+    *x_out = x;
+    return inv.eps > 0.0f ? one_minus_exp_neg(dens * dt * 0.375f * kn_F2(x) * v) : 0.0f;
+}
+
 }  // namespace compton

@@ -27,6 +27,7 @@
 
 #include "ctx.hpp"
 #include "device_math.cuh"
+#include "features.cuh"
 #include "tc_ptx.cuh"
 
 namespace compton {
@@ -47,21 +48,6 @@ constexpr uint32_t kOffSlot = kOffBar + 8;              // TMEM address
 constexpr uint32_t kSmemTc = kOffSlot + 8 + 1024;       // + alignment slack
 
 constexpr uint64_t kWaitNs = 2000000000ull;             // 2 s bound on every wait
-
-__device__ __forceinline__ float sgnlog(float z) { return copysignf(log1pf(fabsf(z)), z); }
-
-__device__ __forceinline__ void features(const MlpDev& m, float ux, float uy, float uz, float kx, float ky, float kz,
-                                         float* f)
-{
-    const float iu = __fdividef(1.0f, m.fs[0]), nu = __fdividef(1.0f, m.fs[1]);
-    const float ik = __fdividef(1.0f, m.fs[2]), nk = __fdividef(1.0f, m.fs[3]);
-    f[0] = sgnlog(ux * iu) * nu;
-    f[1] = sgnlog(uy * iu) * nu;
-    f[2] = sgnlog(uz * iu) * nu;
-    f[3] = sgnlog(kx * ik) * nk;
-    f[4] = sgnlog(ky * ik) * nk;
-    f[5] = sgnlog(kz * ik) * nk;
-}
 
 __device__ __forceinline__ float silu_fast(float z) { return 0.5f * z * (1.0f + tc::tanh_approx(0.5f * z)); }
 __device__ __forceinline__ float silu_exact(float z) { return z / (1.0f + expf(-z)); }
@@ -163,7 +149,56 @@ struct MlpArgs {
     // candidate input (rows of the candidate list) when cand != nullptr
     const CandPair* cand;
     const uint32_t* n_cand;
+    // decide: P and the Bernoulli trial of every candidate row in the
+    // epilogue, accepted pairs appended to the list (r_out unused)
+    bool decide;
+    MlpDecide dec;
+    AcceptedPair* accepted;
+    uint32_t* n_accepted;
 };
+
+// Probability and decision of candidate row `row` from its network output
+// (pre-sigmoid z) and momenta q: P = 1 - exp(-2 n dt r) inside the network's
+// training range (gamma <= 1e3, eps in [1e-4, 1]), else the analytic
+// probability (counted); accepted rows go to the list with their momenta.
+// Called by every thread of a warp.
+__device__ __forceinline__ void decide_row(const MlpArgs& a, int64_t row, bool live, float z, const float* q)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    bool hit = false, fb = false;
+    float x = -1.0f;
+    CandPair c{};
+    if (live) {
+        c = a.cand[row];
+        const float r = __fdividef(1.0f, 1.0f + __expf(-z));
+        const float g2 = fmaf(q[0], q[0], fmaf(q[1], q[1], fmaf(q[2], q[2], 1.0f)));
+        const float e2 = fmaf(q[3], q[3], fmaf(q[4], q[4], q[5] * q[5]));
+        float P;
+        if (g2 <= 1.0e6f && e2 >= 1.0e-8f && e2 <= 1.0f) {
+            P = one_minus_exp_neg(2.0f * c.dens * a.dec.dt * r);
+        } else {
+            fb = true;
+            P = analytic_prob(q[0], q[1], q[2], q[3], q[4], q[5], c.dens, a.dec.dt, a.dec.gamma64, &x);
+        }
+        hit = c.u0 < P;
+        if (a.dec.prob_out) a.dec.prob_out[c.p] = P;
+        if (a.dec.flag_out) a.dec.flag_out[c.p] = hit ? 1 : 0;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    const unsigned mf = __ballot_sync(0xffffffffu, fb);
+    if (m) {
+        uint32_t at = 0;
+        if (lane == 0) at = atomicAdd(a.n_accepted, (uint32_t)__popc(m));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (hit)
+            a.accepted[at + __popc(m & ((1u << lane) - 1u))] =
+                AcceptedPair{c.ie, c.ig, x, c.p, {q[0], q[1], q[2]}, {q[3], q[4], q[5]}, {0u, 0u}};
+    }
+    if (lane == 0) {
+        if (m) atomicAdd(&a.stats->scatters, (unsigned long long)__popc(m));
+        if (mf) atomicAdd(&a.stats->mlp_fallbacks, (unsigned long long)__popc(mf));
+    }
+}
 
 // Electron and photon index of pair p of a binned pair list: the cell is
 // found by binary search between the cells of p's 1024-pair scatter tile.
@@ -189,13 +224,18 @@ __device__ __forceinline__ void load_pair_raw(const MlpArgs& a, int64_t row, int
         for (int i = 0; i < 6; ++i) q[i] = 0.0f;
         return;
     }
-    int ie = (int)row, ig = (int)row;
     if (a.cand) {
-        ie = a.cand[row].ie;
-        ig = a.cand[row].ig;
-    } else if (a.cinfo) {
-        binned_pair(a, row, ie, ig);
+        const CandPair& c = a.cand[row];
+        q[0] = c.u[0];
+        q[1] = c.u[1];
+        q[2] = c.u[2];
+        q[3] = c.k[0];
+        q[4] = c.k[1];
+        q[5] = c.k[2];
+        return;
     }
+    int ie = (int)row, ig = (int)row;
+    if (a.cinfo) binned_pair(a, row, ie, ig);
     q[0] = a.u[0][ie];
     q[1] = a.u[1][ie];
     q[2] = a.u[2][ie];
@@ -264,7 +304,8 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
     for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
         const int64_t row = tile * kTileM + tid;
         float f[6] = {0, 0, 0, 0, 0, 0};
-        if (row < n_rows) features(m, raw[0], raw[1], raw[2], raw[3], raw[4], raw[5], f);
+        const float cur[6] = {raw[0], raw[1], raw[2], raw[3], raw[4], raw[5]};
+        if (row < n_rows) features(m, cur[0], cur[1], cur[2], cur[3], cur[4], cur[5], f);
         if (tile + gridDim.x < n_tiles) load_pair_raw(a, (tile + gridDim.x) * kTileM + tid, n_rows, raw);
         // layer-0 input: the 6 features in chunk 0 of the row, chunk 1 zeroed
         // (the single K step of layer 0 reads bytes 0..31 of the row)
@@ -355,7 +396,8 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
                 break;
             }
         }
-        if (!failed && row < n_rows) a.r_out[row] = __fdividef(1.0f, 1.0f + __expf(-(acc_out + b4)));
+        if (a.decide) decide_row(a, row, !failed && row < n_rows, acc_out + b4, cur);
+        else if (!failed && row < n_rows) a.r_out[row] = __fdividef(1.0f, 1.0f + __expf(-(acc_out + b4)));
     }
     if (failed && tid == 0) atomicOr(&a.stats->error_flags, (unsigned long long)kErrTimeout);
     tc::fence_before_sync();
@@ -495,9 +537,14 @@ compton_status mlp_repack(compton_ctx* ctx, cudaStream_t stream)
 
 compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                 const float* kx, const float* ky, const float* kz, int64_t n, compton_mode mode,
-                                float* r_out, cudaStream_t stream, bool binned, bool candidates)
+                                float* r_out, cudaStream_t stream, bool binned, bool candidates,
+                                const MlpDecide* decide)
 {
     MlpArgs a;
+    a.decide = decide != nullptr && mode != COMPTON_MODE_MLP_FP32;
+    if (decide) a.dec = *decide;
+    a.accepted = ctx->accepted;
+    a.n_accepted = ctx->n_accepted;
     a.m = ctx->mlp;
     a.u[0] = ux;
     a.u[1] = uy;
@@ -580,6 +627,9 @@ compton_status launch_mlp_calibrate(compton_ctx* ctx, const float* ux, const flo
     a.n_pairs = binned ? ctx->n_pairs : nullptr;
     a.cand = nullptr;
     a.n_cand = nullptr;
+    a.decide = false;
+    a.accepted = nullptr;
+    a.n_accepted = nullptr;
     const int smem = (4 * 4096 + 64 * kF32Threads + 256 + 64) * 4;
     COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->mlp.amax, 0, 4 * sizeof(float), stream));
     COMPTON_CUDA_TRY(ctx, cudaFuncSetAttribute(k_mlp_fp32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

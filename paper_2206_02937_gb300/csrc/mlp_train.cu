@@ -22,13 +22,13 @@
 // Scratch: z and delta for 4 layers x 64 units x n samples, laid out
 // [layer][unit][sample] so that consecutive threads touch consecutive words.
 #include "ctx.hpp"
+#include "features.cuh"
 
 namespace compton {
 namespace {
 
 constexpr int kTrThreads = 128;
 
-__device__ __forceinline__ float sgnlog_t(float z) { return copysignf(log1pf(fabsf(z)), z); }
 __device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + expf(-z)); }
 
 struct TrainArgs {
@@ -62,9 +62,8 @@ __global__ void __launch_bounds__(kTrThreads) k_train_fwd_bwd(TrainArgs a)
     float loss_num = 0.0f, wsum = 0.0f;
     for (int64_t s = (int64_t)blockIdx.x * kTrThreads + tid; s < n; s += (int64_t)gridDim.x * kTrThreads) {
         // ---- forward ----
-        const float f[6] = {sgnlog_t(a.u[0][s] / m.fs[0]) / m.fs[1], sgnlog_t(a.u[1][s] / m.fs[0]) / m.fs[1],
-                            sgnlog_t(a.u[2][s] / m.fs[0]) / m.fs[1], sgnlog_t(a.k[0][s] / m.fs[2]) / m.fs[3],
-                            sgnlog_t(a.k[1][s] / m.fs[2]) / m.fs[3], sgnlog_t(a.k[2][s] / m.fs[2]) / m.fs[3]};
+        float f[6];
+        features(m, a.u[0][s], a.u[1][s], a.u[2][s], a.k[0][s], a.k[1][s], a.k[2][s], f);
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             hs[i * kTrThreads + tid] = f[i];

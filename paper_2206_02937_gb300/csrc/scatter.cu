@@ -92,16 +92,11 @@ __device__ __forceinline__ void resolve(const ScatterArgs& a, const AcceptedPair
     a.k[2][e.ig] = kz;
 }
 
-// The analytic probability of one pair and its rest-frame energy x; for
-// electrons above the FP64 threshold the invariants are recomputed in FP64.
+// The analytic probability of one pair and its rest-frame energy x.
 __device__ __forceinline__ float analytic_P(const ScatterArgs& a, float ux, float uy, float uz, float kx, float ky,
                                            float kz, float dens, float* x_out)
 {
-    const Invariants inv = invariants_f32(ux, uy, uz, kx, ky, kz);
-    float x = inv.x, v = inv.v;
-    if (inv.gamma > a.gamma64) invariants_f64(ux, uy, uz, kx, ky, kz, &x, &v);
-    *x_out = x;
-    return inv.eps > 0.0f ? one_minus_exp_neg(dens * a.dt * 0.375f * kn_F2(x) * v) : 0.0f;
+    return analytic_prob(ux, uy, uz, kx, ky, kz, dens, a.dt, a.gamma64, x_out);
 }
 
 // Probability, Bernoulli trial and list of accepted pairs of one tile of
@@ -254,13 +249,15 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
 }
 
 // Surrogate modes, first kernel: phase A of k_pair_prob (locate, Bernoulli
-// uniform, bound test), with the candidates written to the context's
-// candidate list for the network.
+// uniform, bound test); the candidates, with their momenta, go to the
+// context's candidate list for the network.
 template <bool kBinned>
 __global__ void __launch_bounds__(kProbThreads, 4) k_cand(ScatterArgs a)
 {
     __shared__ CellInfo win[kCellWindow];
     __shared__ unsigned red_pairs;
+    __shared__ int warp_cnt[kProbThreads / 32];
+    __shared__ uint32_t cta_base;
     const int tid = threadIdx.x;
     const unsigned lane = tid & 31u;
     const int64_t total = kBinned ? *a.n_pairs : a.p_end;
@@ -283,45 +280,90 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_cand(ScatterArgs a)
     const CellInfo* cw = nwin <= kCellWindow ? win : a.cinfo + c_first;
     int ci = (kBinned && pb < total) ? find_cell(cw, nwin, pb) : 0;
     unsigned n_pairs = 0;
+    int ie[kPairsPerThread], ig[kPairsPerThread];
+    float dens[kPairsPerThread], u0[kPairsPerThread];
+    bool is_cand[kPairsPerThread];
 #pragma unroll
     for (int r = 0; r < kPairsPerThread; ++r) {
         const int64_t p = pb + r;
         const bool valid = p < total;
-        int ie = 0, ig = 0;
-        float dens = 0.0f;
+        ie[r] = 0;
+        ig[r] = 0;
+        dens[r] = 0.0f;
         if (valid) {
             if (kBinned) {
                 while (ci + 1 < nwin && (int64_t)cw[ci + 1].pair_off <= p) ++ci;
                 const CellInfo c = cw[ci];
                 const int j = (int)(p - c.pair_off);
-                ie = c.e_start + j;
-                ig = c.g_start + j;
-                dens = c.dens;
+                ie[r] = c.e_start + j;
+                ig[r] = c.g_start + j;
+                dens[r] = c.dens;
             } else {
-                ie = (int)p;
-                ig = (int)p;
-                dens = a.n_dens[p];
+                ie[r] = (int)p;
+                ig[r] = (int)p;
+                dens[r] = a.n_dens[p];
             }
             ++n_pairs;
         }
-        const float u0 = u24_closed0(words[r]);
-        const bool is_cand = valid && (all || u0 < one_minus_exp_neg(2.0002f * dens * a.dt));
-        if (valid && !is_cand && a.flag_out) a.flag_out[p] = 0;
-        const unsigned m = __ballot_sync(0xffffffffu, is_cand);
-        if (m) {
-            uint32_t at = 0;
-            if (lane == 0) at = atomicAdd(a.n_cand, (uint32_t)__popc(m));
-            at = __shfl_sync(0xffffffffu, at, 0);
-            if (is_cand) {
-                CandPair c;
-                c.ie = ie;
-                c.ig = ig;
-                c.dens = dens;
-                c.u0 = u0;
-                c.p = (uint32_t)p;
-                c.pad[0] = c.pad[1] = c.pad[2] = 0u;
-                a.cand[at + __popc(m & ((1u << lane) - 1u))] = c;
-            }
+        u0[r] = u24_closed0(words[r]);
+        is_cand[r] = valid && (all || u0[r] < one_minus_exp_neg(2.0002f * dens[r] * a.dt));
+        if (valid && !is_cand[r] && a.flag_out) a.flag_out[p] = 0;
+    }
+    // the candidates' momenta: all loads in flight before the first use
+    float mom[kPairsPerThread][6];
+#pragma unroll
+    for (int r = 0; r < kPairsPerThread; ++r) {
+        if (is_cand[r]) {
+            mom[r][0] = a.u[0][ie[r]];
+            mom[r][1] = a.u[1][ie[r]];
+            mom[r][2] = a.u[2][ie[r]];
+            mom[r][3] = a.k[0][ig[r]];
+            mom[r][4] = a.k[1][ig[r]];
+            mom[r][5] = a.k[2][ig[r]];
+        }
+    }
+    // the CTA's candidates take one contiguous range of the list (one atomic
+    // per CTA): lane prefix within the warp, warp prefix within the CTA
+    int mine = 0;
+#pragma unroll
+    for (int r = 0; r < kPairsPerThread; ++r) mine += is_cand[r] ? 1 : 0;
+    int incl = mine;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, incl, d);
+        if ((int)lane >= d) incl += o;
+    }
+    const int w = tid >> 5;
+    if (lane == 31) warp_cnt[w] = incl;
+    __syncthreads();
+    if (tid == 0) {
+        int run = 0;
+        for (int i = 0; i < kProbThreads / 32; ++i) {
+            const int c = warp_cnt[i];
+            warp_cnt[i] = run;
+            run += c;
+        }
+        cta_base = run ? atomicAdd(a.n_cand, (uint32_t)run) : 0u;
+    }
+    __syncthreads();
+    uint32_t at = cta_base + (uint32_t)(warp_cnt[w] + incl - mine);
+#pragma unroll
+    for (int r = 0; r < kPairsPerThread; ++r) {
+        if (is_cand[r]) {
+            CandPair c;
+            c.ie = ie[r];
+            c.ig = ig[r];
+            c.dens = dens[r];
+            c.u0 = u0[r];
+            c.p = (uint32_t)(pb + r);
+            c.u[0] = mom[r][0];
+            c.u[1] = mom[r][1];
+            c.u[2] = mom[r][2];
+            c.k[0] = mom[r][3];
+            c.k[1] = mom[r][4];
+            c.k[2] = mom[r][5];
+            c.pad = 0u;
+            a.cand[at++] = c;
         }
     }
 #pragma unroll
@@ -351,12 +393,12 @@ __global__ void __launch_bounds__(256) k_decide(ScatterArgs a)
         float ux = 0.0f, uy = 0.0f, uz = 0.0f, kx = 0.0f, ky = 0.0f, kz = 0.0f;
         if (i < n) {
             c = a.cand[i];
-            ux = a.u[0][c.ie];
-            uy = a.u[1][c.ie];
-            uz = a.u[2][c.ie];
-            kx = a.k[0][c.ig];
-            ky = a.k[1][c.ig];
-            kz = a.k[2][c.ig];
+            ux = c.u[0];
+            uy = c.u[1];
+            uz = c.u[2];
+            kx = c.k[0];
+            ky = c.k[1];
+            kz = c.k[2];
             const float g2 = fmaf(ux, ux, fmaf(uy, uy, fmaf(uz, uz, 1.0f)));
             const float e2 = fmaf(kx, kx, fmaf(ky, ky, kz * kz));
             float P;
@@ -398,6 +440,82 @@ __global__ void __launch_bounds__(256) k_collide(ScatterArgs a)
     const uint32_t n = *a.n_accepted;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) resolve(a, a.accepted[i]);
+}
+
+// No-Time-Counter candidate selection (Sec. 3.1, second step; Bird 1989),
+// one thread per cell: the cell draws N = floor(E + U) candidates with
+// E = N_e N_g (w/V) 2 dt (sigma_max v_max = 2 sigma_T c) and U from
+// Philox(c, step, 5); candidate j takes the block (c, step, 6 | j << 8):
+// word 0 picks the electron, word 1 the photon, the pair collides iff the
+// uniform of word 2 is below r = sigma_KN(x) v / (2 sigma_T), word 3 drives
+// the angle and word 0 of block (c, step, 7 | j << 8) the azimuth.  An
+// accepted candidate collides at once, so later candidates of the cell see
+// the updated momenta.  E + U is formed in FP64 with explicit rounding so the
+// candidate count is the one FP64 arithmetic gives.
+struct NtcArgs {
+    float* u[3];
+    float* k[3];
+    const int32_t* off_e;
+    const int32_t* off_g;
+    int64_t n_cells;
+    double w_over_v, dt;
+    uint64_t seed, step;
+    float gamma64, collide64_sq;
+    DeviceStats* stats;
+};
+
+__device__ __forceinline__ int pick_index(uint32_t w, int n) { return (int)(((uint64_t)w * (uint64_t)n) >> 32); }
+
+__global__ void __launch_bounds__(256) k_ntc(NtcArgs a)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long n_cand = 0, n_coll = 0;
+    if (c < a.n_cells) {
+        const int e0 = a.off_e[c], ne = a.off_e[c + 1] - e0;
+        const int g0 = a.off_g[c], ng = a.off_g[c + 1] - g0;
+        if (ne > 0 && ng > 0) {
+            const Philox4 rc = draw(a.seed, a.step, 5u, (uint32_t)c);
+            const double expect = __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn((double)ne, (double)ng), a.w_over_v), 2.0),
+                                            a.dt);
+            const double uc = (double)(rc.r0 >> 8) * (1.0 / 16777216.0);
+            const int64_t nc = (int64_t)floor(__dadd_rn(expect, uc));
+            n_cand = (unsigned long long)nc;
+            for (int64_t j = 0; j < nc; ++j) {
+                const Philox4 q = draw(a.seed, a.step, 6u | ((uint32_t)j << 8), (uint32_t)c);
+                const int ie = e0 + pick_index(q.r0, ne);
+                const int ig = g0 + pick_index(q.r1, ng);
+                float ux = a.u[0][ie], uy = a.u[1][ie], uz = a.u[2][ie];
+                float kx = a.k[0][ig], ky = a.k[1][ig], kz = a.k[2][ig];
+                const Invariants inv = invariants_f32(ux, uy, uz, kx, ky, kz);
+                float x = inv.x, v = inv.v;
+                if (inv.gamma > a.gamma64) invariants_f64(ux, uy, uz, kx, ky, kz, &x, &v);
+                const float F2 = kn_F2(x);
+                const float ratio = inv.eps > 0.0f ? 0.5f * 0.375f * F2 * v : 0.0f;
+                if (!(u24_closed0(q.r2) < ratio)) continue;
+                const Philox4 z = draw(a.seed, a.step, 7u | ((uint32_t)j << 8), (uint32_t)c);
+                const Angle ang = kn_sample_angle(x, q.r3 >> 8, F2);
+                const float ge2 = fmaf(ux, ux, fmaf(uy, uy, fmaf(uz, uz, 1.0f))) * fmaf(kx, kx, fmaf(ky, ky, kz * kz));
+                if (ge2 > a.collide64_sq) collide_f64(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(z.r0));
+                else collide_f32(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(z.r0));
+                a.u[0][ie] = ux;
+                a.u[1][ie] = uy;
+                a.u[2][ie] = uz;
+                a.k[0][ig] = kx;
+                a.k[1][ig] = ky;
+                a.k[2][ig] = kz;
+                ++n_coll;
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        n_cand += __shfl_xor_sync(0xffffffffu, n_cand, d);
+        n_coll += __shfl_xor_sync(0xffffffffu, n_coll, d);
+    }
+    if ((threadIdx.x & 31u) == 0) {
+        if (n_cand) atomicAdd(&a.stats->pairs_tested, n_cand);
+        if (n_coll) atomicAdd(&a.stats->scatters, n_coll);
+    }
 }
 
 // r = s(x) v / 2 per explicit pair.
@@ -474,11 +592,17 @@ compton_status launch_step(compton_ctx* ctx, ScatterArgs& a, compton_mode mode, 
             k_cand<kBinned><<<tiles, kProbThreads, 0, stream>>>(a);
         }
         COMPTON_LAUNCH_CHECK(ctx, "k_cand");
+        // tensor-core modes decide inside the network kernel; the FP32
+        // network writes r and k_decide decides
+        const MlpDecide dec{a.dt, a.gamma64, a.prob_out, a.flag_out};
+        const bool fused = mode != COMPTON_MODE_MLP_FP32;
         compton_status st = launch_mlp_infer(ctx, a.u[0], a.u[1], a.u[2], a.k[0], a.k[1], a.k[2], rows, mode,
-                                             ctx->r_buf, stream, false, true);
+                                             ctx->r_buf, stream, false, true, fused ? &dec : nullptr);
         if (st != COMPTON_OK) return st;
-        TimedScope ts_(ctx, COMPTON_K_PROB, stream);
-        k_decide<<<collide_grid(rows), 256, 0, stream>>>(a);
+        if (!fused) {
+            TimedScope ts_(ctx, COMPTON_K_PROB, stream);
+            k_decide<<<collide_grid(rows), 256, 0, stream>>>(a);
+        }
     }
     COMPTON_LAUNCH_CHECK(ctx, "k_pair_prob");
     {
@@ -544,6 +668,35 @@ compton_status launch_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, floa
         const compton_status st = launch_step<false>(ctx, a, mode, tiles, a.p_end - a.p_begin, stream);
         if (st != COMPTON_OK) return st;
     }
+    return COMPTON_OK;
+}
+
+compton_status launch_scatter_ntc(compton_ctx* ctx, compton_species* e, compton_species* g,
+                                  const compton_pairs* pairs, uint64_t step, cudaStream_t stream)
+{
+    if (pairs->n_cells <= 0) return COMPTON_OK;
+    NtcArgs a;
+    a.u[0] = e->ux_dev;
+    a.u[1] = e->uy_dev;
+    a.u[2] = e->uz_dev;
+    a.k[0] = g->ux_dev;
+    a.k[1] = g->uy_dev;
+    a.k[2] = g->uz_dev;
+    a.off_e = pairs->off_e_dev;
+    a.off_g = pairs->off_g_dev;
+    a.n_cells = pairs->n_cells;
+    a.w_over_v = ctx->cfg.w_over_v;
+    a.dt = ctx->cfg.dt;
+    a.seed = ctx->cfg.seed;
+    a.step = step;
+    a.gamma64 = ctx->cfg.gamma_fp64_threshold;
+    a.collide64_sq = ctx->cfg.collide_fp64_threshold * ctx->cfg.collide_fp64_threshold;
+    a.stats = ctx->stats;
+    {
+        TimedScope ts_(ctx, COMPTON_K_NTC, stream);
+        k_ntc<<<(unsigned)((pairs->n_cells + 255) / 256), 256, 0, stream>>>(a);
+    }
+    COMPTON_LAUNCH_CHECK(ctx, "k_ntc");
     return COMPTON_OK;
 }
 

@@ -28,12 +28,13 @@ def _theta(seed, gain=1.0):
     return th
 
 
-def _run(torch, theta, u, k, modes, calibrate=True):
+def _run(torch, theta, u, k, modes, calibrate=True, features=0):
     import paper_2206_02937_gb300 as cg
     cg.build()
     ctx = cg.compton_init(1, 0, 1.0, 0.05, 1)
     try:
         cg.compton_mlp_set_params(ctx, theta.astype(np.float32))
+        cg.compton_mlp_set_features(ctx, features)
         ut, kt = torch.from_numpy(u).cuda(), torch.from_numpy(k).cuda()
         if calibrate:
             cg.compton_mlp_calibrate(ctx, ut, kt)
@@ -106,6 +107,38 @@ def test_save_load_round_trip_bit_exact():
         bad[0:4] = b"XXXX"
         with pytest.raises(cg.ComptonError):
             cg.compton_mlp_load(ctx, bytes(bad))
+    finally:
+        cg.compton_destroy(ctx)
+
+
+@pytest.mark.parametrize("n", [129, 5000])
+def test_forward_parity_invariant_features(n):
+    # inputs ln(x)/8, ln(v)/8 from the FP32 invariants (relative error ~1e-6)
+    # against the FP64 oracle's: FP32 bound 5e-6, the others as above
+    import paper_2206_02937_gb300 as cg
+    torch = torch_cuda()
+    u, k = wl.c3(n, seed=40 + n % 5)
+    th = _theta(3, gain=1.5)
+    ref, _ = omlp.forward(th.astype(np.float32).astype(np.float64), omlp.features(u, k, mode="invariants"))
+    out, blob = _run(torch, th, u, k, [cg.MODE_MLP_FP32, cg.MODE_MLP_BF16, cg.MODE_MLP_FP8],
+                     features=cg.FEATURES_INVARIANTS)
+    e32 = np.abs(out[cg.MODE_MLP_FP32] - ref)
+    assert e32.max() <= 5e-6, e32.max()
+    e16 = np.abs(out[cg.MODE_MLP_BF16] - ref)
+    assert e16.max() <= 2e-2 and e16.mean() <= 4e-3, (e16.max(), e16.mean())
+    e8 = np.abs(out[cg.MODE_MLP_FP8] - ref)
+    assert e8.max() <= 0.12 and e8.mean() <= 0.03, (e8.max(), e8.mean())
+    # the mode travels with a saved network
+    ctx = cg.compton_init(1, 0, 1.0, 0.05, 1)
+    try:
+        cg.compton_mlp_load(ctx, blob)
+        ut, kt = torch.from_numpy(u).cuda(), torch.from_numpy(k).cuda()
+        r = torch.zeros(n, device="cuda")
+        cg.compton_mlp_infer(ctx, ut, kt, cg.MODE_MLP_FP32, r)
+        torch.cuda.synchronize()
+        assert np.array_equal(r.cpu().numpy().astype(np.float64), out[cg.MODE_MLP_FP32])
+        with pytest.raises(cg.ComptonError):
+            cg.compton_mlp_set_features(ctx, 7)
     finally:
         cg.compton_destroy(ctx)
 

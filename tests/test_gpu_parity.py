@@ -311,3 +311,11 @@ def test_filtered_equals_full_evaluation(case):
         for sp in ("after_e", "after_g"):
             for c in ("ux", "uy", "uz"):
                 assert np.array_equal(g[sp][c], full[sp][c])
+
+
+@pytest.mark.parametrize("presorted", [False, True])
+def test_tiles_above_shared_memory_in_chunks(presorted):
+    # cells of ~700 particles: most sort tiles hold more than shared memory
+    # does, so their cells are sorted in runs that fit, block-wide
+    w = _random_workload(19, 40, 700, 650, spread=0.3)
+    compare_with_oracle(_presorted(w) if presorted else w, step=4)

@@ -25,8 +25,8 @@ def _tensors(torch, u, k, y, w):
             None if w is None else torch.from_numpy(w.astype(np.float32)).cuda())
 
 
-@pytest.mark.parametrize("n,weighted", [(1000, False), (4097, True)])
-def test_gradient_and_adam_match_oracle(n, weighted):
+@pytest.mark.parametrize("n,weighted,feat", [(1000, False, 0), (4097, True, 0), (2500, False, 1)])
+def test_gradient_and_adam_match_oracle(n, weighted, feat):
     import paper_2206_02937_gb300 as cg
     torch = torch_cuda()
     cg.build()
@@ -38,13 +38,14 @@ def test_gradient_and_adam_match_oracle(n, weighted):
     ctx = _ctx(cg, n)
     try:
         cg.compton_mlp_set_params(ctx, th)
+        cg.compton_mlp_set_features(ctx, feat)
         ut, kt, yt, wt = _tensors(torch, u, k, y, w)
         loss = cg.compton_mlp_train_step(ctx, ut, kt, yt, wt, lr=1e-3)
         g_gpu = cg.compton_mlp_get_grad(ctx).astype(np.float64)
         th_new = cg.compton_mlp_get_params(ctx).astype(np.float64)
     finally:
         cg.compton_destroy(ctx)
-    f = omlp.features(u, k)
+    f = omlp.features(u, k, mode="invariants" if feat else "momenta")
     loss_ref, g_ref = omlp.backward(th.astype(np.float64), f, y, w)
     assert loss == pytest.approx(loss_ref, rel=1e-5)
     G_gpu, G_ref = omlp.unpack(g_gpu), omlp.unpack(g_ref)

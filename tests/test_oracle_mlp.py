@@ -140,3 +140,23 @@ def test_features_sign_and_scale():
     f = mlp.features(u, k)
     assert np.allclose(f[0], [0.0, np.log(2) / 7, -np.log(2) / 7])
     assert np.allclose(f[3], [np.log(2) / 10, -np.log(2) / 10, 0.0])
+
+
+def test_invariant_features_match_the_pinned_invariants():
+    # x and v of the numpy features against the C oracle's invariants (pinned
+    # at 50 digits in test_oracle_physics), including collinear gamma = 1e3
+    import oracle
+    from paper_2206_02937_gb300 import workloads as wl
+    rng = np.random.default_rng(12)
+    u, k = wl.c3(500, seed=8)
+    d = rng.normal(size=3)
+    d /= np.linalg.norm(d)
+    u[:, :20] = (np.sqrt(1e6 - 1.0) * d)[:, None]
+    k[:, :20] = np.logspace(-4, 0, 20)[None, :] * (d[:, None] + 1e-4 * rng.normal(size=(3, 20)))
+    x, v = mlp.pair_invariants(u, k)
+    for i in range(500):
+        xr, vr = oracle.invariants(u[:, i], k[:, i])
+        assert abs(x[i] / xr - 1) < 1e-8 and abs(v[i] / vr - 1) < 1e-8, i
+    f = mlp.features(u, k, mode="invariants")
+    assert np.allclose(f[0], np.log(x) / 8) and np.allclose(f[1], np.log(v) / 8)
+    assert not f[2:].any()
