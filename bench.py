@@ -31,6 +31,13 @@ sys.path.insert(0, ROOT)
 METRIC = "Compton pair-scatters/s, plain vs MLP on 1 GB300 at stated error; p50/p99 lat"
 UNIT = "pairs/s"
 L2_NOTE = "inputs larger than L2 (particle state ~1.3 GB resident, 129 MB L2)"
+# DRAM bytes (read + write) per unit from one ncu capture of the kernel as it
+# is now, scaled to a launch by its units; the profile file gives the command.
+# A kernel changed since its capture must be taken out of this table.
+MEASURED_TRAFFIC = {
+    "k_sort_gather": (246.747904e6 / 8372876, "particle", "profiles/k_sort_gather_in_place_256x256.md"),
+    "k_count": (34.022912e6 / 8372876, "particle", "profiles/k_count_256x256.md"),
+}
 
 
 def parse():
@@ -274,8 +281,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                          "frac_of_hbm": gbs / hbm_peak}
     dom = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"] * kernels[k]["launches_per_step"])
     D = kernels[dom]
+    traffic = None
+    if dom in MEASURED_TRAFFIC:
+        per_unit, unit_name, src = MEASURED_TRAFFIC[dom]
+        traffic = per_unit * (n_part if unit_name == "particle" else pairs_per_step)
     roofline = {"kernel": dom, "bound": "hbm", "achieved": D["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                "frac": D["frac_of_hbm"], "traffic": None, "peak_source": peak_src,
+                "frac": D["frac_of_hbm"], "traffic": traffic,
+                "traffic_source": MEASURED_TRAFFIC[dom][2] if dom in MEASURED_TRAFFIC else None,
+                "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": D["algorithmic_bytes_per_launch"],
                 "avg_launch_ms": D["avg_launch_ms"],
                 "note": "dominant kernel of the step by device time; durations from CUDA events the library "
@@ -307,12 +320,26 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     torch.cuda.synchronize()
     ntc_ms = n0.elapsed_time(n1) / args.steps
     st_ntc = cg.compton_get_stats(ctx, reset=True)
+    # both collision schemes from the same particles, pairing and draws: the
+    # source buffer is left unchanged, each scheme bins it afresh
+    X, Y = bufs[step % 2], bufs[(step + 1) % 2]
+    same = {"ntc": 0, "pairing": 0}
+    for rep in range(3):
+        for scheme in ("ntc", "pairing"):
+            pr = cg.compton_bin_pairs(ctx, X[0], X[1], Y[0], Y[1], 9000 + rep, stream)
+            cg.compton_get_stats(ctx, reset=True)
+            if scheme == "ntc":
+                cg.compton_scatter_step_ntc(ctx, Y[0], Y[1], pr, 9000 + rep, stream)
+            else:
+                cg.compton_scatter_step(ctx, Y[0], Y[1], pr, cg.MODE_PLAIN, 9000 + rep, None, None, stream)
+            same[scheme] += cg.compton_get_stats(ctx, reset=True)["scatters"]
     ntc = {"ms_per_step": ntc_ms, "candidates_per_step": st_ntc["pairs_tested"] / args.steps,
+           "candidates_per_s": st_ntc["pairs_tested"] / args.steps / (ntc_ms * 1e-3),
            "collisions_per_step": st_ntc["scatters"] / args.steps,
-           "collisions_per_step_pairing": stats["scatters"] / args.steps,
-           "pairs_per_s_equivalent": pairs_per_step / (ntc_ms * 1e-3),
-           "note": "bin + NTC candidates per cell (one thread per cell, sequential in-cell updates); "
-                   "pairs_per_s_equivalent = the pairing method's pairs per step / NTC step time"}
+           "collision_ratio_ntc_to_pairing_same_state": same["ntc"] / max(1, same["pairing"]),
+           "note": "bin + NTC candidates per cell (one thread per cell, sequential in-cell updates); the ratio "
+                   "compares both schemes on the same binned particles over 3 draws (NTC uses the linear "
+                   "probability, pairing 1 - exp(-a): expected about 1 + n dt <s v>/2)"}
 
     # binning of shuffled input: 4 (count) + 20 (placement read) + 20 (record
     # write) + 20 (record read) + 20 (sorted write) = 84 B per particle
