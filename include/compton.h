@@ -57,7 +57,8 @@ typedef enum compton_mode {
     COMPTON_MODE_PLAIN = 0,    /* analytic probability (Klein-Nishina)      */
     COMPTON_MODE_MLP_FP32 = 1, /* surrogate network, FP32 operands          */
     COMPTON_MODE_MLP_BF16 = 2, /* surrogate network, BF16 operands          */
-    COMPTON_MODE_MLP_FP8 = 3   /* surrogate network, FP8 E4M3 operands      */
+    COMPTON_MODE_MLP_FP8 = 3,  /* surrogate network, FP8 E4M3 operands      */
+    COMPTON_MODE_PNET = 4      /* the paper's 9-12-9 network, FP32          */
 } compton_mode;
 
 /* Inputs of the surrogate network (compton_mlp_set_features). */
@@ -306,14 +307,68 @@ compton_status compton_mlp_get_grad(struct compton_ctx* ctx, float* grad_host, i
  * trained in that mode.  EINVAL for another value. */
 compton_status compton_mlp_set_features(struct compton_ctx* ctx, int32_t features);
 
-/* Serialise the network (format "CMLP" version 2: header with the Adam step,
- * feature scales and mode, activation scales, then parameters and both Adam
- * moments; version 1 blobs, without the mode, still load) to buf.  With buf NULL, *len receives the size needed; ERANGE if *len is too
- * small.  Synchronous. */
+/* The network's training range: pairs with gamma > gamma_max or eps outside
+ * [eps_min, eps_max] take the analytic probability instead (and are counted
+ * as fallbacks).  Default gamma_max = 1e3, eps in [1e-4, 1].  Saved with the
+ * network.  EINVAL unless 1 <= gamma_max, 0 <= eps_min < eps_max, finite. */
+compton_status compton_mlp_set_range(struct compton_ctx* ctx, double gamma_max, double eps_min, double eps_max);
+
+/* Serialise the network (format "CMLP" version 3: header with the Adam step,
+ * feature scales and mode, training range, activation scales, then parameters
+ * and both Adam moments; version 1 and 2 blobs still load, keeping the
+ * context's mode or range where they carry none) to buf.  With buf NULL,
+ * *len receives the size needed; ERANGE if *len is too small.
+ * Synchronous. */
 compton_status compton_mlp_save(struct compton_ctx* ctx, void* buf, size_t* len);
 
 /* Load a blob written by compton_mlp_save.  EINVAL on a bad header or size. */
 compton_status compton_mlp_load(struct compton_ctx* ctx, const void* buf, size_t len);
+
+/* ---------------------------------------------------------------------- */
+/* The paper's own network (Sec. 3.2, Fig. 2a): 9 inputs, hidden layers of */
+/* 9, 12 and 9 ReLU units, one sigmoid output; 337 FP32 parameters.        */
+/* ---------------------------------------------------------------------- */
+
+#define COMPTON_PNET_PARAMS 337
+
+/* Load the parameters theta (host, 337 floats, layer by layer: W0 (9 x 9),
+ * b0 (9), W1 (12 x 9), b1 (12), W2 (9 x 12), b2 (9), W3 (1 x 9), b3 (1), each
+ * W (out, in) row-major), reset the Adam state, and set the feature scales
+ * (host, 4 floats s_u, n_u, s_k, n_k, all > 0; NULL keeps the current ones,
+ * by default 1, 7, 1e-4, 10) and the training range (as for
+ * compton_mlp_set_range).  Inputs of a pair:
+ *   sgnlog(u_i / s_u) / n_u, sgnlog(k_i / s_k) / n_k   (i = x, y, z),
+ *   ln(w_e) / 8, ln(w_g) / 8, ln(P_max) / 8,
+ * sgnlog(z) = sign(z) ln(1 + |z|), w the macro-particle weight over the cell
+ * volume, P_max = 2 n dt the cell's probability bound (sigma_T c = 1); output
+ * r = sigma_KN v / (2 sigma_T).  After this call COMPTON_MODE_PNET is
+ * available to the scatter step, which gives both species the context's
+ * w_over_v.  EINVAL on a wrong count, scale or range.  Synchronous. */
+compton_status compton_pnet_set_params(struct compton_ctx* ctx, const float* theta_host, int64_t n_params,
+                                       const float* feature_scales_host, double gamma_max, double eps_min,
+                                       double eps_max);
+
+/* Copy the parameters and / or the gradient of the last train step (the loss
+ * normalised by sum w) to the host (either pointer may be NULL).  ENOMODEL
+ * before compton_pnet_set_params.  Synchronous. */
+compton_status compton_pnet_get_params(struct compton_ctx* ctx, float* theta_host, float* grad_host,
+                                       int64_t n_params);
+
+/* r for n explicit pairs (device SoA momenta, device r_out[n]) at the given
+ * weights and P_max (all > 0).  Asynchronous on stream. */
+compton_status compton_pnet_infer(struct compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
+                                  const float* kx, const float* ky, const float* kz, int64_t n, float w_e,
+                                  float w_g, float p_max, float* r_out, compton_stream_t stream);
+
+/* One Adam step (beta 0.9, 0.999, epsilon 1e-7) on the weighted mean absolute
+ * error sum_i w_i |y'_i - y_i| / sum_i w_i over n > 0 device samples (targets
+ * y, weights w, NULL = all 1); the ReLU and |.| subgradients at 0 are 0.  With
+ * loss_out_host non-NULL the step's loss (before the update) is written there
+ * and the call synchronises on stream; else it is asynchronous. */
+compton_status compton_pnet_train_step(struct compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
+                                       const float* kx, const float* ky, const float* kz, const float* y,
+                                       const float* w, int64_t n, float w_e, float w_g, float p_max, float lr,
+                                       float* loss_out_host, compton_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of pre-paired batches (Sec. 2: the network */

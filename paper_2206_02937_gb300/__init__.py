@@ -22,7 +22,8 @@ c_i32, c_i64, c_u32, c_u64, c_f32, c_f64, c_p = (ctypes.c_int32, ctypes.c_int64,
 
 COMPTON_OK, COMPTON_EINVAL, COMPTON_ENOMEM, COMPTON_EBUSY, COMPTON_ETIMEOUT, COMPTON_ERANGE, \
     COMPTON_ENOTREADY, COMPTON_ECUDA, COMPTON_ENOMODEL = range(9)
-MODE_PLAIN, MODE_MLP_FP32, MODE_MLP_BF16, MODE_MLP_FP8 = range(4)
+MODE_PLAIN, MODE_MLP_FP32, MODE_MLP_BF16, MODE_MLP_FP8, MODE_PNET = range(5)
+PNET_PARAMS = 337
 FEATURES_MOMENTA, FEATURES_INVARIANTS = 0, 1
 
 
@@ -381,11 +382,66 @@ def compton_mlp_balance_weights(ctx: int, r, edges, w_out, stream=None) -> None:
 
 
 SIGNATURES["compton_mlp_set_features"] = (c_i32, [c_p, c_i32])
+SIGNATURES["compton_mlp_set_range"] = (c_i32, [c_p, c_f64, c_f64, c_f64])
+
+
+def compton_mlp_set_range(ctx: int, gamma_max: float, eps_min: float, eps_max: float) -> None:
+    """Training range of the network (outside it: analytic probability)."""
+    _check(lib().compton_mlp_set_range(c_p(ctx), float(gamma_max), float(eps_min), float(eps_max)),
+           "compton_mlp_set_range", ctx)
 
 
 def compton_mlp_set_features(ctx: int, features: int) -> None:
     """Network inputs: FEATURES_MOMENTA (default) or FEATURES_INVARIANTS."""
     _check(lib().compton_mlp_set_features(c_p(ctx), int(features)), "compton_mlp_set_features", ctx)
+
+
+SIGNATURES["compton_pnet_set_params"] = (c_i32, [c_p, c_p, c_i64, c_p, c_f64, c_f64, c_f64])
+SIGNATURES["compton_pnet_get_params"] = (c_i32, [c_p, c_p, c_p, c_i64])
+SIGNATURES["compton_pnet_infer"] = (c_i32, [c_p] * 7 + [c_i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                                      c_p, c_p])
+SIGNATURES["compton_pnet_train_step"] = (c_i32, [c_p] * 9 + [c_i64] + [ctypes.c_float] * 4 + [c_p, c_p])
+
+
+def compton_pnet_set_params(ctx: int, theta, feature_scales=None, gamma_max: float = 1e3, eps_min: float = 1e-4,
+                            eps_max: float = 1.0) -> None:
+    """Load the paper network's 337 parameters (host array) and reset Adam."""
+    import numpy as np
+    t = np.ascontiguousarray(theta, dtype=np.float32)
+    fs = None if feature_scales is None else np.ascontiguousarray(feature_scales, dtype=np.float32)
+    _check(lib().compton_pnet_set_params(c_p(ctx), c_p(t.ctypes.data), int(t.shape[0]),
+                                         None if fs is None else c_p(fs.ctypes.data), float(gamma_max),
+                                         float(eps_min), float(eps_max)), "compton_pnet_set_params", ctx)
+
+
+def compton_pnet_get_params(ctx: int):
+    """(theta, grad of the last train step) as float32 host arrays."""
+    import numpy as np
+    t = np.zeros(PNET_PARAMS, np.float32)
+    g = np.zeros(PNET_PARAMS, np.float32)
+    _check(lib().compton_pnet_get_params(c_p(ctx), c_p(t.ctypes.data), c_p(g.ctypes.data), PNET_PARAMS),
+           "compton_pnet_get_params", ctx)
+    return t, g
+
+
+def compton_pnet_infer(ctx: int, u, k, w_e: float, w_g: float, p_max: float, r_out, stream=None) -> None:
+    """u, k: (3, n) float32 CUDA tensors; r_out: (n,) float32."""
+    _check(lib().compton_pnet_infer(c_p(ctx), _ptr(u[0]), _ptr(u[1]), _ptr(u[2]), _ptr(k[0]), _ptr(k[1]),
+                                    _ptr(k[2]), int(u.shape[1]), float(w_e), float(w_g), float(p_max),
+                                    _ptr(r_out), _stream_ptr(stream)), "compton_pnet_infer", ctx)
+
+
+def compton_pnet_train_step(ctx: int, u, k, y, w, w_e: float, w_g: float, p_max: float, lr: float,
+                            want_loss: bool = True, stream=None):
+    """One Adam step on the weighted MAE; returns the loss before the update
+    (synchronising) when want_loss, else None."""
+    loss = ctypes.c_float(0.0)
+    _check(lib().compton_pnet_train_step(c_p(ctx), _ptr(u[0]), _ptr(u[1]), _ptr(u[2]), _ptr(k[0]), _ptr(k[1]),
+                                         _ptr(k[2]), _ptr(y), None if w is None else _ptr(w), int(u.shape[1]),
+                                         float(w_e), float(w_g), float(p_max), float(lr),
+                                         ctypes.byref(loss) if want_loss else None, _stream_ptr(stream)),
+           "compton_pnet_train_step", ctx)
+    return float(loss.value) if want_loss else None
 
 
 KERNEL_SLOTS = ("k_count", "k_scan", "k_place", "k_sort_gather", "k_pair_prob", "k_collide", "k_mlp", "k_ntc")

@@ -127,6 +127,7 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     }
     size_t o_tr = cv.take<uint8_t>(cfg->max_train_batch > 0 ? compton::train_scratch_bytes(cfg->max_train_batch) : 1);
     size_t o_rb = cv.take<float>(P > 0 ? P : 1);
+    size_t o_pn = cv.take<float>(4 * compton::kPnetParams + 2);
     const size_t total = align_up(cv.used, 256);
     if (cfg->mem_budget_bytes && total > cfg->mem_budget_bytes) {
         delete ctx;
@@ -176,11 +177,31 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     m.hist = reinterpret_cast<int*>(base + o_hi);
     ctx->train_scratch = base + o_tr;
     ctx->r_buf = reinterpret_cast<float*>(base + o_rb);
+    {
+        float* pb = reinterpret_cast<float*>(base + o_pn);
+        compton::PnetDev& pn = ctx->pnet;
+        pn.theta = pb;
+        pn.grad = pb + compton::kPnetParams;
+        pn.adam_m = pb + 2 * compton::kPnetParams;
+        pn.adam_v = pb + 3 * compton::kPnetParams;
+        pn.loss = pb + 4 * compton::kPnetParams;
+        pn.fs[0] = 1.0f;
+        pn.fs[1] = 7.0f;
+        pn.fs[2] = 1e-4f;
+        pn.fs[3] = 10.0f;
+        pn.range[0] = 1.0e6f;
+        pn.range[1] = 1.0e-8f;
+        pn.range[2] = 1.0f;
+        pn.step = 0;
+    }
     m.fs[0] = 1.0f;   // s_u
     m.fs[1] = 7.0f;   // n_u
     m.fs[2] = 1e-4f;  // s_k
     m.fs[3] = 10.0f;  // n_k
     m.feat_mode = COMPTON_FEATURES_MOMENTA;
+    m.range_g2max = 1.0e6f;  // gamma <= 1e3
+    m.range_e2min = 1.0e-8f; // eps >= 1e-4
+    m.range_e2max = 1.0f;    // eps <= 1
     e = cudaMemset(ctx->arena, 0, total);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -323,8 +344,9 @@ compton_status compton_scatter_step(compton_ctx* ctx, compton_species* e, compto
     if (!ctx || !pairs || !species_ok(e) || !species_ok(g)) return COMPTON_EINVAL;
     if (pairs->cell_info_dev != ctx->cinfo || pairs->n_cells != ctx->cfg.n_cells) return COMPTON_EINVAL;
     if (pairs->max_pairs > (e->n < g->n ? e->n : g->n)) return COMPTON_EINVAL;
-    if ((int)mode < 0 || (int)mode > 3) return COMPTON_EINVAL;
-    if (mode != COMPTON_MODE_PLAIN && !ctx->mlp_loaded) return COMPTON_ENOMODEL;
+    if ((int)mode < 0 || (int)mode > 4) return COMPTON_EINVAL;
+    if (mode == COMPTON_MODE_PNET ? !ctx->pnet_loaded : (mode != COMPTON_MODE_PLAIN && !ctx->mlp_loaded))
+        return COMPTON_ENOMODEL;
     return compton::launch_scatter_binned(ctx, e, g, pairs, mode, step, prob_out, flag_out, stream);
 }
 
@@ -471,7 +493,9 @@ struct MlpBlobHeader {
     MlpBlobHeaderV1 v1;
     int32_t feat_mode;
     int32_t reserved;
+    float range[4];  // version 3: gamma^2 max, eps^2 min, eps^2 max, unused
 };
+constexpr size_t kBlobHeadV2 = sizeof(MlpBlobHeaderV1) + 2 * sizeof(int32_t);
 }  // namespace
 
 compton_status compton_mlp_save(compton_ctx* ctx, void* buf, size_t* len)
@@ -487,12 +511,16 @@ compton_status compton_mlp_save(compton_ctx* ctx, void* buf, size_t* len)
     COMPTON_CUDA_TRY(ctx, cudaDeviceSynchronize());
     MlpBlobHeader h;
     std::memcpy(h.v1.magic, "CMLP", 4);
-    h.v1.version = 2;
+    h.v1.version = 3;
     h.v1.n_params = (int64_t)NP;
     h.v1.adam_step = ctx->adam_step;
     for (int i = 0; i < 4; ++i) h.v1.fs[i] = ctx->mlp.fs[i];
     h.feat_mode = ctx->mlp.feat_mode;
     h.reserved = 0;
+    h.range[0] = ctx->mlp.range_g2max;
+    h.range[1] = ctx->mlp.range_e2min;
+    h.range[2] = ctx->mlp.range_e2max;
+    h.range[3] = 0.0f;
     COMPTON_CUDA_TRY(ctx, cudaMemcpy(h.v1.scale_a_inv, ctx->mlp.scale_a_inv, sizeof(h.v1.scale_a_inv),
                                      cudaMemcpyDeviceToHost));
     char* p = static_cast<char*>(buf);
@@ -513,21 +541,23 @@ compton_status compton_mlp_load(compton_ctx* ctx, const void* buf, size_t len)
     MlpBlobHeaderV1 h;
     std::memcpy(&h, buf, sizeof(h));
     const size_t NP = compton::kMlpParams;
-    if (std::memcmp(h.magic, "CMLP", 4) != 0 || (h.version != 1 && h.version != 2) || h.n_params != (int64_t)NP)
+    if (std::memcmp(h.magic, "CMLP", 4) != 0 || h.version < 1 || h.version > 3 || h.n_params != (int64_t)NP)
         return COMPTON_EINVAL;
-    const size_t head = h.version == 1 ? sizeof(MlpBlobHeaderV1) : sizeof(MlpBlobHeader);
+    const size_t head = h.version == 1 ? sizeof(MlpBlobHeaderV1) : (h.version == 2 ? kBlobHeadV2 : sizeof(MlpBlobHeader));
     if (len != head + 3 * NP * sizeof(float)) return COMPTON_EINVAL;
-    int32_t mode = COMPTON_FEATURES_MOMENTA;
-    if (h.version == 2) {
-        MlpBlobHeader h2;
-        std::memcpy(&h2, buf, sizeof(h2));
-        mode = h2.feat_mode;
-        if (mode != COMPTON_FEATURES_MOMENTA && mode != COMPTON_FEATURES_INVARIANTS) return COMPTON_EINVAL;
-    }
+    MlpBlobHeader h3{};
+    std::memcpy(&h3, buf, head);
+    const int32_t mode = h.version >= 2 ? h3.feat_mode : (int32_t)COMPTON_FEATURES_MOMENTA;
+    if (mode != COMPTON_FEATURES_MOMENTA && mode != COMPTON_FEATURES_INVARIANTS) return COMPTON_EINVAL;
     const char* p = static_cast<const char*>(buf) + head;
     compton_status st = compton_mlp_set_params(ctx, reinterpret_cast<const float*>(p), (int64_t)NP, h.fs);
     if (st != COMPTON_OK) return st;
     ctx->mlp.feat_mode = mode;
+    if (h.version >= 3) {
+        ctx->mlp.range_g2max = h3.range[0];
+        ctx->mlp.range_e2min = h3.range[1];
+        ctx->mlp.range_e2max = h3.range[2];
+    }
     p += NP * sizeof(float);
     COMPTON_CUDA_TRY(ctx, cudaMemcpy(ctx->mlp.adam_m, p, NP * sizeof(float), cudaMemcpyHostToDevice));
     p += NP * sizeof(float);
@@ -535,6 +565,86 @@ compton_status compton_mlp_load(compton_ctx* ctx, const void* buf, size_t len)
     COMPTON_CUDA_TRY(ctx, cudaMemcpy(ctx->mlp.scale_a_inv, h.scale_a_inv, sizeof(h.scale_a_inv),
                                      cudaMemcpyHostToDevice));
     ctx->adam_step = h.adam_step;
+    return COMPTON_OK;
+}
+
+compton_status compton_mlp_set_range(compton_ctx* ctx, double gamma_max, double eps_min, double eps_max)
+{
+    if (!ctx) return COMPTON_EINVAL;
+    if (!(gamma_max >= 1.0) || !(eps_min >= 0.0) || !(eps_max > eps_min) || std::isinf(eps_max) ||
+        std::isinf(gamma_max))
+        return COMPTON_EINVAL;
+    ctx->mlp.range_g2max = (float)(gamma_max * gamma_max);
+    ctx->mlp.range_e2min = (float)(eps_min * eps_min);
+    ctx->mlp.range_e2max = (float)(eps_max * eps_max);
+    return COMPTON_OK;
+}
+
+compton_status compton_pnet_set_params(compton_ctx* ctx, const float* theta_host, int64_t n_params,
+                                      const float* feature_scales_host, double gamma_max, double eps_min,
+                                      double eps_max)
+{
+    if (!ctx || !theta_host || n_params != compton::kPnetParams) return COMPTON_EINVAL;
+    if (!(gamma_max >= 1.0) || !(eps_min >= 0.0) || !(eps_max > eps_min) || std::isinf(eps_max) ||
+        std::isinf(gamma_max))
+        return COMPTON_EINVAL;
+    compton::PnetDev& pn = ctx->pnet;
+    if (feature_scales_host) {
+        for (int i = 0; i < 4; ++i)
+            if (!(feature_scales_host[i] > 0.0f)) return COMPTON_EINVAL;
+        for (int i = 0; i < 4; ++i) pn.fs[i] = feature_scales_host[i];
+    }
+    pn.range[0] = (float)(gamma_max * gamma_max);
+    pn.range[1] = (float)(eps_min * eps_min);
+    pn.range[2] = (float)(eps_max * eps_max);
+    COMPTON_CUDA_TRY(ctx, cudaSetDevice(ctx->cfg.device));
+    COMPTON_CUDA_TRY(ctx, cudaMemcpy(pn.theta, theta_host, sizeof(float) * compton::kPnetParams,
+                                     cudaMemcpyHostToDevice));
+    COMPTON_CUDA_TRY(ctx, cudaMemset(pn.adam_m, 0, sizeof(float) * 2 * compton::kPnetParams));
+    pn.step = 0;
+    ctx->pnet_loaded = true;
+    return COMPTON_OK;
+}
+
+compton_status compton_pnet_get_params(compton_ctx* ctx, float* theta_host, float* grad_host, int64_t n_params)
+{
+    if (!ctx || n_params != compton::kPnetParams) return COMPTON_EINVAL;
+    if (!ctx->pnet_loaded) return COMPTON_ENOMODEL;
+    COMPTON_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    if (theta_host)
+        COMPTON_CUDA_TRY(ctx, cudaMemcpy(theta_host, ctx->pnet.theta, sizeof(float) * compton::kPnetParams,
+                                         cudaMemcpyDeviceToHost));
+    if (grad_host)
+        COMPTON_CUDA_TRY(ctx, cudaMemcpy(grad_host, ctx->pnet.grad, sizeof(float) * compton::kPnetParams,
+                                         cudaMemcpyDeviceToHost));
+    return COMPTON_OK;
+}
+
+compton_status compton_pnet_infer(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
+                                  const float* kx, const float* ky, const float* kz, int64_t n, float w_e,
+                                  float w_g, float p_max, float* r_out, compton_stream_t stream)
+{
+    if (!ctx || n < 0 || (n > 0 && (!ux || !uy || !uz || !kx || !ky || !kz || !r_out))) return COMPTON_EINVAL;
+    if (!(w_e > 0.0f) || !(w_g > 0.0f) || !(p_max > 0.0f)) return COMPTON_EINVAL;
+    if (!ctx->pnet_loaded) return COMPTON_ENOMODEL;
+    return compton::launch_pnet_infer(ctx, ux, uy, uz, kx, ky, kz, n, w_e, w_g, p_max, r_out, stream);
+}
+
+compton_status compton_pnet_train_step(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
+                                       const float* kx, const float* ky, const float* kz, const float* y,
+                                       const float* w, int64_t n, float w_e, float w_g, float p_max, float lr,
+                                       float* loss_out_host, compton_stream_t stream)
+{
+    if (!ctx || n <= 0 || !ux || !uy || !uz || !kx || !ky || !kz || !y) return COMPTON_EINVAL;
+    if (!(w_e > 0.0f) || !(w_g > 0.0f) || !(p_max > 0.0f) || !(lr >= 0.0f)) return COMPTON_EINVAL;
+    if (!ctx->pnet_loaded) return COMPTON_ENOMODEL;
+    compton_status st =
+        compton::launch_pnet_train_step(ctx, ux, uy, uz, kx, ky, kz, y, w, n, w_e, w_g, p_max, lr, stream);
+    if (st != COMPTON_OK || !loss_out_host) return st;
+    float l[2];
+    COMPTON_CUDA_TRY(ctx, cudaMemcpyAsync(l, ctx->pnet.loss, sizeof(l), cudaMemcpyDeviceToHost, stream));
+    COMPTON_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+    *loss_out_host = l[1] > 0.0f ? l[0] / l[1] : 0.0f;
     return COMPTON_OK;
 }
 

@@ -108,6 +108,29 @@ struct MlpDev {
     int* hist;           // [256] data-balancing counts
     float fs[4];         // feature scales s_u, n_u, s_k, n_k
     int32_t feat_mode;   // compton_features: momenta or invariants
+    // training range: pairs outside it take the analytic probability
+    float range_g2max;   // gamma^2 at most
+    float range_e2min;   // eps^2 at least
+    float range_e2max;   // eps^2 at most
+};
+
+// Whether a pair lies in the network's training range (gamma^2 = g2, eps^2 = e2).
+__host__ __device__ inline bool mlp_in_range(const MlpDev& m, float g2, float e2)
+{
+    return g2 <= m.range_g2max && e2 >= m.range_e2min && e2 <= m.range_e2max;
+}
+
+// The paper's own network (9-12-9 ReLU, sigmoid): 337 parameters.
+constexpr int kPnetParams = 337;
+struct PnetDev {
+    float* theta;   // [kPnetParams]
+    float* grad;    // [kPnetParams], divided by the weight sum after a step
+    float* adam_m;  // [kPnetParams]
+    float* adam_v;  // [kPnetParams]
+    float* loss;    // [2] weighted |error| sum, weight sum of the last step
+    float fs[4];    // feature scales s_u, n_u, s_k, n_k
+    float range[3]; // training range: gamma^2 max, eps^2 min, eps^2 max
+    int64_t step;   // Adam steps taken
 };
 
 struct ServeEngine;
@@ -155,6 +178,8 @@ struct compton_ctx {
     float* r_buf = nullptr;         // [max_particles] network output per pair (surrogate modes)
     compton::ServeEngine* serve = nullptr;  // continuous-batching engine (compton_serve_start)
     compton::KernelTiming* timing = nullptr;  // per-kernel event pairs (compton_kernel_timing)
+    compton::PnetDev pnet{};                  // the paper's 9-12-9 network
+    bool pnet_loaded = false;
 };
 
 namespace compton {
@@ -212,6 +237,14 @@ compton_status launch_scatter_binned(compton_ctx* ctx, compton_species* e, compt
 compton_status launch_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, float* uz, float* kx, float* ky,
                                     float* kz, const float* n_dens, int64_t n, uint64_t seed, uint64_t step,
                                     compton_mode mode, float* prob_out, uint8_t* flag_out, cudaStream_t stream);
+compton_status launch_pnet_infer(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
+                                 const float* kx, const float* ky, const float* kz, int64_t n, float w_e, float w_g,
+                                 float p_max, float* r_out, cudaStream_t stream);
+compton_status launch_pnet_decide(compton_ctx* ctx, int64_t rows, const MlpDecide& dec, cudaStream_t stream);
+compton_status launch_pnet_train_step(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
+                                      const float* kx, const float* ky, const float* kz, const float* y,
+                                      const float* w, int64_t n, float w_e, float w_g, float p_max, float lr,
+                                      cudaStream_t stream);
 compton_status launch_scatter_ntc(compton_ctx* ctx, compton_species* e, compton_species* g,
                                   const compton_pairs* pairs, uint64_t step, cudaStream_t stream);
 compton_status launch_kn_ratio(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,

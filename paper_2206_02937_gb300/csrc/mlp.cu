@@ -159,7 +159,8 @@ struct MlpArgs {
 
 // Probability and decision of candidate row `row` from its network output
 // (pre-sigmoid z) and momenta q: P = 1 - exp(-2 n dt r) inside the network's
-// training range (gamma <= 1e3, eps in [1e-4, 1]), else the analytic
+// training range (compton_mlp_set_range; by default gamma <= 1e3, eps in
+// [1e-4, 1]), else the analytic
 // probability (counted); accepted rows go to the list with their momenta.
 // Called by every thread of a warp.
 __device__ __forceinline__ void decide_row(const MlpArgs& a, int64_t row, bool live, float z, const float* q)
@@ -174,7 +175,7 @@ __device__ __forceinline__ void decide_row(const MlpArgs& a, int64_t row, bool l
         const float g2 = fmaf(q[0], q[0], fmaf(q[1], q[1], fmaf(q[2], q[2], 1.0f)));
         const float e2 = fmaf(q[3], q[3], fmaf(q[4], q[4], q[5] * q[5]));
         float P;
-        if (g2 <= 1.0e6f && e2 >= 1.0e-8f && e2 <= 1.0f) {
+        if (mlp_in_range(a.m, g2, e2)) {
             P = one_minus_exp_neg(2.0f * c.dens * a.dec.dt * r);
         } else {
             fb = true;

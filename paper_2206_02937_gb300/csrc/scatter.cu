@@ -54,6 +54,7 @@ struct ScatterArgs {
     uint32_t* n_accepted;
     CandPair* cand;
     uint32_t* n_cand;
+    MlpDev mlp;  // the network's training range (surrogate modes)
 };
 
 __device__ __forceinline__ int find_cell(const CellInfo* win, int nwin, int64_t p)
@@ -375,7 +376,7 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_cand(ScatterArgs a)
 
 // Surrogate modes, third kernel: every candidate's probability from its
 // network output r (P = 1 - exp(-2 n dt r)) or, outside the network's
-// training range (gamma > 1e3, eps outside [1e-4, 1]), from the analytic
+// training range (compton_mlp_set_range), from the analytic
 // path (counted); the decision; accepted pairs to the list.
 __global__ void __launch_bounds__(256) k_decide(ScatterArgs a)
 {
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(256) k_decide(ScatterArgs a)
             const float g2 = fmaf(ux, ux, fmaf(uy, uy, fmaf(uz, uz, 1.0f)));
             const float e2 = fmaf(kx, kx, fmaf(ky, ky, kz * kz));
             float P;
-            if (g2 <= 1.0e6f && e2 >= 1.0e-8f && e2 <= 1.0f) {
+            if (mlp_in_range(a.mlp, g2, e2)) {
                 P = one_minus_exp_neg(2.0f * c.dens * a.dt * a.r_mlp[i]);
             } else {
                 ++n_fb;
@@ -571,6 +572,7 @@ void fill_common(ScatterArgs& a, compton_ctx* ctx, uint64_t seed, uint64_t step,
     a.n_accepted = ctx->n_accepted;
     a.cand = ctx->cand;
     a.n_cand = ctx->n_cand;
+    a.mlp = ctx->mlp;
 }
 
 // The step after the pair list is known: probability and trial of every
@@ -592,9 +594,19 @@ compton_status launch_step(compton_ctx* ctx, ScatterArgs& a, compton_mode mode, 
             k_cand<kBinned><<<tiles, kProbThreads, 0, stream>>>(a);
         }
         COMPTON_LAUNCH_CHECK(ctx, "k_cand");
-        // tensor-core modes decide inside the network kernel; the FP32
-        // network writes r and k_decide decides
+        // tensor-core modes and the paper's network decide inside the network
+        // kernel; the FP32 network writes r and k_decide decides
         const MlpDecide dec{a.dt, a.gamma64, a.prob_out, a.flag_out};
+        if (mode == COMPTON_MODE_PNET) {
+            const compton_status sp = launch_pnet_decide(ctx, rows, dec, stream);
+            if (sp != COMPTON_OK) return sp;
+            {
+                TimedScope ts_(ctx, COMPTON_K_COLLIDE, stream);
+                k_collide<<<collide_grid(rows), 256, 0, stream>>>(a);
+            }
+            COMPTON_LAUNCH_CHECK(ctx, "k_collide");
+            return COMPTON_OK;
+        }
         const bool fused = mode != COMPTON_MODE_MLP_FP32;
         compton_status st = launch_mlp_infer(ctx, a.u[0], a.u[1], a.u[2], a.k[0], a.k[1], a.k[2], rows, mode,
                                              ctx->r_buf, stream, false, true, fused ? &dec : nullptr);
@@ -621,7 +633,8 @@ compton_status launch_scatter_binned(compton_ctx* ctx, compton_species* e, compt
 {
     if (pairs->max_pairs <= 0) return COMPTON_OK;
     if (pairs->max_pairs > ctx->accepted_cap) return COMPTON_ERANGE;
-    if (mode != COMPTON_MODE_PLAIN && pairs->max_pairs > ctx->cfg.max_particles) return COMPTON_ERANGE;
+    if (mode != COMPTON_MODE_PLAIN && mode != COMPTON_MODE_PNET && pairs->max_pairs > ctx->cfg.max_particles)
+        return COMPTON_ERANGE;
     ScatterArgs a;
     a.u[0] = e->ux_dev;
     a.u[1] = e->uy_dev;
@@ -645,7 +658,7 @@ compton_status launch_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, floa
                                     compton_mode mode, float* prob_out, uint8_t* flag_out, cudaStream_t stream)
 {
     if (n <= 0) return COMPTON_OK;
-    if (mode != COMPTON_MODE_PLAIN && n > ctx->cfg.max_particles) return COMPTON_ERANGE;
+    if (mode != COMPTON_MODE_PLAIN && mode != COMPTON_MODE_PNET && n > ctx->cfg.max_particles) return COMPTON_ERANGE;
     ScatterArgs a;
     a.u[0] = ux;
     a.u[1] = uy;

@@ -96,7 +96,7 @@ __device__ __forceinline__ void serve_resolve(const ReqDev* reqs, const SQEntry&
 // arithmetic is that of k_scatter on explicit pairs (same device functions).
 __global__ void __launch_bounds__(kServeThreads, 3)
     k_serve(const ReqDev* __restrict__ reqs, const TileDev* __restrict__ tiles, int n_tiles, float dt, float gamma64,
-            float c64sq, DeviceStats* stats)
+            float c64sq, DeviceStats* stats, MlpDev mlp)
 {
     __shared__ SQEntry queue[kServeQueueCap];
     __shared__ int qn;
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kServeThreads, 3)
             if (R.mode != COMPTON_MODE_PLAIN) {
                 const float g2 = fmaf(ux, ux, fmaf(uy, uy, fmaf(uz, uz, 1.0f)));
                 const float e2 = fmaf(kx, kx, fmaf(ky, ky, kz * kz));
-                if (g2 <= 1.0e6f && e2 >= 1.0e-8f && e2 <= 1.0f) {
+                if (mlp_in_range(mlp, g2, e2)) {
                     analytic = false;
                     P = one_minus_exp_neg(2.0f * dens * dt * R.r_mlp[p]);
                 }
@@ -347,7 +347,7 @@ void launch_tiles(ServeEngine* E)
     const compton_config& cfg = E->ctx->cfg;
     k_serve<<<grid, kServeThreads, 0, E->s_compute>>>(E->reqs_dev, td, nt, (float)cfg.dt, cfg.gamma_fp64_threshold,
                                                       cfg.collide_fp64_threshold * cfg.collide_fp64_threshold,
-                                                      E->ctx->stats);
+                                                      E->ctx->stats, E->ctx->mlp);
     cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming);
     cudaEventRecord(L.ev, E->s_compute);
     E->inflight.push_back(std::move(L));

@@ -148,6 +148,38 @@ def c5(n_side: int = 256, ppc: int = 16, seed: int = 5) -> Workload:
                     seed, 20, _species(ue, cell), _species(kg, cell))
 
 
+def waterbag(rng, n: int, p0: float) -> np.ndarray:
+    """(3, n) momenta of an isotropic waterbag: uniform in the ball |p| <= p0
+    (Sec. 3.2 writes f(p) = n0 H(p + p0); read as H(p0 - |p|), the form that
+    confines the momenta)."""
+    r = p0 * rng.uniform(0.0, 1.0, n) ** (1.0 / 3.0)
+    return r * isotropic(rng, n)
+
+
+def waterbag_pairs(n: int, p0: float, seed: int = 25) -> tuple[np.ndarray, np.ndarray]:
+    """Training pairs of one transfer-learning stage: electrons and photons
+    both from the waterbag of radius p0 (the plasmas of Sec. 3.2's
+    training simulations), float32 (3, n) each."""
+    rng = rng_for(seed)
+    return waterbag(rng, n, p0).astype(np.float32), waterbag(rng, n, p0).astype(np.float32)
+
+
+def inverse_compton(p_e: float, eps: float = 2.5, n_cells: int = 512, ppc: int = 128, seed: int = 60,
+                    dt: float = 0.05) -> Workload:
+    """The inverse-Compton benchmark of Sec. 3.3: a monoenergetic electron
+    beam (momentum p_e along +x) crossing a monoenergetic isotropic photon gas
+    (energy eps), ppc of each species in every one of n_cells 1D cells,
+    density 1 (w/V = 1/ppc)."""
+    rng = rng_for(seed)
+    n = n_cells * ppc
+    cell = np.repeat(np.arange(n_cells), ppc)
+    ue = np.zeros((3, n))
+    ue[0] = p_e
+    kg = eps * isotropic(rng, n)
+    return Workload(f"inverse Compton: p_e {p_e} beam on an isotropic eps {eps} photon gas", n_cells, 1.0 / ppc,
+                    dt, seed, 1, _species(ue, cell), _species(kg, cell))
+
+
 def pair_arrays(w: Workload) -> tuple[np.ndarray, np.ndarray]:
     """The (3, n) momentum arrays of a workload's species (no pairing)."""
     u = np.stack([w.e["ux"], w.e["uy"], w.e["uz"]])
