@@ -458,6 +458,43 @@ def train_surrogate(cg, torch, ctx, dev, n_samples=1 << 20, steps=8000, batch=81
             "loss_first": losses[0], "loss_last": losses[-1], "train_s": train_s}
 
 
+def train_pnet(cg, torch, ctx, dev, w_cell, p_max_cells, n_samples=1 << 20, steps=8000, batch=8192, lr=1e-2):
+    """Train the paper's 9-12-9 network on the same analytic targets.  Its
+    inputs also carry the weights (w/V of both species) and the cell's P_max;
+    each Adam step takes the P_max of a random cell of the workload, so the
+    network sees the spread of densities it meets in the step."""
+    from paper_2206_02937_gb300 import workloads as wl
+    rng = np.random.default_rng(2)
+    theta = np.zeros(cg.PNET_PARAMS, dtype=np.float32)
+    at = 0
+    for o, i in [(9, 9), (12, 9), (9, 12), (1, 9)]:
+        lim = np.sqrt(6.0 / (o + i))
+        theta[at:at + o * i] = rng.uniform(-lim, lim, o * i)
+        at += o * i + o
+    cg.compton_pnet_set_params(ctx, theta)
+    u, k = wl.c3(n_samples, seed=30)
+    ut, kt = torch.from_numpy(u).to(dev), torch.from_numpy(k).to(dev)
+    r = torch.zeros(n_samples, device=dev)
+    cg.compton_kn_ratio(ctx, ut, kt, r)
+    gen = torch.Generator(device=dev).manual_seed(2)
+    pm = rng.choice(p_max_cells, steps)
+    losses = []
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for it in range(steps):
+        idx = torch.randint(0, n_samples, (batch,), device=dev, generator=gen)
+        lr_it = lr * 0.5 * (1.0 + np.cos(np.pi * it / steps))
+        loss = cg.compton_pnet_train_step(ctx, ut[:, idx].contiguous(), kt[:, idx].contiguous(), r[idx].contiguous(),
+                                          None, w_cell, w_cell, float(pm[it]), lr_it,
+                                          want_loss=(it % 500 == 0 or it == steps - 1))
+        if loss is not None:
+            losses.append(loss)
+    torch.cuda.synchronize()
+    return {"steps": steps, "batch": batch, "lr": f"{lr} cosine-decayed to 0", "samples": n_samples,
+            "loss": "MAE", "loss_first": losses[0], "loss_last": losses[-1], "train_s": time.time() - t0,
+            "p_max": "per step, that of a random cell of the workload"}
+
+
 def run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step0, peaks):
     """The whole step with the surrogate probability (BF16 tensor cores), its
     network kernel alone, and its error against the analytic path on the same
@@ -569,13 +606,52 @@ def run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step0, peaks):
                  "collision_rate_ratio": n_iv / max(1, n_pl),
                  "spectrum_L1": float((h_iv - h_pl).abs().sum()), "train": train_inv}
     cg.compton_mlp_load(ctx, blob)
+
+    # the paper's own 9-12-9 ReLU network (FP32, CUDA cores)
+    cnt = np.maximum(np.bincount(w.e["cell"], minlength=w.n_cells), np.bincount(w.g["cell"], minlength=w.n_cells))
+    p_max_cells = 2.0 * w.dt * w.w_over_v * cnt[cnt > 0].astype(np.float64)
+    train_pn = train_pnet(cg, torch, ctx, dev, w.w_over_v, p_max_cells, steps=args.train_steps)
+    P_pn = torch.empty(n, device=dev)
+    h_pn, n_pn = scattered_spectrum(cg.MODE_PNET, P_pn)
+    pnv = P_pn[:np_pairs].double()
+    rel_pn = ((pnv - pl).abs() / pl.clamp_min(1e-30))
+    for _ in range(args.warmup):
+        one(bufs[step % 2], bufs[(step + 1) % 2], step, cg.MODE_PNET)
+        step += 1
+    torch.cuda.synchronize()
+    cg.compton_get_stats(ctx, reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one(bufs[step % 2], bufs[(step + 1) % 2], step, cg.MODE_PNET)
+        step += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_pn = e0.elapsed_time(e1)
+    st_pn = cg.compton_get_stats(ctx, reset=True)
+    pm_med = float(np.median(p_max_cells))
+    cg.compton_pnet_infer(ctx, u, k, w.w_over_v, w.w_over_v, pm_med, rr, stream)
+    e0.record(stream)
+    for _ in range(3):
+        cg.compton_pnet_infer(ctx, u, k, w.w_over_v, w.w_over_v, pm_med, rr, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kern_pn = e0.elapsed_time(e1) / 3
+    pnet = {"network": "9-12-9 ReLU, sigmoid output, 337 parameters, FP32 on the CUDA cores",
+            "value": st_pn["pairs_tested"] / (ms_pn * 1e-3), "unit": UNIT, "ms_per_step": ms_pn / args.steps,
+            "network_kernel_ms": kern_pn, "network_samples": n,
+            "network_kernel_bytes_per_sample": 28,
+            "mean_rel_P": float(rel_pn.mean()), "median_rel_P": float(rel_pn.median()),
+            "p99_rel_P": float(rel_pn[::4].float().quantile(0.99)),
+            "collision_rate_ratio": n_pn / max(1, n_pl),
+            "spectrum_L1": float((h_pn - h_pl).abs().sum()), "train": train_pn}
     return {"mode": "bf16", "metric": METRIC, "value": st["pairs_tested"] / (ms * 1e-3), "unit": UNIT,
             "ms_per_step": ms / args.steps, "fallback_fraction": st["mlp_fallbacks"] / max(1, st["pairs_tested"]),
             "network_kernel_ms": kern, "network_samples": n,
             "roofline": {"kernel": "k_mlp_tc<bf16>", "bound": "tensor", "achieved": achieved, "peak": peak_bf16,
                          "unit": "TFLOP/s", "frac": achieved / peak_bf16,
                          "note": "algorithmic FLOPs 2(6*64+3*64*64+64) per sample; peak: measured bf16 burst"},
-            "error_vs_plain": err, "train": train, "invariant_features": invariant}
+            "error_vs_plain": err, "train": train, "invariant_features": invariant, "paper_network": pnet}
 
 
 def run_serving(args, cg, torch, ctx, src, dev):
@@ -832,7 +908,7 @@ IC_RANGE = (100.01, 1e-4, 100.0)       # gamma_max, eps_min, eps_max of the trai
 
 
 def train_tl(cg, torch, ctx, dev, stages=(25.0, 50.0, 100.0), n_set=1 << 19, steps=(6000, 3000, 3000),
-             lr=(1e-2, 3e-3, 3e-3), batch=8192):
+             lr=(3e-3, 1e-3, 1e-3), batch=8192):
     """Three-stage transfer learning (Sec. 3.2): stage s trains on the union of
     the waterbag data sets of radius up to p0_s, starting from the weights of
     the previous stage, with the learning rate decayed on a cosine within each
@@ -857,6 +933,14 @@ def train_tl(cg, torch, ctx, dev, stages=(25.0, 50.0, 100.0), n_set=1 << 19, ste
         n = ut.shape[1]
         r = torch.zeros(n, device=dev)
         cg.compton_kn_ratio(ctx, ut, kt, r)
+        if s_i == 0:
+            # output bias at the logit of the median target: the targets of
+            # these sets lie near 1e-3, and from sigmoid(0) Adam drives the
+            # output into the flat tail of the sigmoid before it learns
+            rm = float(r.median())
+            theta[-1] = np.log(rm / (1.0 - rm))
+            cg.compton_mlp_set_params(ctx, theta, np.array(IC_FS, dtype=np.float32))
+            cg.compton_mlp_set_range(ctx, *IC_RANGE)
         first = last = None
         for it in range(steps[s_i]):
             idx = torch.randint(0, n, (batch,), device=dev, generator=gen)
@@ -873,6 +957,54 @@ def train_tl(cg, torch, ctx, dev, stages=(25.0, 50.0, 100.0), n_set=1 << 19, ste
         info.append({"p0": p0, "samples": n, "steps": steps[s_i], "lr": lr[s_i], "loss_first": first,
                      "loss_last": last})
     return blobs, info
+
+
+def train_tl_pnet(cg, torch, ctx, dev, w_cell, p_max, stages=(25.0, 50.0, 100.0), n_set=1 << 19,
+                  steps=(20000, 8000, 8000), lr=(3e-3, 1e-3, 1e-3), batch=8192):
+    """The same three transfer-learning stages for the paper's own 9-12-9
+    network, whose inputs also carry the macro-particle weights and the
+    cell's P_max (here those of the inverse-Compton cells).  Returns the
+    parameters after each stage."""
+    from paper_2206_02937_gb300 import workloads as wl
+    rng = np.random.default_rng(1)
+    theta = np.zeros(cg.PNET_PARAMS, dtype=np.float32)
+    at = 0
+    for o, i in [(9, 9), (12, 9), (9, 12), (1, 9)]:
+        lim = np.sqrt(6.0 / (o + i))
+        theta[at:at + o * i] = rng.uniform(-lim, lim, o * i)
+        at += o * i + o
+    g_max, e_min, e_max = IC_RANGE
+    cg.compton_pnet_set_params(ctx, theta, np.array(IC_FS, dtype=np.float32), g_max, e_min, e_max)
+    us, ks, thetas, info = [], [], [], []
+    gen = torch.Generator(device=dev).manual_seed(1)
+    for s_i, p0 in enumerate(stages):
+        u, k = wl.waterbag_pairs(n_set, p0, seed=25 + s_i)
+        us.append(torch.from_numpy(u).to(dev))
+        ks.append(torch.from_numpy(k).to(dev))
+        ut, kt = torch.cat(us, dim=1), torch.cat(ks, dim=1)
+        n = ut.shape[1]
+        r = torch.zeros(n, device=dev)
+        cg.compton_kn_ratio(ctx, ut, kt, r)
+        if s_i == 0:
+            rm = float(r.median())
+            theta[-1] = np.log(rm / (1.0 - rm))
+            cg.compton_pnet_set_params(ctx, theta, np.array(IC_FS, dtype=np.float32), g_max, e_min, e_max)
+        first = last = None
+        t0 = time.time()
+        for it in range(steps[s_i]):
+            idx = torch.randint(0, n, (batch,), device=dev, generator=gen)
+            lr_it = lr[s_i] * 0.5 * (1.0 + np.cos(np.pi * it / steps[s_i]))
+            loss = cg.compton_pnet_train_step(ctx, ut[:, idx].contiguous(), kt[:, idx].contiguous(),
+                                              r[idx].contiguous(), None, w_cell, w_cell, p_max, lr_it,
+                                              want_loss=(it == 0 or it == steps[s_i] - 1))
+            if loss is not None:
+                first = loss if first is None else first
+                last = loss
+        torch.cuda.synchronize()
+        thetas.append(cg.compton_pnet_get_params(ctx)[0])
+        info.append({"p0": p0, "samples": n, "steps": steps[s_i], "lr": lr[s_i], "loss_first": first,
+                     "loss_last": last, "stage_s": time.time() - t0})
+    return thetas, info
 
 
 def ic_simulation(cg, torch, ctx, w, steps, mode, dev, step0=0):
@@ -917,6 +1049,10 @@ def run_ic(args, rank: int, world: int, local_rank: int):
     t_train = time.time()
     blobs, tl_info = train_tl(cg, torch, ctx, dev)
     t_train = time.time() - t_train
+    ic_p_max = 2.0 * 1.0 * probe.dt  # density 1 in every cell
+    t_pnet = time.time()
+    pnet_thetas, pnet_info = train_tl_pnet(cg, torch, ctx, dev, probe.w_over_v, ic_p_max)
+    t_pnet = time.time() - t_pnet
 
     # head-on sweep (the paper's probability comparison): p_e along +x,
     # photons along -x with log-spaced energy
@@ -932,7 +1068,11 @@ def run_ic(args, rank: int, world: int, local_rank: int):
         cg.compton_kn_ratio(ctx, ut, kt, ra)
         cg.compton_mlp_infer(ctx, ut, kt, cg.MODE_MLP_BF16, rn)
         rel = ((rn.double() - ra.double()).abs() / ra.double()).cpu().numpy()
+        rp = torch.zeros(eps.size, device=dev)
+        cg.compton_pnet_infer(ctx, ut, kt, probe.w_over_v, probe.w_over_v, ic_p_max, rp)
+        rel_p = ((rp.double() - ra.double()).abs() / ra.double()).cpu().numpy()
         sweep[f"p_e={p_e:g}"] = {"max_rel_r": float(rel.max()), "median_rel_r": float(np.median(rel)),
+                                 "pnet_max_rel_r": float(rel_p.max()), "pnet_median_rel_r": float(np.median(rel_p)),
                                  "eps_range": [1e-3, 100.0]}
 
     results = {}
@@ -964,6 +1104,12 @@ def run_ic(args, rank: int, world: int, local_rank: int):
             entry[tag] = {"scattered_photons": n_nn, "peak_eps": peak_nn,
                           "spectrum_L1_vs_plain": float((h_nn - h_pl).abs().sum()),
                           "fallbacks": st_nn["mlp_fallbacks"]}
+        # the paper's network after the last stage (FP32, CUDA cores)
+        k_pn, st_pn = ic_simulation(cg, torch, ctx, w, n_steps, cg.MODE_PNET, dev)
+        h_pn, n_pn, peak_pn = ic_spectrum(torch, k_pn, 2.5)
+        entry["pnet_tl_stage_3"] = {"scattered_photons": n_pn, "peak_eps": peak_pn,
+                                    "spectrum_L1_vs_plain": float((h_pn - h_pl).abs().sum()),
+                                    "fallbacks": st_pn["mlp_fallbacks"]}
         results[f"p_e={p_e:g}"] = entry
     cg.compton_destroy(ctx)
     if rank == 0:
@@ -975,8 +1121,10 @@ def run_ic(args, rank: int, world: int, local_rank: int):
                                    "gas at eps = 2.5, 512 cells x 128 per species, density 1, dt 0.05; value = "
                                    "pairs/s of the plain runs including host launch overheads"},
             "inverse_compton": results, "head_on_sweep": sweep, "transfer_learning": tl_info, "train_s": t_train,
+            "transfer_learning_pnet": pnet_info, "train_pnet_s": t_pnet,
             "note": "spectra: normalised 70-bin log10(eps) histograms of the photons that scattered at least "
-                    "once, after the run; tl_stage_k = the surrogate after k transfer-learning stages (BF16)",
+                    "once, after the run; tl_stage_k = the surrogate after k transfer-learning stages (BF16); "
+                    "pnet_tl_stage_3 = the paper's 9-12-9 network after the three stages (FP32)",
         }
         print(json.dumps(line), flush=True)
 
