@@ -610,7 +610,7 @@ def run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step0, peaks):
     # the paper's own 9-12-9 ReLU network (FP32, CUDA cores)
     cnt = np.maximum(np.bincount(w.e["cell"], minlength=w.n_cells), np.bincount(w.g["cell"], minlength=w.n_cells))
     p_max_cells = 2.0 * w.dt * w.w_over_v * cnt[cnt > 0].astype(np.float64)
-    train_pn = train_pnet(cg, torch, ctx, dev, w.w_over_v, p_max_cells, steps=args.train_steps)
+    train_pn = train_pnet(cg, torch, ctx, dev, w.w_over_v, p_max_cells, steps=4 * args.train_steps)
     P_pn = torch.empty(n, device=dev)
     h_pn, n_pn = scattered_spectrum(cg.MODE_PNET, P_pn)
     pnv = P_pn[:np_pairs].double()
@@ -1075,6 +1075,22 @@ def run_ic(args, rank: int, world: int, local_rank: int):
                                  "pnet_max_rel_r": float(rel_p.max()), "pnet_median_rel_r": float(np.median(rel_p)),
                                  "eps_range": [1e-3, 100.0]}
 
+    # held-out pairs of the last stage's distribution: r error of each network
+    uv, kv = wl.waterbag_pairs(1 << 18, 100.0, seed=99)
+    uvt, kvt = torch.from_numpy(uv).to(dev), torch.from_numpy(kv).to(dev)
+    rv = torch.zeros(uv.shape[1], device=dev)
+    cg.compton_kn_ratio(ctx, uvt, kvt, rv)
+    held_out = {}
+    for name, fn in (("mlp_fp32", lambda o: cg.compton_mlp_infer(ctx, uvt, kvt, cg.MODE_MLP_FP32, o)),
+                     ("mlp_bf16", lambda o: cg.compton_mlp_infer(ctx, uvt, kvt, cg.MODE_MLP_BF16, o)),
+                     ("pnet", lambda o: cg.compton_pnet_infer(ctx, uvt, kvt, probe.w_over_v, probe.w_over_v,
+                                                              ic_p_max, o))):
+        o = torch.zeros_like(rv)
+        fn(o)
+        rel = ((o.double() - rv.double()).abs() / rv.double()).cpu().numpy()
+        held_out[name] = {"mean_rel_r": float(rel.mean()), "median_rel_r": float(np.median(rel)),
+                          "mean_ratio": float((o.double() / rv.double()).mean())}
+
     results = {}
     pairs_total, ms_total = 0, 0.0
     for p_e in (25.0, 50.0, 100.0):
@@ -1121,7 +1137,7 @@ def run_ic(args, rank: int, world: int, local_rank: int):
                                    "gas at eps = 2.5, 512 cells x 128 per species, density 1, dt 0.05; value = "
                                    "pairs/s of the plain runs including host launch overheads"},
             "inverse_compton": results, "head_on_sweep": sweep, "transfer_learning": tl_info, "train_s": t_train,
-            "transfer_learning_pnet": pnet_info, "train_pnet_s": t_pnet,
+            "transfer_learning_pnet": pnet_info, "train_pnet_s": t_pnet, "held_out_waterbag_p0_100": held_out,
             "note": "spectra: normalised 70-bin log10(eps) histograms of the photons that scattered at least "
                     "once, after the run; tl_stage_k = the surrogate after k transfer-learning stages (BF16); "
                     "pnet_tl_stage_3 = the paper's 9-12-9 network after the three stages (FP32)",

@@ -88,7 +88,11 @@ typedef struct compton_config {
 
 /* One species in structure-of-arrays form (all device pointers, length n).
  * For photons u* hold the momentum k.  id is a per-particle identifier,
- * unique within the species; it orders particles whose random keys tie. */
+ * unique within the species; it orders particles whose random keys tie.
+ * w_dev, optional, holds each macro-particle's weight over the cell volume
+ * (the density it adds to its cell; > 0 and finite); NULL gives every
+ * particle the context's w_over_v.  With weights the binning carries them
+ * along and the scatter step pairs unequal weights (compton_scatter_step). */
 typedef struct compton_species {
     float* ux_dev;
     float* uy_dev;
@@ -96,6 +100,7 @@ typedef struct compton_species {
     int32_t* cell_dev;  /* collision cell in [0, n_cells) */
     uint32_t* id_dev;
     int64_t n;
+    float* w_dev;       /* per-particle weight over cell volume, or NULL */
 } compton_species;
 
 /* Pair list of one step, produced by compton_bin_pairs.  Its pointers refer to
@@ -160,7 +165,10 @@ compton_status compton_get_stats(struct compton_ctx* ctx, compton_stats* out_hos
  * (cell, id) values, never on the input order or on thread timing.
  *
  * e_in/g_in are read; e_out/g_out (same n, distinct memory) receive the
- * sorted copies of all five arrays.  Fills *pairs_out (see compton_pairs).
+ * sorted copies of all five arrays, and of the weights where the input
+ * species has them (the output species then needs w_dev too).  Fills
+ * *pairs_out (see compton_pairs); a pair list binned with weights on either
+ * species is for compton_scatter_step on weighted species only.
  * EINVAL for null pointers, aliasing in/out, n > max_particles; a cell index
  * outside [0, n_cells) is reported by compton_check (ERANGE) and that
  * particle is left out of every cell. */
@@ -187,7 +195,17 @@ compton_status compton_bin_pairs(struct compton_ctx* ctx, const compton_species*
  * Only pairs with u0 < 1 - exp(-2 n_c dt), the bound of every pair's P, are
  * evaluated (the decisions are those of evaluating all pairs); with
  * prob_out_dev given, every pair is evaluated.
- * mode selects the analytic probability or the surrogate network.
+ * Unequal weights (either species with w_dev): the pair's density is
+ * n_p = max(N_e,c, N_g,c) * max(w_e, w_g) (P_max = 2 sigma_T c dt max w of
+ * Sec. 3.2 per pair), so the expected number of real events in the cell is
+ * n_e n_g sigma v dt V as with equal weights; a collision then updates the
+ * lighter partner always and the heavier one only if
+ * (r2 >> 8) 2^-24 < w_light / w_heavy, r2 word 2 of the angle block (weight
+ * rejection: energy and momentum are conserved on average).  Equal weights
+ * reduce to the unweighted step.  The species must be binned with their
+ * weights (EINVAL otherwise).
+ * mode selects the analytic probability or the surrogate network (the
+ * paper's network takes w_e, w_g and P_max = 2 n_p dt among its inputs).
  * prob_out_dev (nullable, float[max_pairs]) receives P per pair;
  * flag_out_dev (nullable, uint8[max_pairs]) receives the decision.
  * Adds to the context stats.  ENOMODEL if a network mode has no weights. */
@@ -218,7 +236,8 @@ compton_status compton_scatter_pairs(struct compton_ctx* ctx, float* ux_dev, flo
  * (2 sigma_T); the collision uses word 3 for the angle and word 0 of block
  * (c, step lo, 7 | j << 8, step hi) for the azimuth, and later candidates of
  * the cell see the updated momenta.  The stats count candidates as pairs
- * tested.  Analytic probability only. */
+ * tested.  Analytic probability and equal weights only (EINVAL for species
+ * with w_dev or a pair list binned with weights). */
 compton_status compton_scatter_step_ntc(struct compton_ctx* ctx, compton_species* e, compton_species* g,
                                         const compton_pairs* pairs, uint64_t step, compton_stream_t stream);
 

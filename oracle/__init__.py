@@ -92,6 +92,11 @@ def lib():
                                   i64, P, P, P, P, P,
                                   P, P, P, P, P, P, P, P, P]
         L.or_ntc_step.restype = i64
+        L.or_step_weighted.argtypes = [i64, d, d, u64, u64,
+                                       i64, P, P, P, P, P, P,
+                                       i64, P, P, P, P, P, P,
+                                       P, P, P, P, P, P, P, P, P, P, P, P]
+        L.or_step_weighted.restype = i64
         _ = (i32,)
         _lib = L
     return _lib
@@ -253,6 +258,42 @@ def step(n_cells, w_over_v, dt, seed, step_idx, e, g):
     if npairs < 0:
         raise ValueError("oracle: bad input")
     for key in ("P", "flag", "x"):
+        out[key] = out[key][:npairs]
+    out["n_pairs"] = int(npairs)
+    return out
+
+
+def step_weighted(n_cells, w_over_v, dt, seed, step_idx, e, g):
+    """One step with unequal macro-particle weights (or_step_weighted): the
+    species dicts of step() with an optional "w" (float32 weight over the
+    cell volume; absent = w_over_v).  Returns step()'s dict plus the sorted
+    weights e_w, g_w and upd (bit 0: electron updated, bit 1: photon)."""
+    def arr(s, key, dt_):
+        return np.ascontiguousarray(s[key], dtype=dt_)
+
+    ex, ey, ez = (arr(e, c, np.float32) for c in ("ux", "uy", "uz"))
+    gx, gy, gz = (arr(g, c, np.float32) for c in ("ux", "uy", "uz"))
+    ec, gc = arr(e, "cell", np.int32), arr(g, "cell", np.int32)
+    ei, gi = arr(e, "id", np.uint32), arr(g, "id", np.uint32)
+    ew = arr(e, "w", np.float32) if e.get("w") is not None else None
+    gw = arr(g, "w", np.float32) if g.get("w") is not None else None
+    ne, ng = ex.shape[0], gx.shape[0]
+    mp = max(1, min(ne, ng))
+    out = dict(
+        e_out=np.zeros((3, ne)), g_out=np.zeros((3, ng)), e_w=np.zeros(ne), g_w=np.zeros(ng),
+        e_perm=np.zeros(ne, dtype=np.int64), g_perm=np.zeros(ng, dtype=np.int64),
+        e_off=np.zeros(n_cells + 1, dtype=np.int64), g_off=np.zeros(n_cells + 1, dtype=np.int64),
+        pair_off=np.zeros(n_cells + 1, dtype=np.int64),
+        P=np.zeros(mp), flag=np.zeros(mp, dtype=np.int32), upd=np.zeros(mp, dtype=np.int32))
+    npairs = lib().or_step_weighted(int(n_cells), float(w_over_v), float(dt), int(seed), int(step_idx),
+                                    ne, _p(ex), _p(ey), _p(ez), _p(ec), _p(ei), None if ew is None else _p(ew),
+                                    ng, _p(gx), _p(gy), _p(gz), _p(gc), _p(gi), None if gw is None else _p(gw),
+                                    _p(out["e_out"]), _p(out["g_out"]), _p(out["e_w"]), _p(out["g_w"]),
+                                    _p(out["e_perm"]), _p(out["g_perm"]), _p(out["e_off"]), _p(out["g_off"]),
+                                    _p(out["pair_off"]), _p(out["P"]), _p(out["flag"]), _p(out["upd"]))
+    if npairs < 0:
+        raise ValueError("oracle: bad input")
+    for key in ("P", "flag", "upd"):
         out[key] = out[key][:npairs]
     out["n_pairs"] = int(npairs)
     return out

@@ -469,6 +469,80 @@ int64_t or_step(int64_t n_cells, double w_over_v, double dt, uint64_t seed, uint
     return np;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Unequal macro-particle weights (Sec. 3.2 gives P_max = 2 sigma_T c dt     */
+/* max[w_e, w_g]: the probability bound of a pair takes the heavier of the   */
+/* two weights).  Reading built here:                                       */
+/*   - w is a macro-particle's weight over the cell volume (the density it  */
+/*     adds); binning and pairing are those of or_step;                     */
+/*   - pair density n_p = max(N_e, N_g) max(w_e, w_g), so that the expected  */
+/*     number of real events of a cell, sum over pairs of P min(w_e, w_g) V, */
+/*     is n_e n_g sigma v dt V in the small-probability limit, as with      */
+/*     equal weights;                                                       */
+/*   - a colliding pair is resolved as in or_collide; the lighter partner   */
+/*     takes its new momentum, the heavier one only if u w_heavy < w_light, */
+/*     u = (r2 >> 8) 2^-24 with r2 word 2 of draw(seed, step, 4, p) (weight  */
+/*     rejection; equal weights update both).                               */
+/* ew or gw NULL: every particle of that species has weight w_over_v.       */
+/* Outputs as or_step, plus the sorted weights (e_w_out, g_w_out; FP64) and */
+/* upd[p] = (electron updated) | (photon updated) << 1 for every pair.      */
+/* ------------------------------------------------------------------------ */
+int64_t or_step_weighted(int64_t n_cells, double w_over_v, double dt, uint64_t seed, uint64_t step,
+                         int64_t n_e, const float* eux, const float* euy, const float* euz,
+                         const int32_t* ecell, const uint32_t* eid, const float* ew,
+                         int64_t n_g, const float* gkx, const float* gky, const float* gkz,
+                         const int32_t* gcell, const uint32_t* gid, const float* gw,
+                         double* e_out, double* g_out, double* e_w_out, double* g_w_out,
+                         int64_t* e_perm, int64_t* g_perm, int64_t* e_off, int64_t* g_off, int64_t* pair_off,
+                         double* P, int32_t* flag, int32_t* upd)
+{
+    if (or_sort_species(n_e, ecell, eid, n_cells, seed, step, 1u, e_perm, e_off)) return -1;
+    if (or_sort_species(n_g, gcell, gid, n_cells, seed, step, 2u, g_perm, g_off)) return -1;
+    for (int64_t j = 0; j < n_e; ++j) {
+        int64_t i = e_perm[j];
+        e_out[j] = eux[i]; e_out[n_e + j] = euy[i]; e_out[2 * n_e + j] = euz[i];
+        e_w_out[j] = ew ? (double)ew[i] : w_over_v;
+    }
+    for (int64_t j = 0; j < n_g; ++j) {
+        int64_t i = g_perm[j];
+        g_out[j] = gkx[i]; g_out[n_g + j] = gky[i]; g_out[2 * n_g + j] = gkz[i];
+        g_w_out[j] = gw ? (double)gw[i] : w_over_v;
+    }
+    int64_t np = 0;
+    pair_off[0] = 0;
+    for (int64_t c = 0; c < n_cells; ++c) {
+        int64_t ne = e_off[c + 1] - e_off[c];
+        int64_t ng = g_off[c + 1] - g_off[c];
+        int64_t m = ne < ng ? ne : ng;
+        double n_max = (double)(ne > ng ? ne : ng);
+        for (int64_t q = 0; q < m; ++q) {
+            int64_t je = e_off[c] + q, jg = g_off[c] + q;
+            double we = e_w_out[je], wg = g_w_out[jg];
+            double n_pair = n_max * (we > wg ? we : wg);
+            double u[3] = {e_out[je], e_out[n_e + je], e_out[2 * n_e + je]};
+            double k[3] = {g_out[jg], g_out[n_g + jg], g_out[2 * n_g + jg]};
+            double uo[3], ko[3], xx;
+            int f;
+            or_scatter_event(u, k, n_pair, dt, seed, step, (uint32_t)np, uo, ko, &P[np], &f, &xx);
+            flag[np] = f;
+            int up_e = 0, up_g = 0;
+            if (f) {
+                uint32_t r[4];
+                draw(seed, step, 4u, (uint32_t)np, r);
+                double uw = unif_closed0(r[2]);
+                up_e = (we <= wg) || (uw * we < wg);
+                up_g = (wg <= we) || (uw * wg < we);
+            }
+            upd[np] = up_e | (up_g << 1);
+            if (up_e) { e_out[je] = uo[0]; e_out[n_e + je] = uo[1]; e_out[2 * n_e + je] = uo[2]; }
+            if (up_g) { g_out[jg] = ko[0]; g_out[n_g + jg] = ko[1]; g_out[2 * n_g + jg] = ko[2]; }
+            ++np;
+        }
+        pair_off[c + 1] = np;
+    }
+    return np;
+}
+
 /* Pre-paired events (the serving form): pair i uses counter id i under the
  * given seed and step, with its own density n[i].  Outputs 3 x n FP64
  * momenta (row-major by component), P and flag per pair. */

@@ -35,7 +35,7 @@ class compton_config(ctypes.Structure):
 
 class compton_species(ctypes.Structure):
     _fields_ = [("ux_dev", c_p), ("uy_dev", c_p), ("uz_dev", c_p), ("cell_dev", c_p), ("id_dev", c_p),
-                ("n", c_i64)]
+                ("n", c_i64), ("w_dev", c_p)]
 
 
 class compton_pairs(ctypes.Structure):
@@ -117,12 +117,15 @@ def _check(st: int, what: str, ctx=None):
 
 @dataclass
 class Species:
-    """One species as five torch CUDA tensors of equal length."""
+    """One species as five torch CUDA tensors of equal length, plus optional
+    per-particle weights over the cell volume (float32; None = the context's
+    w_over_v for every particle)."""
     ux: "object"
     uy: "object"
     uz: "object"
     cell: "object"
     id: "object"
+    w: "object" = None
 
     @property
     def n(self) -> int:
@@ -130,13 +133,15 @@ class Species:
 
     def c(self) -> compton_species:
         return compton_species(self.ux.data_ptr(), self.uy.data_ptr(), self.uz.data_ptr(),
-                               self.cell.data_ptr(), self.id.data_ptr(), self.n)
+                               self.cell.data_ptr(), self.id.data_ptr(), self.n,
+                               None if self.w is None else self.w.data_ptr())
 
     @staticmethod
     def empty_like(s: "Species") -> "Species":
         import torch
         return Species(torch.empty_like(s.ux), torch.empty_like(s.uy), torch.empty_like(s.uz),
-                       torch.empty_like(s.cell), torch.empty_like(s.id))
+                       torch.empty_like(s.cell), torch.empty_like(s.id),
+                       None if s.w is None else torch.empty_like(s.w))
 
 
 def compton_init(n_cells: int, max_particles: int, w_over_v: float, dt: float, seed: int, device: int = 0,

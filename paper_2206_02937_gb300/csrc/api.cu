@@ -41,11 +41,11 @@ bool overlaps(const void* a, const void* b, int64_t n, size_t elem)
 
 bool species_alias(const compton_species* a, const compton_species* b, int64_t n)
 {
-    const void* pa[5] = {a->ux_dev, a->uy_dev, a->uz_dev, a->cell_dev, a->id_dev};
-    const void* pb[5] = {b->ux_dev, b->uy_dev, b->uz_dev, b->cell_dev, b->id_dev};
-    for (int i = 0; i < 5; ++i)
-        for (int j = 0; j < 5; ++j)
-            if (overlaps(pa[i], pb[j], n, 4)) return true;
+    const void* pa[6] = {a->ux_dev, a->uy_dev, a->uz_dev, a->cell_dev, a->id_dev, a->w_dev};
+    const void* pb[6] = {b->ux_dev, b->uy_dev, b->uz_dev, b->cell_dev, b->id_dev, b->w_dev};
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j)
+            if (pa[i] && pb[j] && overlaps(pa[i], pb[j], n, 4)) return true;
     return false;
 }
 
@@ -324,9 +324,13 @@ compton_status compton_bin_pairs(compton_ctx* ctx, const compton_species* e_in, 
     e_out->n = e_in->n;
     g_out->n = g_in->n;
     if (!species_ok(e_out) || !species_ok(g_out)) return COMPTON_EINVAL;
+    // weights travel with the particles: an output for every weighted input
+    if ((e_in->w_dev && e_in->n > 0 && !e_out->w_dev) || (g_in->w_dev && g_in->n > 0 && !g_out->w_dev))
+        return COMPTON_EINVAL;
     if (species_alias(e_in, e_out, e_in->n) || species_alias(g_in, g_out, g_in->n)) return COMPTON_EINVAL;
     compton_status st = compton::launch_bin_pairs(ctx, e_in, g_in, e_out, g_out, step, stream);
     if (st != COMPTON_OK) return st;
+    ctx->bin_weighted = e_in->w_dev || g_in->w_dev;
     pairs_out->off_e_dev = ctx->off[0];
     pairs_out->off_g_dev = ctx->off[1];
     pairs_out->cell_info_dev = ctx->cinfo;
@@ -345,6 +349,7 @@ compton_status compton_scatter_step(compton_ctx* ctx, compton_species* e, compto
     if (pairs->cell_info_dev != ctx->cinfo || pairs->n_cells != ctx->cfg.n_cells) return COMPTON_EINVAL;
     if (pairs->max_pairs > (e->n < g->n ? e->n : g->n)) return COMPTON_EINVAL;
     if ((int)mode < 0 || (int)mode > 4) return COMPTON_EINVAL;
+    if ((e->w_dev || g->w_dev) != ctx->bin_weighted) return COMPTON_EINVAL;
     if (mode == COMPTON_MODE_PNET ? !ctx->pnet_loaded : (mode != COMPTON_MODE_PLAIN && !ctx->mlp_loaded))
         return COMPTON_ENOMODEL;
     return compton::launch_scatter_binned(ctx, e, g, pairs, mode, step, prob_out, flag_out, stream);
@@ -355,6 +360,7 @@ compton_status compton_scatter_step_ntc(compton_ctx* ctx, compton_species* e, co
 {
     if (!ctx || !pairs || !species_ok(e) || !species_ok(g)) return COMPTON_EINVAL;
     if (pairs->cell_info_dev != ctx->cinfo || pairs->n_cells != ctx->cfg.n_cells) return COMPTON_EINVAL;
+    if (e->w_dev || g->w_dev || ctx->bin_weighted) return COMPTON_EINVAL;
     return compton::launch_scatter_ntc(ctx, e, g, pairs, step, stream);
 }
 

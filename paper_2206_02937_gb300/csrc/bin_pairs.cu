@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(256) k_scan_final(ScanFinalArgs a)
 
 // ---------------------------------------------------------------------------
 // Keyed placement of input not yet in cell order: each particle's record
-// (Philox key, id, momentum) goes to off[c] + cursor.  A record fills one
+// (Philox key, id, momentum, weight if any) goes to off[c] + cursor.  A record fills one
 // aligned 32-byte sector, written as two 16-byte stores, so the scattered
 // writes never leave partly written sectors behind.  Input already in cell
 // order (k_count found no descent and no bad index) skips this kernel: the
@@ -292,6 +292,7 @@ struct PlaceArgs {
     const int32_t* cell[2];
     const uint32_t* id[2];
     const float* u[2][3];
+    const float* w[2];  // per-particle weights, or nullptr
     int64_t n[2];
     const int32_t* off[2];
     int32_t* cursor[2];
@@ -301,12 +302,16 @@ struct PlaceArgs {
     uint64_t seed, step;
 };
 
-__device__ __forceinline__ void store_rec(SortRec* r, uint32_t key, uint32_t pid, float ux, float uy, float uz)
+__device__ __forceinline__ void store_rec(SortRec* r, uint32_t key, uint32_t pid, float ux, float uy, float uz,
+                                          float w)
 {
     uint4* q = reinterpret_cast<uint4*>(r);
     q[0] = make_uint4(key, pid, __float_as_uint(ux), __float_as_uint(uy));
-    q[1] = make_uint4(__float_as_uint(uz), 0u, 0u, 0u);
+    q[1] = make_uint4(__float_as_uint(uz), __float_as_uint(w), 0u, 0u);
 }
+
+// The weight a record carries (its first padding word).
+__device__ __forceinline__ float rec_weight(const SortRec* r) { return __uint_as_float(r->pad[0]); }
 
 __global__ void k_place(PlaceArgs a)
 {
@@ -318,6 +323,7 @@ __global__ void k_place(PlaceArgs a)
     const float* __restrict__ u0 = a.u[s][0];
     const float* __restrict__ u1 = a.u[s][1];
     const float* __restrict__ u2 = a.u[s][2];
+    const float* __restrict__ wt = a.w[s];
     const int32_t* __restrict__ off = a.off[s];
     int32_t* __restrict__ cursor = a.cursor[s];
     SortRec* __restrict__ rec = a.rec[s];
@@ -343,7 +349,7 @@ __global__ void k_place(PlaceArgs a)
         base = __shfl_sync(peers, base, leader);
         if (c >= 0) {
             const int64_t slot = (int64_t)off[c] + base + __popc(peers & ((1u << lane) - 1u));
-            store_rec(rec + slot, key, pid, u0[i], u1[i], u2[i]);
+            store_rec(rec + slot, key, pid, u0[i], u1[i], u2[i], wt ? wt[i] : 0.0f);
         }
     }
 }
@@ -365,6 +371,8 @@ __global__ void k_place(PlaceArgs a)
 struct SortGatherArgs {
     const float* in_u[2][3];
     const uint32_t* in_id[2];
+    const float* in_w[2];  // per-particle weights, or nullptr
+    float* out_w[2];
     float* out_u[2][3];
     int32_t* out_cell[2];
     uint32_t* out_id[2];
@@ -382,6 +390,7 @@ struct SortSrc {
     const SortRec* rec;  // nullptr: read the input arrays in place
     const uint32_t* id;
     const float* u[3];
+    const float* w;      // weights (in place), or nullptr
     uint64_t seed, step;
     uint32_t stream;
 };
@@ -572,6 +581,9 @@ __device__ __forceinline__ void sort_tile_block(const SortGatherArgs& g, int s, 
         g.out_u[s][1][go] = m.us[1][i];
         g.out_u[s][2][go] = m.us[2][i];
         g.out_id[s][go] = (uint32_t)m.key64[i];
+        // the weight is not staged: read once more where the tile came from
+        // (a sector this block has just read)
+        if (g.out_w[s]) g.out_w[s][go] = t.rec ? rec_weight(t.rec + o0 + i) : t.w[o0 + i];
     }
 }
 
@@ -585,7 +597,7 @@ __device__ void sort_giant_cell(const SortGatherArgs& g, int s, const SortSrc& t
         for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
             const uint32_t pid = t.id[o + i];
             store_rec(rec + o + i, draw(t.seed, t.step, t.stream, pid).r0, pid, t.u[0][o + i], t.u[1][o + i],
-                      t.u[2][o + i]);
+                      t.u[2][o + i], t.w ? t.w[o + i] : 0.0f);
         }
         __syncthreads();
     }
@@ -602,6 +614,7 @@ __device__ void sort_giant_cell(const SortGatherArgs& g, int s, const SortSrc& t
         g.out_u[s][2][p] = ri.uz;
         g.out_cell[s][p] = c;
         g.out_id[s][p] = ri.id;
+        if (g.out_w[s]) g.out_w[s][p] = rec_weight(&ri);
     }
     __syncthreads();
 }
@@ -637,6 +650,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_gather(SortGatherArgs 
     t.rec = placed ? g.rec[s] : nullptr;
     t.id = g.in_id[s];
     for (int k = 0; k < 3; ++k) t.u[k] = g.in_u[s][k];
+    t.w = g.in_w[s];
     t.seed = g.seed;
     t.step = g.step;
     t.stream = s == 0 ? kStreamPairE : kStreamPairG;
@@ -719,7 +733,10 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
     sf.nb_e = nb_e;
     sf.nb_g = nb_g;
     sf.n_pairs = ctx->n_pairs;
-    sf.w_over_v = ctx->cfg.w_over_v;
+    // with per-particle weights a cell's density is its larger count; each
+    // pair scales it by its own heavier weight
+    const bool weighted = e_in->w_dev || g_in->w_dev;
+    sf.w_over_v = weighted ? 1.0 : ctx->cfg.w_over_v;
     k_scan_final<<<(unsigned)n_tiles, 256, 0, stream>>>(sf);
     scan_scope.end();
     COMPTON_LAUNCH_CHECK(ctx, "k_scan_final");
@@ -734,6 +751,7 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
         pa.u[s][0] = ins[s]->ux_dev;
         pa.u[s][1] = ins[s]->uy_dev;
         pa.u[s][2] = ins[s]->uz_dev;
+        pa.w[s] = ins[s]->w_dev;
         pa.n[s] = ins[s]->n;
         pa.off[s] = ctx->off[s];
         pa.cursor[s] = ctx->count[s];
@@ -756,6 +774,8 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
             sg.in_u[s][1] = ins[s]->uy_dev;
             sg.in_u[s][2] = ins[s]->uz_dev;
             sg.in_id[s] = ins[s]->id_dev;
+            sg.in_w[s] = ins[s]->w_dev;
+            sg.out_w[s] = ins[s]->w_dev ? outs[s]->w_dev : nullptr;
             sg.out_u[s][0] = outs[s]->ux_dev;
             sg.out_u[s][1] = outs[s]->uy_dev;
             sg.out_u[s][2] = outs[s]->uz_dev;

@@ -23,7 +23,8 @@ struct __align__(16) CellInfo {
     int32_t pair_off;  // first pair of the cell
     int32_t e_start;   // first sorted electron
     int32_t g_start;   // first sorted photon
-    float dens;        // pair density n_c = max(N_e, N_g) * w_over_v
+    float dens;        // pair density n_c = max(N_e, N_g) * w_over_v; with per-particle
+                       // weights max(N_e, N_g) alone (the pair takes max(w_e, w_g))
 };
 
 // A particle placed in its cell's segment by the binning: Philox key, id,
@@ -178,6 +179,7 @@ struct compton_ctx {
     float* r_buf = nullptr;         // [max_particles] network output per pair (surrogate modes)
     compton::ServeEngine* serve = nullptr;  // continuous-batching engine (compton_serve_start)
     compton::KernelTiming* timing = nullptr;  // per-kernel event pairs (compton_kernel_timing)
+    bool bin_weighted = false;                // the last binning carried per-particle weights
     compton::PnetDev pnet{};                  // the paper's 9-12-9 network
     bool pnet_loaded = false;
 };
@@ -240,7 +242,8 @@ compton_status launch_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, floa
 compton_status launch_pnet_infer(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                  const float* kx, const float* ky, const float* kz, int64_t n, float w_e, float w_g,
                                  float p_max, float* r_out, cudaStream_t stream);
-compton_status launch_pnet_decide(compton_ctx* ctx, int64_t rows, const MlpDecide& dec, cudaStream_t stream);
+compton_status launch_pnet_decide(compton_ctx* ctx, int64_t rows, const MlpDecide& dec, const float* w_e,
+                                  const float* w_g, cudaStream_t stream);
 compton_status launch_pnet_train_step(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                       const float* kx, const float* ky, const float* kz, const float* y,
                                       const float* w, int64_t n, float w_e, float w_g, float p_max, float lr,

@@ -13,8 +13,9 @@
 // the CUDA cores in FP32, one sample per thread, with the parameters staged
 // in shared memory:
 //   k_pnet_infer   r per explicit pair, or -- in the surrogate step -- per
-//                  candidate of the candidate list with the decision made in
-//                  the same thread (analytic probability outside the
+//                  candidate of the candidate list (weights w/V of the pair's
+//                  particles, P_max = 2 n_p dt of the pair) with the decision
+//                  made in the same thread (analytic probability outside the
 //                  training range) and accepted pairs appended to the list;
 //   k_pnet_train   forward and backward per sample; each parameter's
 //                  gradient is summed over the warp by shuffles, then over
@@ -43,6 +44,8 @@ struct PnetArgs {
     const CandPair* cand;
     const uint32_t* n_cand;
     float dt, gamma64, ln_w;
+    const float* w_e;  // per-particle weights of the sorted species (nullptr: ln_w)
+    const float* w_g;
     float* prob_out;
     uint8_t* flag_out;
     AcceptedPair* accepted;
@@ -143,7 +146,12 @@ __global__ void __launch_bounds__(kPnetThreads, 3) k_pnet_infer(PnetArgs a)
         }
         float f[9], h1[9], h2[12], h3[9];
         const float lpm = kCand ? logf(fmaxf(2.0f * c.dens * a.dt, 1e-30f)) : a.ln_pmax;
-        pnet_features(a.p, q, kCand ? a.ln_w : a.ln_we, kCand ? a.ln_w : a.ln_wg, lpm, f);
+        float lwe = kCand ? a.ln_w : a.ln_we, lwg = kCand ? a.ln_w : a.ln_wg;
+        if (kCand && live) {
+            if (a.w_e) lwe = logf(a.w_e[c.ie]);
+            if (a.w_g) lwg = logf(a.w_g[c.ig]);
+        }
+        pnet_features(a.p, q, lwe, lwg, lpm, f);
         const float r = pnet_forward(th, f, h1, h2, h3);
         if (!kCand) {
             if (live) a.r_out[row] = r;
@@ -334,7 +342,8 @@ compton_status launch_pnet_infer(compton_ctx* ctx, const float* ux, const float*
     return COMPTON_OK;
 }
 
-compton_status launch_pnet_decide(compton_ctx* ctx, int64_t rows, const MlpDecide& dec, cudaStream_t stream)
+compton_status launch_pnet_decide(compton_ctx* ctx, int64_t rows, const MlpDecide& dec, const float* w_e,
+                                  const float* w_g, cudaStream_t stream)
 {
     PnetArgs a{};
     a.p = ctx->pnet;
@@ -343,6 +352,8 @@ compton_status launch_pnet_decide(compton_ctx* ctx, int64_t rows, const MlpDecid
     a.dt = dec.dt;
     a.gamma64 = dec.gamma64;
     a.ln_w = logf((float)ctx->cfg.w_over_v);
+    a.w_e = w_e;
+    a.w_g = w_g;
     a.prob_out = dec.prob_out;
     a.flag_out = dec.flag_out;
     a.accepted = ctx->accepted;

@@ -55,7 +55,24 @@ struct ScatterArgs {
     CandPair* cand;
     uint32_t* n_cand;
     MlpDev mlp;  // the network's training range (surrogate modes)
+    // unequal weights: per-particle weights (nullptr: w_const for all) of the
+    // sorted species; cinfo.dens then holds max(N_e, N_g)
+    const float* w_e;
+    const float* w_g;
+    float w_const;
+    bool weighted;
 };
+
+// A binned pair's density: the cell's, or with unequal weights the cell's
+// larger count times the pair's heavier weight.
+template <bool kWeighted>
+__device__ __forceinline__ float pair_density(const ScatterArgs& a, float cell_dens, int ie, int ig)
+{
+    if (!kWeighted) return cell_dens;
+    const float we = a.w_e ? a.w_e[ie] : a.w_const;
+    const float wg = a.w_g ? a.w_g[ig] : a.w_const;
+    return cell_dens * fmaxf(we, wg);
+}
 
 __device__ __forceinline__ int find_cell(const CellInfo* win, int nwin, int64_t p)
 {
@@ -85,12 +102,27 @@ __device__ __forceinline__ void resolve(const ScatterArgs& a, const AcceptedPair
     const float ge2 = fmaf(ux, ux, fmaf(uy, uy, fmaf(uz, uz, 1.0f))) * fmaf(kx, kx, fmaf(ky, ky, kz * kz));
     if (ge2 > a.collide64_sq) collide_f64(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(rnd.r1));
     else collide_f32(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(rnd.r1));
-    a.u[0][e.ie] = ux;
-    a.u[1][e.ie] = uy;
-    a.u[2][e.ie] = uz;
-    a.k[0][e.ig] = kx;
-    a.k[1][e.ig] = ky;
-    a.k[2][e.ig] = kz;
+    bool upd_e = true, upd_g = true;
+    if (a.weighted) {
+        // weight rejection: the heavier partner takes its new momentum with
+        // probability w_light / w_heavy; u w_heavy < w_light is decided
+        // exactly (both products of 24-bit mantissas fit FP64)
+        const float we = a.w_e ? a.w_e[e.ie] : a.w_const;
+        const float wg = a.w_g ? a.w_g[e.ig] : a.w_const;
+        const double uw = (double)u24_closed0(rnd.r2);
+        if (we > wg) upd_e = uw * (double)we < (double)wg;
+        else if (wg > we) upd_g = uw * (double)wg < (double)we;
+    }
+    if (upd_e) {
+        a.u[0][e.ie] = ux;
+        a.u[1][e.ie] = uy;
+        a.u[2][e.ie] = uz;
+    }
+    if (upd_g) {
+        a.k[0][e.ig] = kx;
+        a.k[1][e.ig] = ky;
+        a.k[2][e.ig] = kz;
+    }
 }
 
 // The analytic probability of one pair and its rest-frame energy x.
@@ -128,7 +160,7 @@ struct Cand {
     uint32_t p;
 };
 
-template <bool kBinned>
+template <bool kBinned, bool kWeighted>
 __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
 {
     __shared__ CellInfo win[kCellWindow];
@@ -173,7 +205,7 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
                 const int j = (int)(p - c.pair_off);
                 ie = c.e_start + j;
                 ig = c.g_start + j;
-                dens = c.dens;
+                dens = pair_density<kWeighted>(a, c.dens, ie, ig);
             } else {
                 ie = (int)p;
                 ig = (int)p;
@@ -252,7 +284,7 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
 // Surrogate modes, first kernel: phase A of k_pair_prob (locate, Bernoulli
 // uniform, bound test); the candidates, with their momenta, go to the
 // context's candidate list for the network.
-template <bool kBinned>
+template <bool kBinned, bool kWeighted>
 __global__ void __launch_bounds__(kProbThreads, 4) k_cand(ScatterArgs a)
 {
     __shared__ CellInfo win[kCellWindow];
@@ -298,7 +330,7 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_cand(ScatterArgs a)
                 const int j = (int)(p - c.pair_off);
                 ie[r] = c.e_start + j;
                 ig[r] = c.g_start + j;
-                dens[r] = c.dens;
+                dens[r] = pair_density<kWeighted>(a, c.dens, ie[r], ig[r]);
             } else {
                 ie[r] = (int)p;
                 ig[r] = (int)p;
@@ -573,32 +605,36 @@ void fill_common(ScatterArgs& a, compton_ctx* ctx, uint64_t seed, uint64_t step,
     a.cand = ctx->cand;
     a.n_cand = ctx->n_cand;
     a.mlp = ctx->mlp;
+    a.w_e = nullptr;
+    a.w_g = nullptr;
+    a.w_const = (float)ctx->cfg.w_over_v;
+    a.weighted = false;
 }
 
 // The step after the pair list is known: probability and trial of every
 // pair (plain: one kernel; surrogate: candidates, network, decisions), then
 // the collisions.  Tiles: pair tiles of this launch; rows: a host bound on
 // the pair count.
-template <bool kBinned>
+template <bool kBinned, bool kWeighted>
 compton_status launch_step(compton_ctx* ctx, ScatterArgs& a, compton_mode mode, unsigned tiles, int64_t rows,
                            cudaStream_t stream)
 {
     COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->n_accepted, 0, sizeof(uint32_t), stream));
     if (mode == COMPTON_MODE_PLAIN) {
         TimedScope ts_(ctx, COMPTON_K_PROB, stream);
-        k_pair_prob<kBinned><<<tiles, kProbThreads, 0, stream>>>(a);
+        k_pair_prob<kBinned, kWeighted><<<tiles, kProbThreads, 0, stream>>>(a);
     } else {
         COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->n_cand, 0, sizeof(uint32_t), stream));
         {
             TimedScope ts_(ctx, COMPTON_K_PROB, stream);
-            k_cand<kBinned><<<tiles, kProbThreads, 0, stream>>>(a);
+            k_cand<kBinned, kWeighted><<<tiles, kProbThreads, 0, stream>>>(a);
         }
         COMPTON_LAUNCH_CHECK(ctx, "k_cand");
         // tensor-core modes and the paper's network decide inside the network
         // kernel; the FP32 network writes r and k_decide decides
         const MlpDecide dec{a.dt, a.gamma64, a.prob_out, a.flag_out};
         if (mode == COMPTON_MODE_PNET) {
-            const compton_status sp = launch_pnet_decide(ctx, rows, dec, stream);
+            const compton_status sp = launch_pnet_decide(ctx, rows, dec, a.w_e, a.w_g, stream);
             if (sp != COMPTON_OK) return sp;
             {
                 TimedScope ts_(ctx, COMPTON_K_COLLIDE, stream);
@@ -650,7 +686,13 @@ compton_status launch_scatter_binned(compton_ctx* ctx, compton_species* e, compt
     a.p_end = 0;
     fill_common(a, ctx, ctx->cfg.seed, step, prob_out, flag_out);
     const unsigned tiles = (unsigned)((pairs->max_pairs + kPairsPerTile - 1) / kPairsPerTile);
-    return launch_step<true>(ctx, a, mode, tiles, pairs->max_pairs, stream);
+    if (ctx->bin_weighted) {
+        a.w_e = e->w_dev;
+        a.w_g = g->w_dev;
+        a.weighted = true;
+        return launch_step<true, true>(ctx, a, mode, tiles, pairs->max_pairs, stream);
+    }
+    return launch_step<true, false>(ctx, a, mode, tiles, pairs->max_pairs, stream);
 }
 
 compton_status launch_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, float* uz, float* kx, float* ky,
@@ -678,7 +720,7 @@ compton_status launch_scatter_pairs(compton_ctx* ctx, float* ux, float* uy, floa
         a.p_begin = b;
         a.p_end = b + chunk < n ? b + chunk : n;
         const unsigned tiles = (unsigned)((a.p_end - a.p_begin + kPairsPerTile - 1) / kPairsPerTile);
-        const compton_status st = launch_step<false>(ctx, a, mode, tiles, a.p_end - a.p_begin, stream);
+        const compton_status st = launch_step<false, false>(ctx, a, mode, tiles, a.p_end - a.p_begin, stream);
         if (st != COMPTON_OK) return st;
     }
     return COMPTON_OK;

@@ -16,14 +16,19 @@ def torch_cuda():
 def to_species(torch, d):
     import paper_2206_02937_gb300 as cg
     dev = "cuda"
+    w = d.get("w")
     return cg.Species(torch.from_numpy(d["ux"]).to(dev), torch.from_numpy(d["uy"]).to(dev),
                       torch.from_numpy(d["uz"]).to(dev), torch.from_numpy(d["cell"]).to(dev),
-                      torch.from_numpy(d["id"].view(np.int32)).to(dev))
+                      torch.from_numpy(d["id"].view(np.int32)).to(dev),
+                      None if w is None else torch.from_numpy(np.ascontiguousarray(w, dtype=np.float32)).to(dev))
 
 
 def species_np(s):
-    return dict(ux=s.ux.cpu().numpy(), uy=s.uy.cpu().numpy(), uz=s.uz.cpu().numpy(),
-                cell=s.cell.cpu().numpy(), id=s.id.cpu().numpy().view(np.uint32))
+    out = dict(ux=s.ux.cpu().numpy(), uy=s.uy.cpu().numpy(), uz=s.uz.cpu().numpy(),
+               cell=s.cell.cpu().numpy(), id=s.id.cpu().numpy().view(np.uint32))
+    if s.w is not None:
+        out["w"] = s.w.cpu().numpy()
+    return out
 
 
 def gpu_step(w, step=0, gamma64=1.0e3, want_prob=True, want_flag=None):
