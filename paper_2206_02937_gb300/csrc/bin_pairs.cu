@@ -3,19 +3,20 @@
 // cells, in which the particles are binned; from this binning a list of
 // colliding leptons and photons is produced for each cell").
 //
-// Five launches per call, both species in each:
-//   k_count        histogram of cell indices (warp-aggregated atomics)
+// Six launches per call, both species in each:
+//   k_count        histogram of cell indices by run boundaries, order check
 //   k_scan_reduce  per-tile sums of N_e,c, N_g,c and M_c = min(N_e,c, N_g,c)
 //   k_scan_blocks  exclusive scan of the tile sums (one CTA)
 //   k_scan_final   per-cell offsets, CellInfo, tile maps; resets the cursors
-//   k_key_scatter  Philox key per particle, (key, index) record placed in its
-//                  cell's segment (arbitrary order inside the segment)
-//   k_sort_gather  per-cell sort of the records by (key, id) in shared memory,
-//                  then a coalesced gather of the five particle arrays into
-//                  sorted order
-// The order within a cell depends only on (key, id): the atomics of
-// k_key_scatter decide where a record lands inside its segment, and the sort
-// removes that freedom.
+//   k_place        input not in cell order only: Philox key per particle,
+//                  (key, id, momentum) record placed in its cell's segment
+//                  (arbitrary order inside the segment)
+//   k_sort_gather  per-cell sort by (key, id) in shared memory (a bucket
+//                  sort of each tile of whole cells), then a coalesced write
+//                  of the particle arrays in sorted order
+// The order within a cell depends only on (key, id): the atomics of k_place
+// decide where a record lands inside its segment, and the sort removes that
+// freedom.
 #include "ctx.hpp"
 #include "device_math.cuh"
 
@@ -60,6 +61,8 @@ __global__ void k_count(const int32_t* __restrict__ cell_e, int64_t n_e, const i
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
     const int64_t n_round = (n + 127) / 128 * 128;  // whole warps in every iteration
     const bool vec = (reinterpret_cast<uintptr_t>(cell) & 15u) == 0;
+    // cell indices are int32, so C above 2^31 admits every non-negative one
+    const uint32_t C32 = C > 0x80000000ll ? 0x80000000u : (uint32_t)C;
     bool disorder = false, bad = false;
     for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i0 < n_round; i0 += stride) {
         const int4 q = load_cells4(cell, i0, n, vec);
@@ -68,6 +71,24 @@ __global__ void k_count(const int32_t* __restrict__ cell_e, int64_t n_e, const i
         int32_t next = __shfl_down_sync(0xffffffffu, v[0], 1);
         if (lane == 0) prev = (i0 > 0 && i0 - 1 < n) ? cell[i0 - 1] : -1;
         if (lane == 31) next = i0 + 4 < n ? cell[i0 + 4] : -1;
+        if (i0 > 0 && i0 + 4 < n) {
+            // interior group: no end of the array in reach, 32-bit positions
+            // (the counts wrap in int32 as in the general path)
+            const int32_t base = (int32_t)i0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int32_t c = v[j];
+                const int32_t pc = j == 0 ? prev : v[j - 1];
+                const int32_t nc = j == 3 ? next : v[j + 1];
+                const bool ok = (uint32_t)c < C32;
+                bad |= !ok;
+                disorder |= pc > c;
+                const bool first = pc != c, last = nc != c;
+                if (ok && (first || last))
+                    atomicAdd(&count[c], (last ? base + j + 1 : 0) - (first ? base + j : 0));
+            }
+            continue;
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int64_t i = i0 + j;
@@ -395,13 +416,9 @@ struct SortSrc {
     uint32_t stream;
 };
 
-// Sort keys are (key << 32 | id) in 64 bits; the position j breaks ties
+// The order inside a cell is by (key, id), with the tile slot breaking ties
 // between equal ids (invalid input), so the order is total and every sort
 // yields a permutation.
-__device__ __forceinline__ int before64(uint64_t kj, int j, uint64_t ki, int i)
-{
-    return (kj < ki) | ((kj == ki) & (j < i));
-}
 
 __device__ __forceinline__ int bucket_of(uint32_t key, int n) { return (int)__umulhi(key, (uint32_t)n); }
 
@@ -414,37 +431,26 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src)
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 struct SortSmem {
-    uint64_t* key64;  // [cap] (key << 32) | id
+    uint32_t* id;     // [cap] particle id of each tile slot
     int32_t* cnt;     // [cap] bucket counts, then bucket starts, then ends
-    uint32_t* cmap;   // [cap] a_c | n_c << 16 of the element's cell
-    uint16_t* bidx;   // [cap] bucket of the element
-    uint16_t* ptmp;   // [cap] tile positions grouped by bucket
-    uint16_t* perm;   // [cap] sorted position -> tile position
+    uint32_t* cmap;   // [cap] a_c | n_c << 16 of the slot's cell; after the
+                      // histogram, the keys in bucket order
+    uint16_t* ptmp;   // [cap] tile slots grouped by bucket
+    uint16_t* perm;   // [cap] sorted position -> tile slot
     float* us[3];     // [cap] momenta staged from global memory
 };
 
-// Element gi of the source to tile slot i: its 64-bit sort key and momentum
-// (by cp.async when read in place; wait before using us).
-__device__ __forceinline__ uint32_t fetch_elem(const SortSrc& t, const SortSmem& m, int64_t gi, int i)
+// Placed record gi to tile slot i: momentum and id into shared memory; the
+// key is returned.
+__device__ __forceinline__ uint32_t fetch_rec(const SortSrc& t, const SortSmem& m, int64_t gi, int i)
 {
-    uint32_t key, pid;
-    if (t.rec) {
-        const uint4* q = reinterpret_cast<const uint4*>(t.rec + gi);
-        const uint4 r0 = q[0], r1 = q[1];
-        key = r0.x;
-        pid = r0.y;
-        m.us[0][i] = __uint_as_float(r0.z);
-        m.us[1][i] = __uint_as_float(r0.w);
-        m.us[2][i] = __uint_as_float(r1.x);
-    } else {
-        cp_async4(&m.us[0][i], t.u[0] + gi);
-        cp_async4(&m.us[1][i], t.u[1] + gi);
-        cp_async4(&m.us[2][i], t.u[2] + gi);
-        pid = t.id[gi];
-        key = draw(t.seed, t.step, t.stream, pid).r0;
-    }
-    m.key64[i] = ((uint64_t)key << 32) | pid;
-    return key;
+    const uint4* q = reinterpret_cast<const uint4*>(t.rec + gi);
+    const uint4 r0 = q[0], r1 = q[1];
+    m.us[0][i] = __uint_as_float(r0.z);
+    m.us[1][i] = __uint_as_float(r0.w);
+    m.us[2][i] = __uint_as_float(r1.x);
+    m.id[i] = r0.y;
+    return r0.x;
 }
 
 // Block-wide exclusive scan of cnt[0 .. R) in place (R <= kSortCap).
@@ -494,29 +500,11 @@ __device__ __forceinline__ void sort_tile_block(const SortGatherArgs& g, int s, 
 {
     const int tid = threadIdx.x, lane = (int)lane_id(), w = tid >> 5;
     const int32_t* __restrict__ off = g.off[s];
-    // cell of every position (warp per cell) and the output cell indices
-    for (int64_t c = c0 + w; c < c1; c += kSortThreads / 32) {
-        const int a = off[c] - (int32_t)o0;
-        const int n = off[c + 1] - off[c];
-        for (int j = lane; j < n; j += 32) {
-            m.cmap[a + j] = (uint32_t)a | ((uint32_t)n << 16);
-            g.out_cell[s][o0 + a + j] = (int32_t)c;
-        }
-    }
-    for (int i = tid; i < R; i += kSortThreads) m.cnt[i] = 0;
-    __syncthreads();
-    // keys, momenta, bucket histogram; the loads of a thread's elements are
-    // all issued before the first key is drawn
     constexpr int kPer = (kSortCap + kSortThreads - 1) / kSortThreads;
-    uint32_t key[kPer];
-    if (t.rec) {
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int i = tid + k * kSortThreads;
-            if (i < R) key[k] = fetch_elem(t, m, o0 + i, i);
-        }
-    } else {
-        uint32_t pid[kPer];
+    uint32_t key[kPer], pid[kPer];
+    // input in cell order: issue the tile's loads first, so they are in
+    // flight while the cell map is built
+    if (!t.rec) {
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             const int i = tid + k * kSortThreads;
@@ -527,49 +515,108 @@ __device__ __forceinline__ void sort_tile_block(const SortGatherArgs& g, int s, 
                 pid[k] = t.id[o0 + i];
             }
         }
+    }
+    // the tile's cell offsets, staged once (in the placement buffers, unused
+    // until later) when they fit; the bucket counters cleared
+    const int n_cells = (int)(c1 - c0);
+    int32_t* offs = reinterpret_cast<int32_t*>(m.ptmp);
+    const bool staged = n_cells < kSortCap;
+    if (staged)
+        for (int i = tid; i <= n_cells; i += kSortThreads) offs[i] = off[c0 + i] - (int32_t)o0;
+    for (int i = tid; i < R; i += kSortThreads) m.cnt[i] = 0;
+    __syncthreads();
+    // cell of every position (warp per cell) and the output cell indices
+    for (int64_t c = c0 + w; c < c1; c += kSortThreads / 32) {
+        const int a = staged ? offs[c - c0] : off[c] - (int32_t)o0;
+        const int n = (staged ? offs[c - c0 + 1] : off[c + 1] - (int32_t)o0) - a;
+        for (int j = lane; j < n; j += 32) {
+            m.cmap[a + j] = (uint32_t)a | ((uint32_t)n << 16);
+            g.out_cell[s][o0 + a + j] = (int32_t)c;
+        }
+    }
+    // keys (and, from placed records, momenta)
+    if (t.rec) {
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = tid + k * kSortThreads;
+            if (i < R) key[k] = fetch_rec(t, m, o0 + i, i);
+        }
+    } else {
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             const int i = tid + k * kSortThreads;
             if (i < R) {
                 key[k] = draw(t.seed, t.step, t.stream, pid[k]).r0;
-                m.key64[i] = ((uint64_t)key[k] << 32) | pid[k];
+                m.id[i] = pid[k];
             }
         }
     }
+    __syncthreads();
+    // bucket histogram; the slots' buckets stay in registers, two 16-bit
+    // buckets to a register
+    uint32_t bk2[(kPer + 1) / 2];
+#pragma unroll
+    for (int k = 0; k < (kPer + 1) / 2; ++k) bk2[k] = 0u;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
         const int i = tid + k * kSortThreads;
         if (i < R) {
             const uint32_t cm = m.cmap[i];
-            const int b = (int)(cm & 0xffffu) + bucket_of(key[k], (int)(cm >> 16));
-            m.bidx[i] = (uint16_t)b;
+            const uint32_t b = (cm & 0xffffu) + (uint32_t)bucket_of(key[k], (int)(cm >> 16));
+            bk2[k >> 1] |= b << ((k & 1) * 16);
             atomicAdd(&m.cnt[b], 1);
         }
     }
     __syncthreads();
     block_scan_counts(m.cnt, R);
     __syncthreads();
-    // positions grouped by bucket; afterwards cnt[b] = end of bucket b
-    for (int i = tid; i < R; i += kSortThreads) {
-        const int pos = atomicAdd(&m.cnt[m.bidx[i]], 1);
-        m.ptmp[pos] = (uint16_t)i;
+    // slots and keys grouped by bucket (the cell map is no longer needed);
+    // afterwards cnt[b] = end of bucket b
+    uint32_t* pkey = m.cmap;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int i = tid + k * kSortThreads;
+        if (i < R) {
+            const int pos = atomicAdd(&m.cnt[(bk2[k >> 1] >> ((k & 1) * 16)) & 0xffffu], 1);
+            m.ptmp[pos] = (uint16_t)i;
+            pkey[pos] = key[k];
+        }
     }
     __syncthreads();
     // exact rank inside each bucket (the end of bucket b - 1 is the start of
-    // bucket b, also across cells)
-    for (int i = tid; i < R; i += kSortThreads) {
-        const int b = m.bidx[i];
-        const int lo = b == 0 ? 0 : m.cnt[b - 1];
-        const int hi = m.cnt[b];
-        int fin = lo;
-        if (hi - lo > 1) {
-            const uint64_t ki = m.key64[i];
-            for (int q = lo; q < hi; ++q) {
-                const int jj = m.ptmp[q];
-                fin += before64(m.key64[jj], jj, ki, i);
+    // bucket b, also across cells): the keys of the bucket are contiguous;
+    // only a key that occurs twice needs the ids (and, for equal ids, the
+    // slots) to break the tie
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int i = tid + k * kSortThreads;
+        if (i < R) {
+            const int b = (int)((bk2[k >> 1] >> ((k & 1) * 16)) & 0xffffu);
+            const int lo = b == 0 ? 0 : m.cnt[b - 1];
+            const int hi = m.cnt[b];
+            int fin = lo;
+            if (hi - lo > 1) {
+                const uint32_t ki = key[k];
+                int less = 0, eq = 0;
+                for (int q = lo; q < hi; ++q) {
+                    const uint32_t kq = pkey[q];
+                    less += kq < ki;
+                    eq += kq == ki;
+                }
+                if (eq == 1) {
+                    fin = lo + less;
+                } else {
+                    const uint32_t di = m.id[i];
+                    for (int q = lo; q < hi; ++q) {
+                        const uint32_t kq = pkey[q];
+                        const int jj = m.ptmp[q];
+                        const uint32_t dj = m.id[jj];
+                        fin += (kq < ki) | ((kq == ki) & ((dj < di) | ((dj == di) & (jj < i))));
+                    }
+                }
             }
+            m.perm[fin] = (uint16_t)i;
         }
-        m.perm[fin] = (uint16_t)i;
     }
     cp_async_wait_all();
     __syncthreads();
@@ -580,7 +627,7 @@ __device__ __forceinline__ void sort_tile_block(const SortGatherArgs& g, int s, 
         g.out_u[s][0][go] = m.us[0][i];
         g.out_u[s][1][go] = m.us[1][i];
         g.out_u[s][2][go] = m.us[2][i];
-        g.out_id[s][go] = (uint32_t)m.key64[i];
+        g.out_id[s][go] = m.id[i];
         // the weight is not staged: read once more where the tile came from
         // (a sector this block has just read)
         if (g.out_w[s]) g.out_w[s][go] = t.rec ? rec_weight(t.rec + o0 + i) : t.w[o0 + i];
@@ -619,20 +666,19 @@ __device__ void sort_giant_cell(const SortGatherArgs& g, int s, const SortSrc& t
     __syncthreads();
 }
 
-constexpr size_t kSortSmem = (size_t)kSortCap * (8 + 4 + 4 + 2 + 2 + 2 + 12);
+constexpr size_t kSortSmem = (size_t)kSortCap * (4 + 4 + 4 + 12 + 2 + 2);
 
 __global__ void __launch_bounds__(kSortThreads, 4) k_sort_gather(SortGatherArgs g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem m;
-    m.key64 = reinterpret_cast<uint64_t*>(smem_raw);
-    m.cnt = reinterpret_cast<int32_t*>(m.key64 + kSortCap);
+    m.id = reinterpret_cast<uint32_t*>(smem_raw);
+    m.cnt = reinterpret_cast<int32_t*>(m.id + kSortCap);
     m.cmap = reinterpret_cast<uint32_t*>(m.cnt + kSortCap);
     m.us[0] = reinterpret_cast<float*>(m.cmap + kSortCap);
     m.us[1] = m.us[0] + kSortCap;
     m.us[2] = m.us[1] + kSortCap;
-    m.bidx = reinterpret_cast<uint16_t*>(m.us[2] + kSortCap);
-    m.ptmp = m.bidx + kSortCap;
+    m.ptmp = reinterpret_cast<uint16_t*>(m.us[2] + kSortCap);
     m.perm = m.ptmp + kSortCap;
 
     const int s = (int64_t)blockIdx.x < g.nb_e ? 0 : 1;

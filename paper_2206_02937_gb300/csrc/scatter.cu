@@ -147,7 +147,8 @@ __device__ __forceinline__ float analytic_P(const ScatterArgs& a, float ux, floa
 // Phase A (all pairs): locate each pair's cell in the tile's CellInfo window
 // (binary search, then forward steps), draw one Philox block for the four
 // Bernoulli uniforms, test u0 < P_b and append the candidates to the warp's
-// shared-memory list.  Phase B (candidates, one per lane): load both momenta,
+// shared-memory list.  Phase B (the lists of all warps of the CTA pooled,
+// one candidate per lane, so whole warps stay busy): load both momenta,
 // evaluate P (FP32 invariants and series sigma_KN; FP64 invariants above the
 // gamma threshold, closed-form sigma_KN above the series range; or the
 // network output), decide, append the accepted pairs to the global list
@@ -165,6 +166,7 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
 {
     __shared__ CellInfo win[kCellWindow];
     __shared__ Cand cand[kProbThreads / 32][kCandPerWarp];
+    __shared__ int warp_nq[kProbThreads / 32];
     __shared__ unsigned red[3];
     const int tid = threadIdx.x;
     const unsigned lane = tid & 31u;
@@ -220,17 +222,32 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
         if (is_cand) cand[w][nq + __popc(m & ((1u << lane) - 1u))] = Cand{ie, ig, dens, u0, (uint32_t)p};
         nq += __popc(m);
     }
-    __syncwarp();
+    if (lane == 0) warp_nq[w] = nq;
+    __syncthreads();
+    // the warps' lists as one list of the CTA's candidates, so that phase B
+    // keeps whole warps busy (about a tenth of the pairs are candidates)
+    int pre[kProbThreads / 32 + 1];
+    pre[0] = 0;
+#pragma unroll
+    for (int v = 0; v < kProbThreads / 32; ++v) pre[v + 1] = pre[v] + warp_nq[v];
+    const int n_tot = pre[kProbThreads / 32];
 
     // ---------------- phase B: candidates, one per lane ----------------
-    for (int base = 0; base < nq; base += 32) {
+    for (int base = w * 32; base < n_tot; base += kProbThreads) {
         const int j = base + (int)lane;
         bool hit = false;
         Cand c{0, 0, 0.0f, 1.0f, 0u};
         float x = -1.0f;
         float ux = 0.0f, uy = 0.0f, uz = 0.0f, kx = 0.0f, ky = 0.0f, kz = 0.0f;
-        if (j < nq) {
-            c = cand[w][j];
+        if (j < n_tot) {
+            int v = 0, first = 0;
+#pragma unroll
+            for (int q = 1; q < kProbThreads / 32; ++q)
+                if (pre[q] <= j) {
+                    v = q;
+                    first = pre[q];
+                }
+            c = cand[v][j - first];
             ux = a.u[0][c.ie];
             uy = a.u[1][c.ie];
             uz = a.u[2][c.ie];
