@@ -432,10 +432,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 struct SortSmem {
     uint32_t* id;     // [cap] particle id of each tile slot
-    int32_t* cnt;     // [cap] bucket counts, then bucket starts, then ends
+    int32_t* cnt;     // [kBucketsPerSlot * cap] bucket counts, then starts, then ends
     uint32_t* cmap;   // [cap] a_c | n_c << 16 of the slot's cell; after the
                       // histogram, the keys in bucket order
     uint16_t* ptmp;   // [cap] tile slots grouped by bucket
+    uint16_t* pbk;    // [cap] their buckets
     uint16_t* perm;   // [cap] sorted position -> tile slot
     float* us[3];     // [cap] momenta staged from global memory
 };
@@ -453,10 +454,15 @@ __device__ __forceinline__ uint32_t fetch_rec(const SortSrc& t, const SortSmem& 
     return r0.x;
 }
 
-// Block-wide exclusive scan of cnt[0 .. R) in place (R <= kSortCap).
+// Buckets per tile slot: a cell of n particles takes kBucketsPerSlot * n
+// buckets, so a bucket holds Poisson(1 / kBucketsPerSlot) particles.
+constexpr int kBucketsPerSlot = 1;
+
+// Block-wide exclusive scan of cnt[0 .. R) in place (R <= kBucketsPerSlot *
+// kSortCap).
 __device__ __forceinline__ void block_scan_counts(int32_t* cnt, int R)
 {
-    constexpr int kPer = (kSortCap + kSortThreads - 1) / kSortThreads;
+    constexpr int kPer = (kBucketsPerSlot * kSortCap + kSortThreads - 1) / kSortThreads;
     __shared__ int32_t warp_tot[kSortThreads / 32];
     const int tid = threadIdx.x, lane = (int)lane_id(), w = tid >> 5;
     const int b0 = tid * kPer;
@@ -523,7 +529,7 @@ __device__ __forceinline__ void sort_tile_block(const SortGatherArgs& g, int s, 
     const bool staged = n_cells < kSortCap;
     if (staged)
         for (int i = tid; i <= n_cells; i += kSortThreads) offs[i] = off[c0 + i] - (int32_t)o0;
-    for (int i = tid; i < R; i += kSortThreads) m.cnt[i] = 0;
+    for (int i = tid; i < kBucketsPerSlot * R; i += kSortThreads) m.cnt[i] = 0;
     __syncthreads();
     // cell of every position (warp per cell) and the output cell indices
     for (int64_t c = c0 + w; c < c1; c += kSortThreads / 32) {
@@ -562,61 +568,62 @@ __device__ __forceinline__ void sort_tile_block(const SortGatherArgs& g, int s, 
         const int i = tid + k * kSortThreads;
         if (i < R) {
             const uint32_t cm = m.cmap[i];
-            const uint32_t b = (cm & 0xffffu) + (uint32_t)bucket_of(key[k], (int)(cm >> 16));
+            const uint32_t b = kBucketsPerSlot * (cm & 0xffffu) +
+                               (uint32_t)bucket_of(key[k], kBucketsPerSlot * (int)(cm >> 16));
             bk2[k >> 1] |= b << ((k & 1) * 16);
             atomicAdd(&m.cnt[b], 1);
         }
     }
     __syncthreads();
-    block_scan_counts(m.cnt, R);
+    block_scan_counts(m.cnt, kBucketsPerSlot * R);
     __syncthreads();
-    // slots and keys grouped by bucket (the cell map is no longer needed);
-    // afterwards cnt[b] = end of bucket b
+    // slots, keys and buckets grouped by bucket (the cell map is no longer
+    // needed); afterwards cnt[b] = end of bucket b
     uint32_t* pkey = m.cmap;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
         const int i = tid + k * kSortThreads;
         if (i < R) {
-            const int pos = atomicAdd(&m.cnt[(bk2[k >> 1] >> ((k & 1) * 16)) & 0xffffu], 1);
+            const uint32_t b = (bk2[k >> 1] >> ((k & 1) * 16)) & 0xffffu;
+            const int pos = atomicAdd(&m.cnt[b], 1);
             m.ptmp[pos] = (uint16_t)i;
+            m.pbk[pos] = (uint16_t)b;
             pkey[pos] = key[k];
         }
     }
     __syncthreads();
-    // exact rank inside each bucket (the end of bucket b - 1 is the start of
-    // bucket b, also across cells): the keys of the bucket are contiguous;
-    // only a key that occurs twice needs the ids (and, for equal ids, the
-    // slots) to break the tie
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const int i = tid + k * kSortThreads;
-        if (i < R) {
-            const int b = (int)((bk2[k >> 1] >> ((k & 1) * 16)) & 0xffffu);
-            const int lo = b == 0 ? 0 : m.cnt[b - 1];
-            const int hi = m.cnt[b];
-            int fin = lo;
-            if (hi - lo > 1) {
-                const uint32_t ki = key[k];
-                int less = 0, eq = 0;
-                for (int q = lo; q < hi; ++q) {
-                    const uint32_t kq = pkey[q];
-                    less += kq < ki;
-                    eq += kq == ki;
-                }
-                if (eq == 1) {
-                    fin = lo + less;
-                } else {
-                    const uint32_t di = m.id[i];
-                    for (int q = lo; q < hi; ++q) {
-                        const uint32_t kq = pkey[q];
-                        const int jj = m.ptmp[q];
-                        const uint32_t dj = m.id[jj];
-                        fin += (kq < ki) | ((kq == ki) & ((dj < di) | ((dj == di) & (jj < i))));
-                    }
+    // exact rank inside each bucket, one thread per entry of the grouped list
+    // (the end of bucket b - 1 is the start of bucket b, also across cells):
+    // neighbouring threads read the same or neighbouring buckets, so a
+    // bucket's keys reach them by broadcast; only a key that occurs twice
+    // needs the ids (and, for equal ids, the slots) to break the tie
+    for (int q = tid; q < R; q += kSortThreads) {
+        const int b = m.pbk[q];
+        const int lo = b == 0 ? 0 : m.cnt[b - 1];
+        const int hi = m.cnt[b];
+        const int i = m.ptmp[q];
+        int fin = lo;
+        if (hi - lo > 1) {
+            const uint32_t ki = pkey[q];
+            int less = 0, eq = 0;
+            for (int r = lo; r < hi; ++r) {
+                const uint32_t kr = pkey[r];
+                less += kr < ki;
+                eq += kr == ki;
+            }
+            if (eq == 1) {
+                fin = lo + less;
+            } else {
+                const uint32_t di = m.id[i];
+                for (int r = lo; r < hi; ++r) {
+                    const uint32_t kr = pkey[r];
+                    const int jj = m.ptmp[r];
+                    const uint32_t dj = m.id[jj];
+                    fin += (kr < ki) | ((kr == ki) & ((dj < di) | ((dj == di) & (jj < i))));
                 }
             }
-            m.perm[fin] = (uint16_t)i;
         }
+        m.perm[fin] = (uint16_t)i;
     }
     cp_async_wait_all();
     __syncthreads();
@@ -666,7 +673,7 @@ __device__ void sort_giant_cell(const SortGatherArgs& g, int s, const SortSrc& t
     __syncthreads();
 }
 
-constexpr size_t kSortSmem = (size_t)kSortCap * (4 + 4 + 4 + 12 + 2 + 2);
+constexpr size_t kSortSmem = (size_t)kSortCap * (4 + 4 * kBucketsPerSlot + 4 + 12 + 2 + 2 + 2);
 
 __global__ void __launch_bounds__(kSortThreads, 4) k_sort_gather(SortGatherArgs g)
 {
@@ -674,12 +681,13 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_gather(SortGatherArgs 
     SortSmem m;
     m.id = reinterpret_cast<uint32_t*>(smem_raw);
     m.cnt = reinterpret_cast<int32_t*>(m.id + kSortCap);
-    m.cmap = reinterpret_cast<uint32_t*>(m.cnt + kSortCap);
+    m.cmap = reinterpret_cast<uint32_t*>(m.cnt + kBucketsPerSlot * kSortCap);
     m.us[0] = reinterpret_cast<float*>(m.cmap + kSortCap);
     m.us[1] = m.us[0] + kSortCap;
     m.us[2] = m.us[1] + kSortCap;
     m.ptmp = reinterpret_cast<uint16_t*>(m.us[2] + kSortCap);
     m.perm = m.ptmp + kSortCap;
+    m.pbk = m.perm + kSortCap;
 
     const int s = (int64_t)blockIdx.x < g.nb_e ? 0 : 1;
     const int64_t b = s == 0 ? blockIdx.x : blockIdx.x - g.nb_e;
