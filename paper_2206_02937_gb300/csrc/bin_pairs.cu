@@ -64,13 +64,34 @@ __global__ void k_count(const int32_t* __restrict__ cell_e, int64_t n_e, const i
     // cell indices are int32, so C above 2^31 admits every non-negative one
     const uint32_t C32 = C > 0x80000000ll ? 0x80000000u : (uint32_t)C;
     bool disorder = false, bad = false;
-    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i0 < n_round; i0 += stride) {
-        const int4 q = load_cells4(cell, i0, n, vec);
+    // the next group's loads are issued before this group is processed, so
+    // two groups per thread are in flight
+    auto edge = [&](int64_t j0) -> int32_t {
+        if (lane == 0) return (j0 > 0 && j0 - 1 < n) ? cell[j0 - 1] : -1;
+        if (lane == 31) return j0 + 4 < n ? cell[j0 + 4] : -1;
+        return -1;
+    };
+    int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    int4 q = make_int4(-1, -1, -1, -1);
+    int32_t e = -1;
+    if (i0 < n_round) {
+        q = load_cells4(cell, i0, n, vec);
+        e = edge(i0);
+    }
+    for (; i0 < n_round; i0 += stride) {
+        int4 qn = make_int4(-1, -1, -1, -1);
+        int32_t en = -1;
+        if (i0 + stride < n_round) {
+            qn = load_cells4(cell, i0 + stride, n, vec);
+            en = edge(i0 + stride);
+        }
         const int32_t v[4] = {q.x, q.y, q.z, q.w};
         int32_t prev = __shfl_up_sync(0xffffffffu, v[3], 1);
         int32_t next = __shfl_down_sync(0xffffffffu, v[0], 1);
-        if (lane == 0) prev = (i0 > 0 && i0 - 1 < n) ? cell[i0 - 1] : -1;
-        if (lane == 31) next = i0 + 4 < n ? cell[i0 + 4] : -1;
+        if (lane == 0) prev = e;
+        if (lane == 31) next = e;
+        q = qn;
+        e = en;
         if (i0 > 0 && i0 + 4 < n) {
             // interior group: no end of the array in reach, 32-bit positions
             // (the counts wrap in int32 as in the general path)

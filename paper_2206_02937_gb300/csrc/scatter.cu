@@ -165,6 +165,7 @@ template <bool kBinned, bool kWeighted>
 __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
 {
     __shared__ CellInfo win[kCellWindow];
+    __shared__ float wbound[kCellWindow];  // each staged cell's candidate bound
     __shared__ Cand cand[kProbThreads / 32][kCandPerWarp];
     __shared__ int warp_nq[kProbThreads / 32];
     __shared__ unsigned red[3];
@@ -181,7 +182,11 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
         c_first = a.tile_cell[tile];
         nwin = a.tile_cell[tile + 1] - c_first + 1;
         if (nwin <= kCellWindow)
-            for (int i = tid; i < nwin; i += kProbThreads) win[i] = a.cinfo[c_first + i];
+            for (int i = tid; i < nwin; i += kProbThreads) {
+                const CellInfo c = a.cinfo[c_first + i];
+                win[i] = c;
+                if (!kWeighted) wbound[i] = one_minus_exp_neg(2.0002f * c.dens * a.dt);
+            }
     }
     __syncthreads();
 
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
         const int64_t p = pb + r;
         const bool valid = p < total;
         int ie = 0, ig = 0;
-        float dens = 0.0f;
+        float dens = 0.0f, bound = 0.0f;
         if (valid) {
             if (kBinned) {
                 while (ci + 1 < nwin && (int64_t)cw[ci + 1].pair_off <= p) ++ci;
@@ -208,15 +213,17 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
                 ie = c.e_start + j;
                 ig = c.g_start + j;
                 dens = pair_density<kWeighted>(a, c.dens, ie, ig);
+                bound = (!kWeighted && nwin <= kCellWindow) ? wbound[ci] : one_minus_exp_neg(2.0002f * dens * a.dt);
             } else {
                 ie = (int)p;
                 ig = (int)p;
                 dens = a.n_dens[p];
+                bound = one_minus_exp_neg(2.0002f * dens * a.dt);
             }
             ++n_pairs;
         }
         const float u0 = u24_closed0(words[r]);
-        const bool is_cand = valid && (all || u0 < one_minus_exp_neg(2.0002f * dens * a.dt));
+        const bool is_cand = valid && (all || u0 < bound);
         if (valid && !is_cand && a.flag_out) a.flag_out[p] = 0;
         const unsigned m = __ballot_sync(0xffffffffu, is_cand);
         if (is_cand) cand[w][nq + __popc(m & ((1u << lane) - 1u))] = Cand{ie, ig, dens, u0, (uint32_t)p};
@@ -305,6 +312,7 @@ template <bool kBinned, bool kWeighted>
 __global__ void __launch_bounds__(kProbThreads, 4) k_cand(ScatterArgs a)
 {
     __shared__ CellInfo win[kCellWindow];
+    __shared__ float wbound[kCellWindow];  // each staged cell's candidate bound
     __shared__ unsigned red_pairs;
     __shared__ int warp_cnt[kProbThreads / 32];
     __shared__ uint32_t cta_base;
@@ -320,7 +328,11 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_cand(ScatterArgs a)
         c_first = a.tile_cell[tile];
         nwin = a.tile_cell[tile + 1] - c_first + 1;
         if (nwin <= kCellWindow)
-            for (int i = tid; i < nwin; i += kProbThreads) win[i] = a.cinfo[c_first + i];
+            for (int i = tid; i < nwin; i += kProbThreads) {
+                const CellInfo c = a.cinfo[c_first + i];
+                win[i] = c;
+                if (!kWeighted) wbound[i] = one_minus_exp_neg(2.0002f * c.dens * a.dt);
+            }
     }
     __syncthreads();
     const int64_t pb = p0 + (int64_t)tid * kPairsPerThread;
@@ -340,6 +352,7 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_cand(ScatterArgs a)
         ie[r] = 0;
         ig[r] = 0;
         dens[r] = 0.0f;
+        float bound = 0.0f;
         if (valid) {
             if (kBinned) {
                 while (ci + 1 < nwin && (int64_t)cw[ci + 1].pair_off <= p) ++ci;
@@ -348,15 +361,18 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_cand(ScatterArgs a)
                 ie[r] = c.e_start + j;
                 ig[r] = c.g_start + j;
                 dens[r] = pair_density<kWeighted>(a, c.dens, ie[r], ig[r]);
+                bound = (!kWeighted && nwin <= kCellWindow) ? wbound[ci]
+                                                            : one_minus_exp_neg(2.0002f * dens[r] * a.dt);
             } else {
                 ie[r] = (int)p;
                 ig[r] = (int)p;
                 dens[r] = a.n_dens[p];
+                bound = one_minus_exp_neg(2.0002f * dens[r] * a.dt);
             }
             ++n_pairs;
         }
         u0[r] = u24_closed0(words[r]);
-        is_cand[r] = valid && (all || u0[r] < one_minus_exp_neg(2.0002f * dens[r] * a.dt));
+        is_cand[r] = valid && (all || u0[r] < bound);
         if (valid && !is_cand[r] && a.flag_out) a.flag_out[p] = 0;
     }
     // the candidates' momenta: all loads in flight before the first use
