@@ -45,7 +45,7 @@ MEASURED_TRAFFIC = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nx", type=int, default=512)
@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--train-steps", type=int, default=8000)
     ap.add_argument("--train-balanced", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "c5", "ic"],
@@ -412,11 +412,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         dist.destroy_process_group()
 
 
-def train_surrogate(cg, torch, ctx, dev, n_samples=1 << 20, steps=8000, batch=8192, lr=1e-2, balanced=False):
+def train_surrogate(cg, torch, ctx, dev, n_samples=10_000_000, steps=8000, batch=8192, lr=1e-2, balanced=False):
     """Train the network on the GPU on analytic targets over the surrogate's
     range (gamma log-uniform on [1, 1e3], eps log-uniform on [1e-4, 1]):
     Adam with the learning rate decayed from lr to 0 on a cosine, MAE loss,
-    Glorot-uniform weights (seed 0).  balanced=True weights the loss by the
+    Glorot-uniform weights (seed 0), 10M samples split 80/20 into training
+    and held-out sets.  balanced=True weights the loss by the
     data-balancing weights (32 log bins of r on [1e-6, 1]); with the MAE
     loss that pulls the network towards the rare tiny targets and costs
     accuracy everywhere else, so it is off by default.  Not timed as part of
@@ -440,11 +441,12 @@ def train_surrogate(cg, torch, ctx, dev, n_samples=1 << 20, steps=8000, batch=81
         edges = (1e-6 * (1e6) ** (np.arange(33) / 32)).astype(np.float32)
         cg.compton_mlp_balance_weights(ctx, r, edges, wts)
     gen = torch.Generator(device=dev).manual_seed(0)
+    n_train = n_samples * 4 // 5
     losses = []
     torch.cuda.synchronize()
     t0 = time.time()
     for it in range(steps):
-        idx = torch.randint(0, n_samples, (batch,), device=dev, generator=gen)
+        idx = torch.randint(0, n_train, (batch,), device=dev, generator=gen)
         lr_it = lr * 0.5 * (1.0 + np.cos(np.pi * it / steps))
         loss = cg.compton_mlp_train_step(ctx, ut[:, idx].contiguous(), kt[:, idx].contiguous(),
                                          r[idx].contiguous(), None if wts is None else wts[idx].contiguous(),
@@ -454,10 +456,22 @@ def train_surrogate(cg, torch, ctx, dev, n_samples=1 << 20, steps=8000, batch=81
     torch.cuda.synchronize()
     train_s = time.time() - t0
     cg.compton_mlp_calibrate(ctx, ut[:, :65536].contiguous(), kt[:, :65536].contiguous())
+    # held-out 20 %: error of r in FP32 and BF16 inference
+    uh, kh, rh = ut[:, n_train:].contiguous(), kt[:, n_train:].contiguous(), r[n_train:]
+    held = {}
+    for md, name in ((cg.MODE_MLP_FP32, "fp32"), (cg.MODE_MLP_BF16, "bf16")):
+        o = torch.empty_like(rh)
+        cg.compton_mlp_infer(ctx, uh, kh, md, o)
+        err = (o.double() - rh.double()).abs()
+        big = rh > 1e-3
+        held[name] = {"mae_r": float(err.mean()),
+                      "mean_rel_r_above_1e-3": float((err[big] / rh[big].double()).mean()),
+                      "max_rel_r_above_1e-3": float((err[big] / rh[big].double()).max())}
     torch.cuda.synchronize()
     return {"steps": steps, "batch": batch, "lr": f"{lr} cosine-decayed to 0", "samples": n_samples,
+            "split": "80 % training / 20 % held out",
             "loss": "MAE" + (" weighted by 32 log bins of r" if balanced else ""),
-            "loss_first": losses[0], "loss_last": losses[-1], "train_s": train_s}
+            "loss_first": losses[0], "loss_last": losses[-1], "train_s": train_s, "held_out": held}
 
 
 def train_pnet(cg, torch, ctx, dev, w_cell, p_max_cells, n_samples=1 << 20, steps=8000, batch=8192, lr=1e-2):

@@ -6,19 +6,21 @@
 // section in the lepton rest frame, carried back to the simulation frame).
 //
 // Two kernels per step:
-//   k_pair_prob  one CTA per tile of 1024 pairs (256 threads x 4 consecutive
-//                pairs): the tile's CellInfo window staged in shared memory,
-//                each thread locates its pairs (binary search in the window,
-//                then forward steps), loads both momenta, draws one Philox
-//                block for the four Bernoulli uniforms and evaluates all four
-//                probabilities in straight-line FP32 (x and v without
-//                cancellation, sigma_KN from its series, 1 - exp(-n dt s v)),
-//                with a second pass for the rare pairs (FP64 invariants above
-//                the gamma threshold, closed-form sigma_KN above the series
-//                range).  Accepted pairs are appended to a list in global
-//                memory (warp-aggregated atomics).  No queue and little shared
-//                memory: many warps per SM hide the latency of the long
-//                arithmetic chains.
+//   k_pair_prob  persistent CTAs (four per SM), each taking tiles of 1024
+//                pairs (256 threads x 4 consecutive pairs) in turn, with the
+//                next tile's CellInfo window copied into shared memory while
+//                the current one is processed.  Each thread locates its pairs
+//                (binary search in the window, then forward steps) and draws
+//                one Philox block for the four Bernoulli uniforms; pairs whose
+//                uniform lies below the probability bound (candidates, about a
+//                tenth) are pooled over the CTA, and each candidate's momenta
+//                are loaded and its probability evaluated in straight-line
+//                FP32 (x and v without cancellation, sigma_KN from its series,
+//                1 - exp(-n dt s v)), with a second pass for the rare pairs
+//                (FP64 invariants above the gamma threshold, closed-form
+//                sigma_KN above the series range).  Accepted pairs are
+//                appended to a list in global memory (warp-aggregated
+//                atomics).
 //   k_collide    every accepted pair (a few percent of all pairs) at full
 //                warp width: inverse-CDF angle, rest-frame boost and momentum
 //                update (FP32, or FP64 above the configured gamma eps),
@@ -161,146 +163,182 @@ struct Cand {
     uint32_t p;
 };
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Persistent CTAs, each taking tiles blockIdx.x, blockIdx.x + gridDim.x, ...:
+// the CellInfo window of the next tile is copied into the other of two
+// shared-memory buffers while the current tile is processed, and the tile
+// map entries of the tile after that are loaded into registers, so the two
+// dependent global round trips of a tile (tile map, then window) overlap the
+// work of the tile before.
 template <bool kBinned, bool kWeighted>
 __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
 {
-    __shared__ CellInfo win[kCellWindow];
-    __shared__ float wbound[kCellWindow];  // each staged cell's candidate bound
+    __shared__ __align__(16) CellInfo win[2][kCellWindow];
     __shared__ Cand cand[kProbThreads / 32][kCandPerWarp];
     __shared__ int warp_nq[kProbThreads / 32];
-    __shared__ unsigned red[3];
+    __shared__ unsigned red[2];
     const int tid = threadIdx.x;
     const unsigned lane = tid & 31u;
     const int w = tid >> 5;
     const int64_t total = kBinned ? *a.n_pairs : a.p_end;
-    const int64_t tile = blockIdx.x;
-    const int64_t p0 = (kBinned ? 0 : a.p_begin) + tile * kPairsPerTile;
-    if (p0 >= total) return;
-    if (tid < 3) red[tid] = 0;
-    int c_first = 0, nwin = 0;
-    if (kBinned) {
-        c_first = a.tile_cell[tile];
-        nwin = a.tile_cell[tile + 1] - c_first + 1;
-        if (nwin <= kCellWindow)
-            for (int i = tid; i < nwin; i += kProbThreads) {
-                const CellInfo c = a.cinfo[c_first + i];
-                win[i] = c;
-                if (!kWeighted) wbound[i] = one_minus_exp_neg(2.0002f * c.dens * a.dt);
-            }
-    }
-    __syncthreads();
-
-    // ---------------- phase A: every pair ----------------
-    const int64_t pb = p0 + (int64_t)tid * kPairsPerThread;
-    const Philox4 rnd4 = draw(a.seed, a.step, kStreamScatter, (uint32_t)(pb >> 2));
-    const uint32_t words[4] = {rnd4.r0, rnd4.r1, rnd4.r2, rnd4.r3};
+    const int64_t pbase = kBinned ? 0 : a.p_begin;
+    const int64_t n_tiles = total > pbase ? (total - pbase + kPairsPerTile - 1) / kPairsPerTile : 0;
+    const int64_t G = gridDim.x;
+    if (tid < 2) red[tid] = 0;
     const bool all = a.prob_out != nullptr;
-    const CellInfo* cw = nwin <= kCellWindow ? win : a.cinfo + c_first;
-    int ci = (kBinned && pb < total) ? find_cell(cw, nwin, pb) : 0;
-    unsigned n_pairs = 0, n_hit = 0, n_fb = 0;
-    int nq = 0;
-#pragma unroll
-    for (int r = 0; r < kPairsPerThread; ++r) {
-        const int64_t p = pb + r;
-        const bool valid = p < total;
-        int ie = 0, ig = 0;
-        float dens = 0.0f, bound = 0.0f;
-        if (valid) {
-            if (kBinned) {
-                while (ci + 1 < nwin && (int64_t)cw[ci + 1].pair_off <= p) ++ci;
-                const CellInfo c = cw[ci];
-                const int j = (int)(p - c.pair_off);
-                ie = c.e_start + j;
-                ig = c.g_start + j;
-                dens = pair_density<kWeighted>(a, c.dens, ie, ig);
-                bound = (!kWeighted && nwin <= kCellWindow) ? wbound[ci] : one_minus_exp_neg(2.0002f * dens * a.dt);
-            } else {
-                ie = (int)p;
-                ig = (int)p;
-                dens = a.n_dens[p];
-                bound = one_minus_exp_neg(2.0002f * dens * a.dt);
-            }
-            ++n_pairs;
-        }
-        const float u0 = u24_closed0(words[r]);
-        const bool is_cand = valid && (all || u0 < bound);
-        if (valid && !is_cand && a.flag_out) a.flag_out[p] = 0;
-        const unsigned m = __ballot_sync(0xffffffffu, is_cand);
-        if (is_cand) cand[w][nq + __popc(m & ((1u << lane) - 1u))] = Cand{ie, ig, dens, u0, (uint32_t)p};
-        nq += __popc(m);
-    }
-    if (lane == 0) warp_nq[w] = nq;
-    __syncthreads();
-    // the warps' lists as one list of the CTA's candidates, so that phase B
-    // keeps whole warps busy (about a tenth of the pairs are candidates)
-    int pre[kProbThreads / 32 + 1];
-    pre[0] = 0;
-#pragma unroll
-    for (int v = 0; v < kProbThreads / 32; ++v) pre[v + 1] = pre[v] + warp_nq[v];
-    const int n_tot = pre[kProbThreads / 32];
+    unsigned n_pairs = 0, n_hit = 0;
 
-    // ---------------- phase B: candidates, one per lane ----------------
-    for (int base = w * 32; base < n_tot; base += kProbThreads) {
-        const int j = base + (int)lane;
-        bool hit = false;
-        Cand c{0, 0, 0.0f, 1.0f, 0u};
-        float x = -1.0f;
-        float ux = 0.0f, uy = 0.0f, uz = 0.0f, kx = 0.0f, ky = 0.0f, kz = 0.0f;
-        if (j < n_tot) {
-            int v = 0, first = 0;
-#pragma unroll
-            for (int q = 1; q < kProbThreads / 32; ++q)
-                if (pre[q] <= j) {
-                    v = q;
-                    first = pre[q];
-                }
-            c = cand[v][j - first];
-            ux = a.u[0][c.ie];
-            uy = a.u[1][c.ie];
-            uz = a.u[2][c.ie];
-            kx = a.k[0][c.ig];
-            ky = a.k[1][c.ig];
-            kz = a.k[2][c.ig];
-            const Invariants inv = invariants_f32(ux, uy, uz, kx, ky, kz);
-            x = inv.x;
-            float P;
-            if (inv.gamma > a.gamma64 || !(inv.x < 0.99f)) {
-                P = analytic_P(a, ux, uy, uz, kx, ky, kz, c.dens, &x);
-            } else {
-                const float Pr = one_minus_exp_neg(c.dens * a.dt * 0.375f * kn_F2_series(inv.x) * inv.v);
-                P = inv.eps > 0.0f ? Pr : 0.0f;
-            }
-            hit = c.u0 < P;
-            if (a.prob_out) a.prob_out[c.p] = P;
-            if (a.flag_out) a.flag_out[c.p] = hit ? 1 : 0;
+    // window of tile tt: its first cell and the number of staged CellInfo
+    int cf = 0, nw = 0, cf_n = 0, nw_n = 0;
+    auto meta = [&](int64_t tt, int& c_first, int& nwin) {
+        c_first = a.tile_cell[tt];
+        nwin = a.tile_cell[tt + 1] - c_first + 1;
+    };
+    auto stage = [&](int buf, int c_first, int nwin) {
+        if (nwin <= kCellWindow)
+            for (int i = tid; i < nwin; i += kProbThreads) cp_async16(&win[buf][i], a.cinfo + c_first + i);
+        cp_async_commit();
+    };
+    int64_t t = blockIdx.x;
+    if (kBinned) {
+        if (t < n_tiles) {
+            meta(t, cf, nw);
+            stage(0, cf, nw);
         }
-        const unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (m) {
-            uint32_t at = 0;
-            if (lane == 0) at = atomicAdd(a.n_accepted, (uint32_t)__popc(m));
-            at = __shfl_sync(0xffffffffu, at, 0);
-            if (hit) {
-                a.accepted[at + __popc(m & ((1u << lane) - 1u))] =
-                    AcceptedPair{c.ie, c.ig, x, c.p, {ux, uy, uz}, {kx, ky, kz}, {0u, 0u}};
-                ++n_hit;
-            }
-        }
+        if (t + G < n_tiles) meta(t + G, cf_n, nw_n);
     }
+    for (int buf = 0; t < n_tiles; t += G, buf ^= 1) {
+        int cf_nn = 0, nw_nn = 0;
+        if (kBinned) {
+            cp_async_wait_all();
+            __syncthreads();  // this tile's window is in; the previous tile is done with the other buffer
+            if (t + G < n_tiles) stage(buf ^ 1, cf_n, nw_n);
+            if (t + 2 * G < n_tiles) meta(t + 2 * G, cf_nn, nw_nn);
+        } else {
+            __syncthreads();  // the previous tile is done with the candidate lists
+        }
+        const int64_t p0 = pbase + t * kPairsPerTile;
+
+        // ---------------- phase A: every pair ----------------
+        const int64_t pb = p0 + (int64_t)tid * kPairsPerThread;
+        const Philox4 rnd4 = draw(a.seed, a.step, kStreamScatter, (uint32_t)(pb >> 2));
+        const uint32_t words[4] = {rnd4.r0, rnd4.r1, rnd4.r2, rnd4.r3};
+        const CellInfo* cw = nw <= kCellWindow ? win[buf] : a.cinfo + cf;
+        int ci = (kBinned && pb < total) ? find_cell(cw, nw, pb) : 0;
+        int nq = 0;
+#pragma unroll
+        for (int r = 0; r < kPairsPerThread; ++r) {
+            const int64_t p = pb + r;
+            const bool valid = p < total;
+            int ie = 0, ig = 0;
+            float dens = 0.0f;
+            if (valid) {
+                if (kBinned) {
+                    while (ci + 1 < nw && (int64_t)cw[ci + 1].pair_off <= p) ++ci;
+                    const CellInfo c = cw[ci];
+                    const int j = (int)(p - c.pair_off);
+                    ie = c.e_start + j;
+                    ig = c.g_start + j;
+                    dens = pair_density<kWeighted>(a, c.dens, ie, ig);
+                } else {
+                    ie = (int)p;
+                    ig = (int)p;
+                    dens = a.n_dens[p];
+                }
+                ++n_pairs;
+            }
+            const float u0 = u24_closed0(words[r]);
+            const bool is_cand = valid && (all || u0 < one_minus_exp_neg(2.0002f * dens * a.dt));
+            if (valid && !is_cand && a.flag_out) a.flag_out[p] = 0;
+            const unsigned m = __ballot_sync(0xffffffffu, is_cand);
+            if (is_cand) cand[w][nq + __popc(m & ((1u << lane) - 1u))] = Cand{ie, ig, dens, u0, (uint32_t)p};
+            nq += __popc(m);
+        }
+        if (lane == 0) warp_nq[w] = nq;
+        __syncthreads();
+        // the warps' lists as one list of the CTA's candidates, so that phase
+        // B keeps whole warps busy (about a tenth of the pairs are candidates)
+        int pre[kProbThreads / 32 + 1];
+        pre[0] = 0;
+#pragma unroll
+        for (int v = 0; v < kProbThreads / 32; ++v) pre[v + 1] = pre[v] + warp_nq[v];
+        const int n_tot = pre[kProbThreads / 32];
+
+        // ---------------- phase B: candidates, one per lane ----------------
+        for (int base = w * 32; base < n_tot; base += kProbThreads) {
+            const int j = base + (int)lane;
+            bool hit = false;
+            Cand c{0, 0, 0.0f, 1.0f, 0u};
+            float x = -1.0f;
+            float ux = 0.0f, uy = 0.0f, uz = 0.0f, kx = 0.0f, ky = 0.0f, kz = 0.0f;
+            if (j < n_tot) {
+                int v = 0, first = 0;
+#pragma unroll
+                for (int q = 1; q < kProbThreads / 32; ++q)
+                    if (pre[q] <= j) {
+                        v = q;
+                        first = pre[q];
+                    }
+                c = cand[v][j - first];
+                ux = a.u[0][c.ie];
+                uy = a.u[1][c.ie];
+                uz = a.u[2][c.ie];
+                kx = a.k[0][c.ig];
+                ky = a.k[1][c.ig];
+                kz = a.k[2][c.ig];
+                const Invariants inv = invariants_f32(ux, uy, uz, kx, ky, kz);
+                x = inv.x;
+                float P;
+                if (inv.gamma > a.gamma64 || !(inv.x < 0.99f)) {
+                    P = analytic_P(a, ux, uy, uz, kx, ky, kz, c.dens, &x);
+                } else {
+                    const float Pr = one_minus_exp_neg(c.dens * a.dt * 0.375f * kn_F2_series(inv.x) * inv.v);
+                    P = inv.eps > 0.0f ? Pr : 0.0f;
+                }
+                hit = c.u0 < P;
+                if (a.prob_out) a.prob_out[c.p] = P;
+                if (a.flag_out) a.flag_out[c.p] = hit ? 1 : 0;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (m) {
+                uint32_t at = 0;
+                if (lane == 0) at = atomicAdd(a.n_accepted, (uint32_t)__popc(m));
+                at = __shfl_sync(0xffffffffu, at, 0);
+                if (hit) {
+                    a.accepted[at + __popc(m & ((1u << lane) - 1u))] =
+                        AcceptedPair{c.ie, c.ig, x, c.p, {ux, uy, uz}, {kx, ky, kz}, {0u, 0u}};
+                    ++n_hit;
+                }
+            }
+        }
+        cf = cf_n;
+        nw = nw_n;
+        cf_n = cf_nn;
+        nw_n = nw_nn;
+    }
+    cp_async_wait_all();
 
     // counters: warp sums, then one atomic per block
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         n_pairs += __shfl_xor_sync(0xffffffffu, n_pairs, d);
         n_hit += __shfl_xor_sync(0xffffffffu, n_hit, d);
-        n_fb += __shfl_xor_sync(0xffffffffu, n_fb, d);
     }
+    __syncthreads();
     if (lane == 0) {
         atomicAdd(&red[0], n_pairs);
         atomicAdd(&red[1], n_hit);
     }
     __syncthreads();
     if (tid == 0) {
-        atomicAdd(&a.stats->pairs_tested, (unsigned long long)red[0]);
+        if (red[0]) atomicAdd(&a.stats->pairs_tested, (unsigned long long)red[0]);
         if (red[1]) atomicAdd(&a.stats->scatters, (unsigned long long)red[1]);
     }
 }
@@ -612,6 +650,17 @@ __global__ void k_sample_angle(const float* __restrict__ x, const uint32_t* __re
     }
 }
 
+// Persistent probability kernel: at most the CTAs resident at once (four
+// per SM).
+unsigned prob_grid(unsigned tiles)
+{
+    int dev = 0, n_sm = 1;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm < 1) n_sm = 1;
+    const unsigned cap = (unsigned)n_sm * 4u;
+    return tiles < 1u ? 1u : (tiles < cap ? tiles : cap);
+}
+
 int collide_grid(int64_t max_accepted)
 {
     int dev = 0, n_sm = 1;
@@ -655,7 +704,7 @@ compton_status launch_step(compton_ctx* ctx, ScatterArgs& a, compton_mode mode, 
     COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->n_accepted, 0, sizeof(uint32_t), stream));
     if (mode == COMPTON_MODE_PLAIN) {
         TimedScope ts_(ctx, COMPTON_K_PROB, stream);
-        k_pair_prob<kBinned, kWeighted><<<tiles, kProbThreads, 0, stream>>>(a);
+        k_pair_prob<kBinned, kWeighted><<<prob_grid(tiles), kProbThreads, 0, stream>>>(a);
     } else {
         COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->n_cand, 0, sizeof(uint32_t), stream));
         {
