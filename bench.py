@@ -1007,13 +1007,14 @@ def train_tl(cg, torch, ctx, dev, stages=(25.0, 50.0, 100.0), n_set=1 << 19, ste
 
 
 def train_tl_pnet(cg, torch, ctx, dev, w_cell, p_max, stages=(25.0, 50.0, 100.0), n_set=1 << 19,
-                  steps=(20000, 8000, 8000), lr=(3e-3, 1e-3, 1e-3), batch=8192):
+                  steps=(20000, 8000, 8000), lr=(3e-3, 1e-3, 1e-3), batch=8192, seed=1):
     """The same three transfer-learning stages for the paper's own 9-12-9
     network, whose inputs also carry the macro-particle weights and the
     cell's P_max (here those of the inverse-Compton cells).  Returns the
-    parameters after each stage."""
+    parameters after each stage.  seed sets the initial weights and the
+    minibatch draws."""
     from paper_2206_02937_gb300 import workloads as wl
-    rng = np.random.default_rng(1)
+    rng = np.random.default_rng(seed)
     theta = np.zeros(cg.PNET_PARAMS, dtype=np.float32)
     at = 0
     for o, i in [(9, 9), (12, 9), (9, 12), (1, 9)]:
@@ -1023,7 +1024,7 @@ def train_tl_pnet(cg, torch, ctx, dev, w_cell, p_max, stages=(25.0, 50.0, 100.0)
     g_max, e_min, e_max = IC_RANGE
     cg.compton_pnet_set_params(ctx, theta, np.array(IC_FS, dtype=np.float32), g_max, e_min, e_max)
     us, ks, thetas, info = [], [], [], []
-    gen = torch.Generator(device=dev).manual_seed(1)
+    gen = torch.Generator(device=dev).manual_seed(seed)
     for s_i, p0 in enumerate(stages):
         u, k = wl.waterbag_pairs(n_set, p0, seed=25 + s_i)
         us.append(torch.from_numpy(u).to(dev))
@@ -1097,9 +1098,19 @@ def run_ic(args, rank: int, world: int, local_rank: int):
     blobs, tl_info = train_tl(cg, torch, ctx, dev)
     t_train = time.time() - t_train
     ic_p_max = 2.0 * 1.0 * probe.dt  # density 1 in every cell
+    # the paper's network, three training runs (initial weights and
+    # minibatches from seeds 1, 2, 3; the gradient sums use float atomics, so
+    # a run is not bit-reproducible either): its extrapolation to the
+    # benchmark's photons varies from run to run, so all three are reported
     t_pnet = time.time()
-    pnet_thetas, pnet_info = train_tl_pnet(cg, torch, ctx, dev, probe.w_over_v, ic_p_max)
-    t_pnet = time.time() - t_pnet
+    pnet_runs = [train_tl_pnet(cg, torch, ctx, dev, probe.w_over_v, ic_p_max, seed=sd) for sd in (1, 2, 3)]
+    t_pnet = (time.time() - t_pnet) / len(pnet_runs)
+    pnet_info = pnet_runs[0][1]
+
+    def load_pnet(run):
+        cg.compton_pnet_set_params(ctx, pnet_runs[run][0][-1], np.array(IC_FS, dtype=np.float32), *IC_RANGE)
+
+    load_pnet(0)
 
     # head-on sweep (the paper's probability comparison): p_e along +x,
     # photons along -x with log-spaced energy
@@ -1167,12 +1178,19 @@ def run_ic(args, rank: int, world: int, local_rank: int):
             entry[tag] = {"scattered_photons": n_nn, "peak_eps": peak_nn,
                           "spectrum_L1_vs_plain": float((h_nn - h_pl).abs().sum()),
                           "fallbacks": st_nn["mlp_fallbacks"]}
-        # the paper's network after the last stage (FP32, CUDA cores)
-        k_pn, st_pn = ic_simulation(cg, torch, ctx, w, n_steps, cg.MODE_PNET, dev)
-        h_pn, n_pn, peak_pn = ic_spectrum(torch, k_pn, 2.5)
-        entry["pnet_tl_stage_3"] = {"scattered_photons": n_pn, "peak_eps": peak_pn,
-                                    "spectrum_L1_vs_plain": float((h_pn - h_pl).abs().sum()),
-                                    "fallbacks": st_pn["mlp_fallbacks"]}
+        # the paper's network after the last stage (FP32, CUDA cores), each
+        # training run
+        runs = []
+        for run in range(len(pnet_runs)):
+            load_pnet(run)
+            k_pn, st_pn = ic_simulation(cg, torch, ctx, w, n_steps, cg.MODE_PNET, dev)
+            h_pn, n_pn, peak_pn = ic_spectrum(torch, k_pn, 2.5)
+            runs.append({"scattered_photons": n_pn, "peak_eps": peak_pn,
+                         "spectrum_L1_vs_plain": float((h_pn - h_pl).abs().sum()),
+                         "fallbacks": st_pn["mlp_fallbacks"]})
+        entry["pnet_tl_stage_3"] = {"training_runs": runs,
+                                    "median_spectrum_L1_vs_plain":
+                                        float(np.median([r_["spectrum_L1_vs_plain"] for r_ in runs]))}
         results[f"p_e={p_e:g}"] = entry
     cg.compton_destroy(ctx)
     if rank == 0:
@@ -1184,10 +1202,12 @@ def run_ic(args, rank: int, world: int, local_rank: int):
                                    "gas at eps = 2.5, 512 cells x 128 per species, density 1, dt 0.05; value = "
                                    "pairs/s of the plain runs including host launch overheads"},
             "inverse_compton": results, "head_on_sweep": sweep, "transfer_learning": tl_info, "train_s": t_train,
-            "transfer_learning_pnet": pnet_info, "train_pnet_s": t_pnet, "held_out_waterbag_p0_100": held_out,
+            "transfer_learning_pnet": pnet_info, "train_pnet_s_per_run": t_pnet,
+            "held_out_waterbag_p0_100": held_out,
             "note": "spectra: normalised 70-bin log10(eps) histograms of the photons that scattered at least "
                     "once, after the run; tl_stage_k = the surrogate after k transfer-learning stages (BF16); "
-                    "pnet_tl_stage_3 = the paper's 9-12-9 network after the three stages (FP32)",
+                    "pnet_tl_stage_3 = the paper's 9-12-9 network after the three stages (FP32), three training "
+                    "runs; the sweep and held-out figures of the paper's network are those of the first run",
         }
         print(json.dumps(line), flush=True)
 

@@ -115,7 +115,7 @@ def _random_workload(seed, n_cells, ppc_e, ppc_g, spread=0.5, gamma_max=100.0, e
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
 def test_random_ragged(seed):
-    # several scatter tiles (1024 pairs) and sort tiles (4096 particles), ragged tails
+    # several scatter tiles (1024 pairs) and sort tiles (512 particles), ragged tails
     w = _random_workload(seed, n_cells=257 + 37 * seed, ppc_e=40 + 7 * seed, ppc_g=33)
     compare_with_oracle(w, step=seed)
 
@@ -315,7 +315,8 @@ def test_filtered_equals_full_evaluation(case):
 
 @pytest.mark.parametrize("presorted", [False, True])
 def test_tiles_above_shared_memory_in_chunks(presorted):
-    # cells of ~700 particles: most sort tiles hold more than shared memory
-    # does, so their cells are sorted in runs that fit, block-wide
+    # cells of ~700 particles (spread 0.3): sort tiles above shared memory,
+    # sorted in runs of whole cells that fit, and cells above it alone, ranked
+    # in global memory
     w = _random_workload(19, 40, 700, 650, spread=0.3)
     compare_with_oracle(_presorted(w) if presorted else w, step=4)
