@@ -320,3 +320,13 @@ def test_tiles_above_shared_memory_in_chunks(presorted):
     # in global memory
     w = _random_workload(19, 40, 700, 650, spread=0.3)
     compare_with_oracle(_presorted(w) if presorted else w, step=4)
+
+
+def test_sparse_cells_beyond_the_staged_window():
+    # about one particle of each species per cell, many cells empty: each
+    # tile of 1024 pairs spans about 2000 cells, more than the probability
+    # kernel stages in shared memory (512), so its cell records are read
+    # from global memory
+    w = _random_workload(21, n_cells=12000, ppc_e=1, ppc_g=1, spread=0.8)
+    g, o, _ = compare_with_oracle(w, step=3)
+    assert o["n_pairs"] > 2048
