@@ -58,19 +58,12 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&v);
 }
-__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d)
 {
     const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
     const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
     return (uint32_t)lo | ((uint32_t)hi << 16);
-}
-__device__ __forceinline__ float e4m3_round(float x)
-{
-    const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
-    const __half_raw h = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
-    return __half2float(__half(h));
 }
 
 // ---------------------------------------------------------------------------
