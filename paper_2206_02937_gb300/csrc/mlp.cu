@@ -34,17 +34,18 @@ namespace compton {
 
 namespace {
 
-constexpr int kMlpThreads = 128;
+constexpr int kMlpGroups = 2;  // row groups (warpgroups) per CTA: one 128-row tile each, shared weights
+constexpr int kMlpThreads = 128 * kMlpGroups;
 constexpr int kTileM = 128;
 // shared-memory layout of the tensor-core kernels (base aligned to 1024 B)
 constexpr uint32_t kOffW = 0;                           // 4 weight tiles
 constexpr uint32_t kWTileBytes = 8192;                  // 64 rows x 128 B
-constexpr uint32_t kOffA = kOffW + 4 * kWTileBytes;     // A tile (128 x 128 B): features, then activations
-constexpr uint32_t kOffBias = kOffA + 16384;            // 4 x 64 floats
+constexpr uint32_t kOffA = kOffW + 4 * kWTileBytes;     // A tiles (128 x 128 B each, one per group)
+constexpr uint32_t kOffBias = kOffA + 16384 * kMlpGroups;  // 4 x 64 floats
 constexpr uint32_t kOffW4 = kOffBias + 1024;            // 64 floats
 constexpr uint32_t kOffScale = kOffW4 + 256;            // 8 floats
-constexpr uint32_t kOffBar = kOffScale + 32;            // mbarrier
-constexpr uint32_t kOffSlot = kOffBar + 8;              // TMEM address
+constexpr uint32_t kOffBar = kOffScale + 32;            // one mbarrier per group
+constexpr uint32_t kOffSlot = kOffBar + 8 * kMlpGroups;  // TMEM address
 constexpr uint32_t kSmemTc = kOffSlot + 8 + 1024;       // + alignment slack
 
 constexpr uint64_t kWaitNs = 2000000000ull;             // 2 s bound on every wait
@@ -245,25 +246,44 @@ __device__ __forceinline__ void load_pair_features(const MlpArgs& a, int64_t row
     features(a.m, q[0], q[1], q[2], q[3], q[4], q[5], f);
 }
 
+// Barrier of the 128 threads of row group g (named barrier 1 + g), and the
+// same with an OR over their flags.
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
+__device__ __forceinline__ bool group_sync_or(int g, bool flag)
+{
+    uint32_t out;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(out)
+        : "r"((uint32_t)flag), "r"(1 + g)
+        : "memory");
+    return out != 0;
+}
+
 template <bool kFp8>
-__global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
+__global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_tc(MlpArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* Wt = sm + kOffW;
-    uint8_t* Ah = sm + kOffA;
+    const int tid = threadIdx.x;
+    const int g = tid >> 7;     // row group: its own tile, A buffer, TMEM columns and mbarrier
+    const int lt = tid & 127;   // row within the group's tile
+    uint8_t* Ah = sm + kOffA + g * 16384;
     float* bias = reinterpret_cast<float*>(sm + kOffBias);
     float* w4 = reinterpret_cast<float*>(sm + kOffW4);
     float* scale = reinterpret_cast<float*>(sm + kOffScale);  // [0..3] w scales, [4..7] 1/activation scales
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kOffBar);
+    uint64_t* bar0 = reinterpret_cast<uint64_t*>(sm + kOffBar);
+    uint64_t* bar = bar0 + g;
     uint32_t* slot = reinterpret_cast<uint32_t*>(sm + kOffSlot);
 
-    const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const MlpDev& m = a.m;
     const uint4* wsrc = reinterpret_cast<const uint4*>(kFp8 ? m.wfp8 : m.wbf16);
     for (int i = tid; i < (int)(4 * kWTileBytes / 16); i += kMlpThreads) reinterpret_cast<uint4*>(Wt)[i] = wsrc[i];
-    for (int i = tid; i < 16384 / 16; i += kMlpThreads) reinterpret_cast<uint4*>(Ah)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < kMlpGroups * 16384 / 16; i += kMlpThreads)
+        reinterpret_cast<uint4*>(sm + kOffA)[i] = make_uint4(0, 0, 0, 0);
     for (int i = tid; i < 256; i += kMlpThreads) bias[i] = m.bias[i];
     if (tid < 64) w4[tid] = m.w4[tid];
     if (tid < 4) {
@@ -272,19 +292,20 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
     }
     const float b4 = m.b4[0];
     if (tid == 0) {
-        tc::mbar_init(bar, 1);
+        for (int q = 0; q < kMlpGroups; ++q) tc::mbar_init(bar0 + q, 1);
         tc::fence_barrier_init();
     }
     if (warp == 0) {
-        tc::tmem_alloc(slot, 64);
+        tc::tmem_alloc(slot, 64 * kMlpGroups);
         tc::tmem_relinquish();
     }
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = *slot;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t tmem = *slot + 64u * (uint32_t)g;  // the group's 64 columns
+    // a warp reads the TMEM lanes of its quarter of the warpgroup
+    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     constexpr uint32_t idesc = kFp8 ? tc::make_idesc(0, 0, 128, 64) : tc::make_idesc(1, 1, 128, 64);
     const uint32_t sW = tc::smem_u32(Wt), sA = tc::smem_u32(Ah);
     uint32_t phase = 0;
@@ -293,34 +314,36 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
     const int64_t n_tiles = (n_rows + kTileM - 1) / kTileM;
 
     // the next tile's momenta are loaded while the current tile runs its layers
+    const int64_t tile0 = (int64_t)blockIdx.x * kMlpGroups + g;
+    const int64_t tstride = (int64_t)gridDim.x * kMlpGroups;
     float raw[6];
-    load_pair_raw(a, (int64_t)blockIdx.x * kTileM + tid, n_rows, raw);
-    for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
-        const int64_t row = tile * kTileM + tid;
+    load_pair_raw(a, tile0 * kTileM + lt, n_rows, raw);
+    for (int64_t tile = tile0; tile < n_tiles && !failed; tile += tstride) {
+        const int64_t row = tile * kTileM + lt;
         float f[6] = {0, 0, 0, 0, 0, 0};
         const float cur[6] = {raw[0], raw[1], raw[2], raw[3], raw[4], raw[5]};
         if (row < n_rows) features(m, cur[0], cur[1], cur[2], cur[3], cur[4], cur[5], f);
-        if (tile + gridDim.x < n_tiles) load_pair_raw(a, (tile + gridDim.x) * kTileM + tid, n_rows, raw);
+        if (tile + tstride < n_tiles) load_pair_raw(a, (tile + tstride) * kTileM + lt, n_rows, raw);
         // layer-0 input: the 6 features in chunk 0 of the row, chunk 1 zeroed
         // (the single K step of layer 0 reads bytes 0..31 of the row)
         if (kFp8) {
             const float s = scale[4];
-            *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(tid, 0)) =
+            *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(lt, 0)) =
                 make_uint4(pack_e4m3x4(f[0] * s, f[1] * s, f[2] * s, f[3] * s), pack_e4m3x4(f[4] * s, f[5] * s, 0, 0),
                            0u, 0u);
         } else {
-            *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(tid, 0)) =
+            *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(lt, 0)) =
                 make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]), 0u);
         }
-        *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(tid, 1)) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(lt, 1)) = make_uint4(0u, 0u, 0u, 0u);
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
-        __syncthreads();
+        group_sync(g);
         tc::fence_after_sync();
 
         float acc_out = 0.0f;
         for (int l = 0; l < 4; ++l) {
-            if (tid == 0) {
+            if (lt == 0) {
                 const uint64_t ad = tc::sw128_kmajor_desc(sA);
                 const uint64_t bd = tc::sw128_kmajor_desc(sW + l * kWTileBytes);
                 // K steps of 32 bytes that hold data: layer 0 one (6 features),
@@ -364,12 +387,12 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
                                     pack_e4m3x4(v[16 * q + 4], v[16 * q + 5], v[16 * q + 6], v[16 * q + 7]),
                                     pack_e4m3x4(v[16 * q + 8], v[16 * q + 9], v[16 * q + 10], v[16 * q + 11]),
                                     pack_e4m3x4(v[16 * q + 12], v[16 * q + 13], v[16 * q + 14], v[16 * q + 15]));
-                                *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(tid, 2 * h + q)) = val;
+                                *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(lt, 2 * h + q)) = val;
                             }
                         } else {
 #pragma unroll
                             for (int q = 0; q < 4; ++q)
-                                *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(tid, 4 * h + q)) =
+                                *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(lt, 4 * h + q)) =
                                     make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
                         }
                     } else {
@@ -383,7 +406,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
             }
             if (l < 3) tc::fence_proxy_async_smem();
             tc::fence_before_sync();
-            const int bad = __syncthreads_or(ok ? 0 : 1);
+            const bool bad = group_sync_or(g, !ok);
             tc::fence_after_sync();
             if (bad) {
                 failed = true;
@@ -393,11 +416,11 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_tc(MlpArgs a)
         if (a.decide) decide_row(a, row, !failed && row < n_rows, acc_out + b4, cur);
         else if (!failed && row < n_rows) a.r_out[row] = __fdividef(1.0f, 1.0f + __expf(-(acc_out + b4)));
     }
-    if (failed && tid == 0) atomicOr(&a.stats->error_flags, (unsigned long long)kErrTimeout);
+    if (failed && lt == 0) atomicOr(&a.stats->error_flags, (unsigned long long)kErrTimeout);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, 64);
+    if (warp == 0) tc::tmem_dealloc(*slot, 64 * kMlpGroups);
 }
 
 // ---------------------------------------------------------------------------
@@ -569,7 +592,7 @@ compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* 
     const bool fp8 = mode == COMPTON_MODE_MLP_FP8;
     const void* kern = fp8 ? (const void*)k_mlp_tc<true> : (const void*)k_mlp_tc<false>;
     COMPTON_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTc));
-    const int grid = grid_persistent(kern, kMlpThreads, (int)kSmemTc, n, kTileM);
+    const int grid = grid_persistent(kern, kMlpThreads, (int)kSmemTc, n, kTileM * kMlpGroups);
     {
         TimedScope ts_(ctx, COMPTON_K_MLP, stream);
         if (fp8) k_mlp_tc<true><<<grid, kMlpThreads, kSmemTc, stream>>>(a);
