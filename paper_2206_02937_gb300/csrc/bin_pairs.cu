@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(256) k_scan_final(ScanFinalArgs a)
         }
         write_sort_tiles(a.stile_e, a.nb_e, p.e, ne[j], c);
         write_sort_tiles(a.stile_g, a.nb_g, p.g, ng[j], c);
-        a.count_e[c] = 0;  // becomes the insertion cursor of k_key_scatter
+        a.count_e[c] = 0;  // becomes the insertion cursor of k_place
         a.count_g[c] = 0;
         if (c == a.C - 1) {
             a.off_e[a.C] = (int32_t)(p.e + ne[j]);

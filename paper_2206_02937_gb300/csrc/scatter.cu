@@ -232,6 +232,8 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
         const uint32_t words[4] = {rnd4.r0, rnd4.r1, rnd4.r2, rnd4.r3};
         const CellInfo* cw = nw <= kCellWindow ? win[buf] : a.cinfo + cf;
         int ci = (kBinned && pb < total) ? find_cell(cw, nw, pb) : 0;
+        int ci_bound = -1;  // the cell whose candidate bound `bound` holds
+        float bound = 0.0f;
         int nq = 0;
 #pragma unroll
         for (int r = 0; r < kPairsPerThread; ++r) {
@@ -247,15 +249,22 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
                     ie = c.e_start + j;
                     ig = c.g_start + j;
                     dens = pair_density<kWeighted>(a, c.dens, ie, ig);
+                    // equal weights: one bound per cell, recomputed only when
+                    // this thread's pairs reach the next cell
+                    if (kWeighted || ci != ci_bound) {
+                        ci_bound = ci;
+                        bound = one_minus_exp_neg(2.0002f * dens * a.dt);
+                    }
                 } else {
                     ie = (int)p;
                     ig = (int)p;
                     dens = a.n_dens[p];
+                    bound = one_minus_exp_neg(2.0002f * dens * a.dt);
                 }
                 ++n_pairs;
             }
             const float u0 = u24_closed0(words[r]);
-            const bool is_cand = valid && (all || u0 < one_minus_exp_neg(2.0002f * dens * a.dt));
+            const bool is_cand = valid && (all || u0 < bound);
             if (valid && !is_cand && a.flag_out) a.flag_out[p] = 0;
             const unsigned m = __ballot_sync(0xffffffffu, is_cand);
             if (is_cand) cand[w][nq + __popc(m & ((1u << lane) - 1u))] = Cand{ie, ig, dens, u0, (uint32_t)p};
