@@ -696,7 +696,7 @@ __device__ void sort_giant_cell(const SortGatherArgs& g, int s, const SortSrc& t
 
 constexpr size_t kSortSmem = (size_t)kSortCap * (4 + 4 * kBucketsPerSlot + 4 + 12 + 2 + 2 + 2);
 
-__global__ void __launch_bounds__(kSortThreads, 9) k_sort_gather(SortGatherArgs g)
+__global__ void __launch_bounds__(kSortThreads, 10) k_sort_gather(SortGatherArgs g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem m;

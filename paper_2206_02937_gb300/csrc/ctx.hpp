@@ -14,7 +14,7 @@ namespace compton {
 // Tiling constants shared by the binning and scattering kernels.
 constexpr int kScanTile = 2048;       // cells per scan tile (256 threads x 8)
 constexpr int kSortTile = 512;        // particles per sort tile (by cell start offsets)
-constexpr int kSortCap = 768;         // particles a sort CTA holds in shared memory
+constexpr int kSortCap = 640;         // particles a sort CTA holds in shared memory
 constexpr int kPairsPerTile = 1024;   // pairs per scatter CTA (256 threads x 4)
 constexpr int kCellWindow = 512;      // cells of a scatter tile staged in shared memory
 
