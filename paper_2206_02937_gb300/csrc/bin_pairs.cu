@@ -12,8 +12,8 @@
 //                  (key, id, momentum) record placed in its cell's segment
 //                  (arbitrary order inside the segment)
 //   k_sort_gather  per-cell sort by (key, id) in shared memory (a bucket
-//                  sort of each tile of whole cells), then a coalesced write
-//                  of the particle arrays in sorted order
+//                  sort of each tile of whole cells), each particle written
+//                  to its sorted position
 // The order within a cell depends only on (key, id): the atomics of k_place
 // decide where a record lands inside its segment, and the sort removes that
 // freedom.
@@ -406,9 +406,10 @@ __global__ void k_place(PlaceArgs a)
 // counting sort over all buckets of the tile sorts every cell at once: a
 // histogram in shared memory, one block-wide exclusive scan (its value at the
 // start of a cell's buckets is a_c), placement by bucket, and an exact rank
-// by (key, id) inside each bucket.  The sorted tile leaves through an inverse
-// permutation, so the global writes are coalesced.  O(1) work per particle,
-// every lane busy whatever the cell sizes.
+// by (key, id) inside each bucket, after which each element is written to its
+// sorted position (entries of neighbouring threads lie in neighbouring
+// buckets, so a warp's writes stay within a few sectors).  O(1) work per
+// particle, every lane busy whatever the cell sizes.
 // ---------------------------------------------------------------------------
 struct SortGatherArgs {
     const float* in_u[2][3];
@@ -458,7 +459,6 @@ struct SortSmem {
                       // histogram, the keys in bucket order
     uint16_t* ptmp;   // [cap] tile slots grouped by bucket
     uint16_t* pbk;    // [cap] their buckets
-    uint16_t* perm;   // [cap] sorted position -> tile slot
     float* us[3];     // [cap] momenta staged from global memory
 };
 
@@ -612,6 +612,7 @@ __device__ __forceinline__ void sort_tile_block(const SortGatherArgs& g, int s, 
             pkey[pos] = key[k];
         }
     }
+    cp_async_wait_all();
     __syncthreads();
     // exact rank inside each bucket, one thread per entry of the grouped list
     // (the end of bucket b - 1 is the start of bucket b, also across cells):
@@ -644,14 +645,9 @@ __device__ __forceinline__ void sort_tile_block(const SortGatherArgs& g, int s, 
                 }
             }
         }
-        m.perm[fin] = (uint16_t)i;
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    // coalesced write of the sorted tile
-    for (int q = tid; q < R; q += kSortThreads) {
-        const int i = m.perm[q];
-        const int64_t go = o0 + q;
+        // the element goes straight to its sorted position: neighbouring
+        // threads hold neighbouring buckets, so the writes stay close
+        const int64_t go = o0 + fin;
         g.out_u[s][0][go] = m.us[0][i];
         g.out_u[s][1][go] = m.us[1][i];
         g.out_u[s][2][go] = m.us[2][i];
@@ -694,7 +690,7 @@ __device__ void sort_giant_cell(const SortGatherArgs& g, int s, const SortSrc& t
     __syncthreads();
 }
 
-constexpr size_t kSortSmem = (size_t)kSortCap * (4 + 4 * kBucketsPerSlot + 4 + 12 + 2 + 2 + 2);
+constexpr size_t kSortSmem = (size_t)kSortCap * (4 + 4 * kBucketsPerSlot + 4 + 12 + 2 + 2);
 
 __global__ void __launch_bounds__(kSortThreads, 10) k_sort_gather(SortGatherArgs g)
 {
@@ -707,8 +703,7 @@ __global__ void __launch_bounds__(kSortThreads, 10) k_sort_gather(SortGatherArgs
     m.us[1] = m.us[0] + kSortCap;
     m.us[2] = m.us[1] + kSortCap;
     m.ptmp = reinterpret_cast<uint16_t*>(m.us[2] + kSortCap);
-    m.perm = m.ptmp + kSortCap;
-    m.pbk = m.perm + kSortCap;
+    m.pbk = m.ptmp + kSortCap;
 
     const int s = (int64_t)blockIdx.x < g.nb_e ? 0 : 1;
     const int64_t b = s == 0 ? blockIdx.x : blockIdx.x - g.nb_e;
