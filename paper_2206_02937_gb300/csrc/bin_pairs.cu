@@ -628,10 +628,23 @@ __device__ __forceinline__ void sort_tile_block(const SortGatherArgs& g, int s, 
         if (hi - lo > 1) {
             const uint32_t ki = pkey[q];
             int less = 0, eq = 0;
-            for (int r = lo; r < hi; ++r) {
-                const uint32_t kr = pkey[r];
-                less += kr < ki;
-                eq += kr == ki;
+            if (hi - lo <= 4) {
+                // buckets hold Poisson(1) keys: up to four, a fixed unrolled
+                // pass (no loop control, the same instructions in every lane)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    if (lo + r < hi) {
+                        const uint32_t kr = pkey[lo + r];
+                        less += kr < ki;
+                        eq += kr == ki;
+                    }
+                }
+            } else {
+                for (int r = lo; r < hi; ++r) {
+                    const uint32_t kr = pkey[r];
+                    less += kr < ki;
+                    eq += kr == ki;
+                }
             }
             if (eq == 1) {
                 fin = lo + less;
