@@ -826,9 +826,36 @@ def run_e2e(args, cg, torch, ctx, w, stream, dev):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
     pairs = cg.compton_get_stats(ctx, reset=True)["pairs_tested"]
+
+    # the host link's own bound: the same copies of every step, both
+    # directions at once, without the kernels
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    c0.record(stream)
+    up.wait_stream(stream)
+    down.wait_stream(stream)
+    for i in range(n_steps):
+        b = i % 2
+        with torch.cuda.stream(up):
+            for s, h in zip(dev_in[b], host_in):
+                for t, src in zip((s.ux, s.uy, s.uz, s.cell, s.id), h):
+                    t.copy_(src, non_blocking=True)
+        with torch.cuda.stream(down):
+            for s, h in zip(dev_out[b], host_out[b]):
+                for t, dst in zip((s.ux, s.uy, s.uz), h):
+                    dst.copy_(t, non_blocking=True)
+    stream.wait_stream(up)
+    stream.wait_stream(down)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    copy_ms = c0.elapsed_time(c1) / n_steps
     return {"value": pairs / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "steps": n_steps, "ms_per_step": ms / n_steps,
-            "note": "uploads, kernels and downloads of consecutive steps overlap on three streams"}
+            "copies_only_ms_per_step": copy_ms, "link_GBps": (h2d + d2h) / (copy_ms * 1e6),
+            "link_bound_frac": copy_ms / (ms / n_steps),
+            "note": "uploads, kernels and downloads of consecutive steps overlap on three streams; "
+                    "copies_only_ms_per_step times the same copies without the kernels"}
 
 
 # ---------------------------------------------------------------------------

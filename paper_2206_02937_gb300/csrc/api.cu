@@ -96,14 +96,16 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     ctx->max_pair_tiles = (P + compton::kPairsPerTile - 1) / compton::kPairsPerTile + 1;
 
     Carver cv;
-    size_t o_count[2], o_off[2], o_rec[2], o_stile[2];
+    // both histograms and the two order flags in one block, cleared by one
+    // memset per binning call; the second histogram starts 256-byte aligned
+    const size_t C_pad = align_up((size_t)C, 64);
+    const size_t o_count = cv.take<int32_t>(2 * C_pad + 2);
+    size_t o_off[2], o_rec[2], o_stile[2];
     for (int s = 0; s < 2; ++s) {
-        o_count[s] = cv.take<int32_t>(C);
         o_off[s] = cv.take<int32_t>(C + 1);
         o_rec[s] = cv.take<compton::SortRec>(P > 0 ? P : 1);
         o_stile[s] = cv.take<int32_t>(ctx->max_sort_tiles + 1);
     }
-    size_t o_uns = cv.take<int32_t>(2);
     size_t o_bs = cv.take<int64_t>(3 * ctx->max_scan_tiles);
     size_t o_ci = cv.take<CellInfo>(C);
     size_t o_tc = cv.take<int32_t>(ctx->max_pair_tiles + 1);
@@ -142,12 +144,12 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     ctx->arena_bytes = total;
     char* base = static_cast<char*>(ctx->arena);
     for (int s = 0; s < 2; ++s) {
-        ctx->count[s] = reinterpret_cast<int32_t*>(base + o_count[s]);
+        ctx->count[s] = reinterpret_cast<int32_t*>(base + o_count) + s * C_pad;
         ctx->off[s] = reinterpret_cast<int32_t*>(base + o_off[s]);
         ctx->rec[s] = reinterpret_cast<compton::SortRec*>(base + o_rec[s]);
         ctx->stile[s] = reinterpret_cast<int32_t*>(base + o_stile[s]);
     }
-    ctx->unsorted = reinterpret_cast<int32_t*>(base + o_uns);
+    ctx->unsorted = reinterpret_cast<int32_t*>(base + o_count) + 2 * C_pad;
     ctx->block_sums = reinterpret_cast<int64_t*>(base + o_bs);
     ctx->cinfo = reinterpret_cast<CellInfo*>(base + o_ci);
     ctx->tile_cell = reinterpret_cast<int32_t*>(base + o_tc);

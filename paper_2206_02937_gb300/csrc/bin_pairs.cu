@@ -778,9 +778,9 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
     const int64_t C = ctx->cfg.n_cells;
     const int64_t ne = e_in->n, ng = g_in->n;
     const int64_t n_tiles = (C + kScanTile - 1) / kScanTile;
-    COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->count[0], 0, sizeof(int32_t) * C, stream));
-    COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->count[1], 0, sizeof(int32_t) * C, stream));
-    COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->unsorted, 0, 2 * sizeof(int32_t), stream));
+    // count[0], count[1] and unsorted lie in one block of the workspace
+    COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->count[0], 0, sizeof(int32_t) * (ctx->unsorted + 2 - ctx->count[0]),
+                                          stream));
 
     const int64_t nmax = ne > ng ? ne : ng;
     const dim3 cgrid(grid_for((nmax + 3) / 4, 256, 152 * 16), 2);  // four particles per thread
