@@ -398,6 +398,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if not args.no_mlp:
         mlp = run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step, peaks)
         step += args.warmup + args.steps + 2
+        # the surrogate step's rate over the plain step's on the same pairs
+        # (below 1: the network step is slower)
+        mlp["gain_vs_plain"] = (total_ms / args.steps) / mlp["ms_per_step"]
 
     serving = None
     if not args.no_serving and rank == 0:
