@@ -22,8 +22,9 @@
  *
  * Parity status: every function here is pinned by the CPU tests (closed
  * forms, high-precision evaluation, quadrature, conservation, brute force,
- * chi-square).  Philox is pinned by statistics on the CPU and by agreement
- * with an independent CUDA implementation on the GPU.
+ * chi-square).  Philox4x32-10 is pinned by the generator's published
+ * known-answer vectors (Salmon et al., SC'11) and by statistics on the CPU,
+ * and on a GPU by agreement with cuRAND's device Philox4_32_10.
  *
  * Everything is FP64, single-threaded, in the order the method states it.
  */

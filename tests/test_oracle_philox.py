@@ -1,16 +1,43 @@
-"""Statistical pins of the oracle's Philox4x32-10 (Salmon et al., SC'11).
+"""Pins of the oracle's Philox4x32-10 (Salmon et al., SC'11).
 
-The published known-answer vectors are not available here, so the CPU pins
-are the generator's defining properties: uniform output words, full
-avalanche of every counter and key bit (a bijective mixing of 10 rounds), and
-independence of the four output words.  Bit-exact agreement with an
-independent implementation is checked on the GPU (cuRAND's device Philox, run
-as a library) in tests/test_gpu_philox.py.
+The block function is pinned to the generator's published known-answer
+vectors (tests/golden/philox4x32_10_kat.txt): a wrong round permutation,
+swapped high and low product halves, a missing key bump or a wrong multiplier
+changes every one of them.  The statistics tests below check the properties
+the method relies on: uniform output words, full avalanche of every counter
+and key bit, and independence of the four output words.  On a GPU,
+tests/test_gpu_philox.py compares the same vectors and a sweep of counters
+with cuRAND's device Philox4_32_10, run as a library.
 """
+import os
+
 import numpy as np
 import pytest
 
 import oracle
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
+
+
+def kat_vectors():
+    rows = []
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            w = [int(t, 16) for t in line.split()]
+            assert len(w) == 10
+            rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+def test_known_answer_vectors():
+    rows = kat_vectors()
+    assert len(rows) == 3
+    for ctr, key, want in rows:
+        got = [int(x) for x in oracle.philox4x32_10(ctr, key)]
+        assert got == want, f"ctr={ctr} key={key}: {[hex(x) for x in got]} != {[hex(x) for x in want]}"
 
 
 def _batch(ctrs, key):
