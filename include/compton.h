@@ -301,6 +301,18 @@ compton_status compton_mlp_train_step(struct compton_ctx* ctx, const float* ux_d
                                       const float* kz_dev, const float* y_dev, const float* w_dev, int64_t n,
                                       float lr, float* loss_out_host, compton_stream_t stream);
 
+/* Arithmetic of the following compton_mlp_train_step calls (Sec. 3.2
+ * trains the network; the precision is this library's choice).
+ * COMPTON_MODE_MLP_FP32 (the default): forward and backward in FP32 on the
+ * CUDA cores, one sample per thread.  COMPTON_MODE_MLP_BF16: every
+ * contraction (forward z = a W^T, backward delta W and the weight gradients
+ * delta^T a) on the tcgen05 tensor cores with BF16 operands and FP32
+ * accumulation in tensor memory, 128-sample tiles, one CTA per SM holding all
+ * 512 TMEM columns; pre-activations, bias and output-layer gradients, the
+ * loss and Adam stay in FP32.  Both compute the same gradient (the loss
+ * normalised by sum w) to within BF16 rounding.  EINVAL for another mode. */
+compton_status compton_mlp_set_train_precision(struct compton_ctx* ctx, compton_mode mode);
+
 /* Data-balancing weights (Sec. 3.2: events of every probability range
  * should appear about equally often in training).  Sample i falls in bin
  * b = number of edges_host[1 .. n_bins-1] that are <= r_dev[i] (values beyond
@@ -460,16 +472,24 @@ compton_status compton_serve_info(struct compton_ctx* ctx, uint64_t* bytes_in_us
  * paper has no counterpart: this serves callers that cannot allocate device
  * memory when they need the offsets, such as a particle-in-cell code whose
  * memory manager owns all device memory, or a time-step loop that must not
- * allocate).  off_out_dev[c] = number of particles with a cell index below c
- * (indices outside [0, n_cells) are not counted), off_out_dev[n_cells] = the
- * number counted; the same values as compton_pairs.off_*_dev of
- * compton_bin_pairs.  Needs no context.  The counts live in a library-owned
- * static device array of 2^20 int32 (4 MiB, held on every GPU that loads the
- * library until exit): n_cells above 1048576 is rejected with ERANGE.  The
- * first call on a device looks up that array's device address, so make it
- * before any stream capture.  Every call reuses the array and clears it
- * first; calls whose work overlaps on the GPU race on it and must be ordered
- * by the caller.  Asynchronous on `stream`. */
+ * allocate).  cell_dev: n int32 cell indices (device); off_out_dev: n_cells
+ * + 1 int32 (device, caller-owned).  off_out_dev[c] = number of particles
+ * with a cell index below c; off_out_dev[n_cells] = the number counted.
+ * Indices outside [0, n_cells) are skipped without an error (unlike
+ * compton_bin_pairs, which reports them through compton_check): the caller
+ * sees how many were skipped as n - off_out_dev[n_cells].  For in-range input
+ * these are the values of compton_pairs.off_*_dev of compton_bin_pairs.
+ * Needs no context.  The counts live in a library-owned static device array
+ * of 2^20 int32 plus 256 strip sums (about 4 MiB, held on every GPU that
+ * loads the library until exit): n_cells above 1048576 is rejected with
+ * ERANGE, n < 0 or above INT32_MAX with EINVAL.  The first call on a device
+ * looks up that array's device address (and the SM count), so make it before
+ * any stream capture; a cudaDeviceReset makes the kept address stale, so do
+ * not call this after a reset in the same process.  Every call reuses the
+ * array and clears it first; calls whose work overlaps on the GPU race on it
+ * and must be ordered by the caller.  An error pending from the caller's
+ * earlier work is cleared on entry and not reported as this call's; ECUDA
+ * means a launch of this call failed.  Asynchronous on `stream`. */
 compton_status compton_cell_offsets_noalloc(const int32_t* cell_dev, int64_t n, int64_t n_cells,
                                             int32_t* off_out_dev, compton_stream_t stream);
 
@@ -510,6 +530,18 @@ compton_status compton_kernel_times(struct compton_ctx* ctx, double* ms_out_host
  * counterpart; this exists so the failure path can be tested without a
  * fault. */
 compton_status compton_selftest_wait(struct compton_ctx* ctx, uint64_t timeout_ns, compton_stream_t stream);
+
+/* Host-side fault injection, for testing the error paths (the paper has no
+ * counterpart).  Process-wide: after this call the library's checks of CUDA
+ * calls let `skip` of them pass and then report `fail` failures, without
+ * making the failing call and without touching the device: the device
+ * allocation of compton_init and compton_serve_start then fails as if out of
+ * memory (ENOMEM), any other checked call or launch as a CUDA error (ECUDA,
+ * with compton_last_error naming the call).  fail = 0 disarms it.
+ * pending_out (nullable): failures still pending from the previous arming.
+ * The context stays usable after an injected failure: the next call of the
+ * same entry point starts from a clean state.  EINVAL for negative counts. */
+compton_status compton_debug_inject(int64_t skip, int64_t fail, int64_t* pending_out);
 
 /* The scattering-angle sampler of compton_scatter_step on its own, for
  * validation (the paper resolves each collision by sampling the scattered

@@ -369,7 +369,14 @@ SIGNATURES["compton_cell_offsets_noalloc"] = (c_i32, [c_p, c_i64, c_i64, c_p, c_
 
 def compton_cell_offsets_noalloc(cell, n_cells: int, off_out, stream=None) -> None:
     """Per-cell offsets of one species (cell: int32 CUDA tensor; off_out:
-    int32 CUDA tensor of n_cells + 1), with no device allocation."""
+    int32 CUDA tensor of at least n_cells + 1), with no device allocation."""
+    import torch
+    for name, t in (("cell", cell), ("off_out", off_out)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()):
+            raise ValueError(f"compton_cell_offsets_noalloc: {name} must be a contiguous int32 CUDA tensor")
+    if off_out.numel() < int(n_cells) + 1:
+        raise ValueError(f"compton_cell_offsets_noalloc: off_out holds {off_out.numel()} values, "
+                         f"n_cells + 1 = {int(n_cells) + 1} needed")
     _check(lib().compton_cell_offsets_noalloc(_ptr(cell), int(cell.shape[0]), int(n_cells), _ptr(off_out),
                                               _stream_ptr(stream)), "compton_cell_offsets_noalloc")
 
@@ -384,6 +391,15 @@ def compton_mlp_balance_weights(ctx: int, r, edges, w_out, stream=None) -> None:
     _check(lib().compton_mlp_balance_weights(c_p(ctx), _ptr(r), int(r.shape[0]), c_p(e.ctypes.data),
                                              int(e.shape[0] - 1), _ptr(w_out), _stream_ptr(stream)),
            "compton_mlp_balance_weights", ctx)
+
+
+SIGNATURES["compton_mlp_set_train_precision"] = (c_i32, [c_p, c_i32])
+
+
+def compton_mlp_set_train_precision(ctx: int, mode: int) -> None:
+    """Training arithmetic: MODE_MLP_FP32 (CUDA cores, the default) or
+    MODE_MLP_BF16 (tcgen05 tensor cores, BF16 operands, FP32 accumulation)."""
+    _check(lib().compton_mlp_set_train_precision(c_p(ctx), int(mode)), "compton_mlp_set_train_precision", ctx)
 
 
 SIGNATURES["compton_mlp_set_features"] = (c_i32, [c_p, c_i32])
@@ -467,6 +483,18 @@ def compton_kernel_times(ctx: int) -> dict:
     n = (ctypes.c_int64 * len(KERNEL_SLOTS))()
     _check(lib().compton_kernel_times(c_p(ctx), ms, n), "compton_kernel_times", ctx)
     return {name: {"ms": ms[i], "launches": n[i]} for i, name in enumerate(KERNEL_SLOTS)}
+
+
+SIGNATURES["compton_debug_inject"] = (c_i32, [c_i64, c_i64, c_p])
+
+
+def compton_debug_inject(skip: int, fail: int) -> int:
+    """Arm host-side fault injection: the next `skip` checked CUDA calls pass,
+    the `fail` after them report an error.  Returns the failures that were
+    still pending."""
+    pending = c_i64(0)
+    _check(lib().compton_debug_inject(int(skip), int(fail), ctypes.byref(pending)), "compton_debug_inject")
+    return int(pending.value)
 
 
 SIGNATURES["compton_selftest_wait"] = (c_i32, [c_p, c_u64, c_p])

@@ -5,6 +5,9 @@
 #include <cstdlib>
 #include <new>
 
+#include <atomic>
+#include <mutex>
+
 #include "ctx.hpp"
 
 using compton::CellInfo;
@@ -113,6 +116,8 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     ctx->accepted_cap = P > ((int64_t)1 << 20) ? P : ((int64_t)1 << 20);
     size_t o_acc = cv.take<compton::AcceptedPair>(ctx->accepted_cap);
     size_t o_nacc = cv.take<uint32_t>(1);
+    size_t o_wacc = cv.take<uint32_t>(compton::kMaxProbWarps);
+    size_t o_wcand = cv.take<uint32_t>(compton::kMaxProbWarps);
     size_t o_cand = cv.take<compton::CandPair>(ctx->accepted_cap);
     size_t o_ncand = cv.take<uint32_t>(1);
     size_t o_st = cv.take<compton::DeviceStats>(1);
@@ -135,7 +140,7 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
         delete ctx;
         return COMPTON_ENOMEM;
     }
-    e = cudaMalloc(&ctx->arena, total);
+    e = compton::inject_fault() ? cudaErrorMemoryAllocation : cudaMalloc(&ctx->arena, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
@@ -156,6 +161,8 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     ctx->n_pairs = reinterpret_cast<int64_t*>(base + o_np);
     ctx->accepted = reinterpret_cast<compton::AcceptedPair*>(base + o_acc);
     ctx->n_accepted = reinterpret_cast<uint32_t*>(base + o_nacc);
+    ctx->warp_acc = reinterpret_cast<uint32_t*>(base + o_wacc);
+    ctx->warp_cand = reinterpret_cast<uint32_t*>(base + o_wcand);
     ctx->cand = reinterpret_cast<compton::CandPair*>(base + o_cand);
     ctx->n_cand = reinterpret_cast<uint32_t*>(base + o_ncand);
     ctx->stats = reinterpret_cast<compton::DeviceStats*>(base + o_st);
@@ -466,6 +473,14 @@ compton_status compton_mlp_train_step(compton_ctx* ctx, const float* ux, const f
     return COMPTON_OK;
 }
 
+compton_status compton_mlp_set_train_precision(compton_ctx* ctx, compton_mode mode)
+{
+    if (!ctx) return COMPTON_EINVAL;
+    if (mode != COMPTON_MODE_MLP_FP32 && mode != COMPTON_MODE_MLP_BF16) return COMPTON_EINVAL;
+    ctx->train_tc = mode == COMPTON_MODE_MLP_BF16;
+    return COMPTON_OK;
+}
+
 compton_status compton_mlp_balance_weights(compton_ctx* ctx, const float* r, int64_t n, const float* edges,
                                            int32_t n_bins, float* w_out, compton_stream_t stream)
 {
@@ -723,3 +738,42 @@ compton_status compton_kn_sample_angle(compton_ctx* ctx, const float* x, const u
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Host-side fault injection (test support).
+// ---------------------------------------------------------------------------
+namespace compton {
+namespace {
+std::mutex g_inject_mu;
+std::atomic<int64_t> g_inject_fail{0};
+int64_t g_inject_skip = 0;
+}  // namespace
+
+bool inject_fault()
+{
+    if (g_inject_fail.load(std::memory_order_relaxed) <= 0) return false;
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    if (g_inject_fail.load(std::memory_order_relaxed) <= 0) return false;
+    if (g_inject_skip > 0) {
+        --g_inject_skip;
+        return false;
+    }
+    g_inject_fail.fetch_sub(1, std::memory_order_relaxed);
+    return true;
+}
+
+void inject_arm(int64_t skip, int64_t fail)
+{
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    g_inject_skip = skip > 0 ? skip : 0;
+    g_inject_fail.store(fail > 0 ? fail : 0, std::memory_order_relaxed);
+}
+}  // namespace compton
+
+compton_status compton_debug_inject(int64_t skip, int64_t fail, int64_t* pending_out)
+{
+    if (skip < 0 || fail < 0) return COMPTON_EINVAL;
+    if (pending_out) *pending_out = compton::g_inject_fail.load();
+    compton::inject_arm(skip, fail);
+    return COMPTON_OK;
+}

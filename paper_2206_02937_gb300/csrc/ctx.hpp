@@ -17,6 +17,7 @@ constexpr int kSortTile = 512;        // particles per sort tile (by cell start 
 constexpr int kSortCap = 640;         // particles a sort CTA holds in shared memory
 constexpr int kPairsPerTile = 1024;   // pairs per scatter CTA (256 threads x 4)
 constexpr int kCellWindow = 512;      // cells of a scatter tile staged in shared memory
+constexpr int kMaxProbWarps = 8192;   // warps of the probability kernel (their accepted counts)
 
 // Per-cell record written by the scan and read by the scatter kernel.
 struct __align__(16) CellInfo {
@@ -166,6 +167,8 @@ struct compton_ctx {
     int64_t* n_pairs = nullptr;                  // device scalar
     compton::AcceptedPair* accepted = nullptr;   // [accepted_cap] pairs that passed their trial
     uint32_t* n_accepted = nullptr;              // device scalar
+    uint32_t* warp_acc = nullptr;                // [kMaxProbWarps] accepted pairs per probability region
+    uint32_t* warp_cand = nullptr;               // [kMaxProbWarps] candidates per probability region
     int64_t accepted_cap = 0;                    // max(max_particles, 2^20)
     compton::CandPair* cand = nullptr;           // [accepted_cap] candidates of the surrogate modes
     uint32_t* n_cand = nullptr;                  // device scalar
@@ -180,11 +183,26 @@ struct compton_ctx {
     compton::ServeEngine* serve = nullptr;  // continuous-batching engine (compton_serve_start)
     compton::KernelTiming* timing = nullptr;  // per-kernel event pairs (compton_kernel_timing)
     bool bin_weighted = false;                // the last binning carried per-particle weights
+    bool train_tc = false;                    // training contractions on the tensor cores (BF16)
     compton::PnetDev pnet{};                  // the paper's 9-12-9 network
     bool pnet_loaded = false;
 };
 
 namespace compton {
+
+// Host-side fault injection (compton_debug_inject, test support): while a
+// fault is pending, the CUDA checks of the library count down `skip` passes
+// and then report `fail` failures without making the failing call (an
+// allocation reports cudaErrorMemoryAllocation, any other call
+// cudaErrorLaunchFailure).  Nothing is done to the device.
+bool inject_fault();
+void inject_arm(int64_t skip, int64_t fail);
+
+inline compton_status set_injected_error(compton_ctx* ctx, const char* where)
+{
+    if (ctx) std::snprintf(ctx->last_error, sizeof(ctx->last_error), "%s: injected failure", where);
+    return COMPTON_ECUDA;
+}
 
 inline compton_status set_cuda_error(compton_ctx* ctx, cudaError_t e, const char* where)
 {
@@ -196,6 +214,7 @@ inline compton_status set_cuda_error(compton_ctx* ctx, cudaError_t e, const char
 
 #define COMPTON_CUDA_TRY(ctx, expr)                                  \
     do {                                                             \
+        if (compton::inject_fault()) return compton::set_injected_error((ctx), #expr); \
         cudaError_t _e = (expr);                                     \
         if (_e != cudaSuccess) return compton::set_cuda_error((ctx), _e, #expr); \
     } while (0)
@@ -204,6 +223,7 @@ inline compton_status set_cuda_error(compton_ctx* ctx, cudaError_t e, const char
 #define COMPTON_LAUNCH_CHECK(ctx, name)                              \
     do {                                                             \
         cudaError_t _e = cudaGetLastError();                         \
+        if (_e == cudaSuccess && compton::inject_fault()) return compton::set_injected_error((ctx), name); \
         if (_e != cudaSuccess) return compton::set_cuda_error((ctx), _e, name); \
     } while (0)
 
@@ -266,6 +286,9 @@ compton_status launch_balance_weights(compton_ctx* ctx, const float* r, int64_t 
 compton_status launch_mlp_train_step(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                      const float* kx, const float* ky, const float* kz, const float* y,
                                      const float* w, int64_t n, float lr, cudaStream_t stream);
+compton_status launch_mlp_grad_tc(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
+                                  const float* kx, const float* ky, const float* kz, const float* y, const float* w,
+                                  int64_t n, cudaStream_t stream);
 compton_status launch_mlp_calibrate(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                     const float* kx, const float* ky, const float* kz, int64_t n,
                                     cudaStream_t stream);

@@ -324,9 +324,10 @@ __device__ __forceinline__ Angle kn_sample_angle(float x, uint32_t r24, float F2
 }
 
 // ---------------------------------------------------------------------------
-// FP64 reciprocal and reciprocal square root from an FP32 seed and one
-// Newton-Raphson step (the error squares: ~1e-14 relative).  Arguments far
-// outside the FP32 range take the full-precision operator instead.
+// FP64 reciprocal, reciprocal square root and square root from an FP32 seed
+// and one Newton-Raphson step (the seed's error squares: within 5e-14
+// relative, checked against CUDA's correctly rounded operators).  Arguments
+// far outside the FP32 range take the full-precision operator instead.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double rcp_nr(double d)
 {
@@ -352,26 +353,62 @@ __device__ __forceinline__ double sqrt_nr(double d)
 }
 
 // ---------------------------------------------------------------------------
-// The same collision in FP32.  Its error relative to the pair's energy scale
-// gamma + eps grows with gamma eps (the rest-frame photon k' forms by
-// cancellation when a fast electron and its photon nearly co-move): measured
-// against the FP64 formulas over random and co-moving geometries it stays
-// below 2e-6 for gamma eps <= 8 and reaches ~1e-5 near gamma eps = 30.  The
-// scatter kernel therefore takes this path only below a configured gamma eps
-// and the FP64 one above it.
+// The same collision in FP32, in a form without cancellation.  With u = |u| u^
+// and beta = |u|/gamma, split every vector into its parts along u^ and across
+// it; the part across is taken from cross products (no subtraction), and the
+// part along from the identities
+//   boost to the rest frame:  k'_par = gamma eps (c_psi - beta),
+//   boost back:               k1_par = gamma eps1' (c + beta),
+// with c_psi = u^.k^ and c = u^.d (d the scattered rest-frame direction);
+// when the two terms of (c_psi - beta) or (c + beta) nearly cancel they are
+// formed as (1/gamma^2 - s_psi^2)/(c_psi + beta) and
+// (s^2 - 1/gamma^2)/(beta - c), s^2 = 1 - c^2 from the cross product, whose
+// denominators do not cancel.  So no step loses digits: the photon emitted
+// backward in the electron frame, whose lab energy is a small fraction of
+// gamma eps1', keeps FP32 relative accuracy, and both momenta match the FP64
+// formulas to a few times 1e-7 of their own magnitude (only u <- u + k - k1
+// can lose digits, when the electron ends far slower than it was).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void cross3(float a0, float a1, float a2, float b0, float b1, float b2, float& c0, float& c1,
+                                       float& c2)
+{
+    c0 = diff_of_products(a1, b2, a2, b1);
+    c1 = diff_of_products(a2, b0, a0, b2);
+    c2 = diff_of_products(a0, b1, a1, b0);
+}
+
 __device__ __forceinline__ void collide_f32(float& ux, float& uy, float& uz, float& kx, float& ky, float& kz,
                                             float x, Angle ang, float u2)
 {
     const float U0 = ux, U1 = uy, U2 = uz, K0 = kx, K1 = ky, K2 = kz;
-    const float gamma = sqrtf(1.0f + fmaf(U0, U0, fmaf(U1, U1, U2 * U2)));
-    const float eps = sqrtf(fmaf(K0, K0, fmaf(K1, K1, K2 * K2)));
-    const float uk = fmaf(U0, K0, fmaf(U1, K1, U2 * K2));
-    const float igp1 = __fdividef(1.0f, gamma + 1.0f);
-    const float f = fmaf(uk, igp1, -eps);
-    const float r0 = fmaf(U0, f, K0), r1 = fmaf(U1, f, K1), r2 = fmaf(U2, f, K2);
+    const float uu = fmaf(U0, U0, fmaf(U1, U1, U2 * U2));
+    const float kk = fmaf(K0, K0, fmaf(K1, K1, K2 * K2));
+    const float rg = rsqrtf(1.0f + uu);  // 1/gamma
+    const float gamma = (1.0f + uu) * rg;
+    const float ig2 = rg * rg;           // 1/gamma^2 = 1 - beta^2
+    const float rk = rsqrtf(kk);
+    const float eps = kk * rk;
+    const bool moving = uu > 0.0f;
+    const float ru = moving ? rsqrtf(uu) : 0.0f;
+    const float un = uu * ru;
+    const float beta = un * rg;
+    // unit vectors along u (any unit vector at rest) and along k
+    const float h0 = moving ? U0 * ru : 0.0f, h1 = moving ? U1 * ru : 0.0f, h2 = moving ? U2 * ru : 1.0f;
+    const float e0 = K0 * rk, e1 = K1 * rk, e2 = K2 * rk;
+    // incoming photon in the rest frame: across part eps (h x e) x h, along part gamma eps (c_psi - beta)
+    float c0, c1, c2;
+    cross3(h0, h1, h2, e0, e1, e2, c0, c1, c2);
+    const float sp2 = fmaf(c0, c0, fmaf(c1, c1, c2 * c2));
+    const float cp = fmaf(h0, e0, fmaf(h1, e1, h2 * e2));
+    const float cmb = cp > 0.0f ? __fdividef(ig2 - sp2, cp + beta) : cp - beta;
+    float p0, p1, p2;
+    cross3(c0, c1, c2, h0, h1, h2, p0, p1, p2);
+    const float along = gamma * cmb;
+    const float r0 = fmaf(along, h0, p0), r1 = fmaf(along, h1, p1), r2 = fmaf(along, h2, p2);
     const float inv = rsqrtf(fmaf(r0, r0, fmaf(r1, r1, r2 * r2)));
     const float n0 = r0 * inv, n1 = r1 * inv, n2 = r2 * inv;
+    // scattered direction: polar angle theta' from n, azimuth in the
+    // orthonormal basis of Duff et al. completing n
     const float sg = n2 >= 0.0f ? 1.0f : -1.0f;
     const float a = -__fdividef(1.0f, sg + n2);
     const float b = n0 * n1 * a;
@@ -383,9 +420,16 @@ __device__ __forceinline__ void collide_f32(float& ux, float& uy, float& uz, flo
     const float d0 = fmaf(ang.cth, n0, ang.sth * fmaf(cph, b10, sph * b20));
     const float d1 = fmaf(ang.cth, n1, ang.sth * fmaf(cph, b11, sph * b21));
     const float d2 = fmaf(ang.cth, n2, ang.sth * fmaf(cph, b12, sph * b22));
-    const float q0 = e1r * d0, q1 = e1r * d1, q2 = e1r * d2;
-    const float g = fmaf(fmaf(U0, q0, fmaf(U1, q1, U2 * q2)), igp1, e1r);
-    const float k10 = fmaf(U0, g, q0), k11 = fmaf(U1, g, q1), k12 = fmaf(U2, g, q2);
+    // back to the lab: across part eps1' (h x d) x h, along part gamma eps1' (c + beta)
+    float x0, x1, x2;
+    cross3(h0, h1, h2, d0, d1, d2, x0, x1, x2);
+    const float s2 = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
+    const float c = fmaf(h0, d0, fmaf(h1, d1, h2 * d2));
+    const float cpb = c < 0.0f ? __fdividef(s2 - ig2, beta - c) : c + beta;
+    float q0, q1, q2;
+    cross3(x0, x1, x2, h0, h1, h2, q0, q1, q2);
+    const float al = gamma * cpb;
+    const float k10 = e1r * fmaf(al, h0, q0), k11 = e1r * fmaf(al, h1, q1), k12 = e1r * fmaf(al, h2, q2);
     ux = (U0 + K0) - k10;
     uy = (U1 + K1) - k11;
     uz = (U2 + K2) - k12;
@@ -453,6 +497,18 @@ __device__ __forceinline__ void collide_f64(float& ux, float& uy, float& uz, flo
     kx = (float)k10;
     ky = (float)k11;
     kz = (float)k12;
+}
+
+// ---------------------------------------------------------------------------
+// The collision of one accepted pair: FP64 when gamma eps exceeds the
+// configured threshold (c64sq = its square), FP32 below it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void collide_pair(float& ux, float& uy, float& uz, float& kx, float& ky, float& kz,
+                                             float x, Angle ang, float u2, float c64sq)
+{
+    const float ge2 = fmaf(ux, ux, fmaf(uy, uy, fmaf(uz, uz, 1.0f))) * fmaf(kx, kx, fmaf(ky, ky, kz * kz));
+    if (ge2 > c64sq) collide_f64(ux, uy, uz, kx, ky, kz, x, ang, u2);
+    else collide_f32(ux, uy, uz, kx, ky, kz, x, ang, u2);
 }
 
 // ---------------------------------------------------------------------------

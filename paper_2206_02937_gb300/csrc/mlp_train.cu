@@ -19,6 +19,9 @@
 //   k_train_adam     Adam (Kingma and Ba 2014, Algorithm 1) on the FP32 master
 //                    parameters with the gradient divided by sum w, then the
 //                    inference images are rebuilt (k_mlp_pack).
+// With the tensor-core training precision selected (compton_mlp_set_train_
+// precision), the gradient comes from k_train_tc (mlp_train_tc.cu) instead of
+// the first two kernels; Adam and the repacking are shared.
 // Scratch: z and delta for 4 layers x 64 units x n samples, laid out
 // [layer][unit][sample] so that consecutive threads touch consecutive words.
 #include "ctx.hpp"
@@ -305,6 +308,8 @@ size_t train_scratch_bytes(int64_t max_batch)
     return (size_t)max_batch * sizeof(float) * (2 * 4 * 64 + 1 + 6);
 }
 
+compton_status adam_and_repack(compton_ctx* ctx, float lr, cudaStream_t stream);
+
 compton_status launch_mlp_train_step(compton_ctx* ctx, const float* ux, const float* uy, const float* uz,
                                      const float* kx, const float* ky, const float* kz, const float* y,
                                      const float* w, int64_t n, float lr, cudaStream_t stream)
@@ -327,6 +332,11 @@ compton_status launch_mlp_train_step(compton_ctx* ctx, const float* ux, const fl
     a.feat = a.dout + n;
     COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->mlp.grad, 0, sizeof(float) * kMlpParams, stream));
     COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->mlp.loss, 0, 2 * sizeof(float), stream));
+    if (ctx->train_tc) {
+        const compton_status st = launch_mlp_grad_tc(ctx, ux, uy, uz, kx, ky, kz, y, w, n, stream);
+        if (st != COMPTON_OK) return st;
+        return adam_and_repack(ctx, lr, stream);
+    }
     const int smem = (4 * 4096 + 64 * kTrThreads + 256 + 64) * 4;
     COMPTON_CUDA_TRY(ctx, cudaFuncSetAttribute(k_train_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int n_sm = 0, dev = 0;
@@ -341,6 +351,12 @@ compton_status launch_mlp_train_step(compton_ctx* ctx, const float* ux, const fl
     const dim3 grid((unsigned)((n + chunk - 1) / chunk), 5);
     k_train_dw<<<grid, kDwThreads, 0, stream>>>(a, chunk);
     COMPTON_LAUNCH_CHECK(ctx, "k_train_dw");
+    return adam_and_repack(ctx, lr, stream);
+}
+
+// Adam on the gradient sums of the step, then the inference images.
+compton_status adam_and_repack(compton_ctx* ctx, float lr, cudaStream_t stream)
+{
     ctx->adam_step += 1;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-7f;
     const float bc1 = 1.0f - (float)std::pow(0.9, (double)ctx->adam_step);

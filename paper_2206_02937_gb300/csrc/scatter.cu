@@ -6,27 +6,29 @@
 // section in the lepton rest frame, carried back to the simulation frame).
 //
 // Two kernels per step:
-//   k_pair_prob  persistent CTAs (four per SM), each taking tiles of 1024
-//                pairs (256 threads x 4 consecutive pairs) in turn, with the
-//                next tile's CellInfo window copied into shared memory while
-//                the current one is processed.  Each thread locates its pairs
-//                (binary search in the window, then forward steps) and draws
-//                one Philox block for the four Bernoulli uniforms; pairs whose
-//                uniform lies below the probability bound (candidates, about a
-//                tenth) are pooled over the CTA, and each candidate's momenta
-//                are loaded and its probability evaluated in straight-line
-//                FP32 (x and v without cancellation, sigma_KN from its series,
-//                1 - exp(-n dt s v)), with a second pass for the rare pairs
-//                (FP64 invariants above the gamma threshold, closed-form
-//                sigma_KN above the series range).  Accepted pairs are
-//                appended to a list in global memory (warp-aggregated
-//                atomics).
+//   k_pair_prob  persistent CTAs (four per SM) of eight independent warps:
+//                each warp owns a contiguous run of 128-pair chunks (32 lanes
+//                x 4 consecutive pairs, one Philox block per lane for the
+//                four Bernoulli uniforms), stages the current pair tile's
+//                cells in its own shared-memory window, locates each pair's
+//                cell, and appends the pairs whose uniform lies below the
+//                probability bound (candidates, about a tenth) to its own
+//                queue; candidates are evaluated 32 at a time, one per lane,
+//                with a batch's momenta loads issued one chunk ahead:
+//                straight-line FP32 (x and v without cancellation, sigma_KN
+//                from its series, 1 - exp(-n dt s v)), with a second pass for
+//                the rare pairs (FP64 invariants above the gamma threshold,
+//                closed-form sigma_KN above the series range).  Accepted
+//                pairs are appended to a list in global memory
+//                (warp-aggregated atomics).  No CTA-wide barrier.
 //   k_collide    every accepted pair (a few percent of all pairs) at full
 //                warp width: inverse-CDF angle, rest-frame boost and momentum
 //                update (FP32, or FP64 above the configured gamma eps),
 //                write-back of both momenta in place.
 // Every draw is keyed by the pair index, so the order of the list does not
 // change any result.
+#include <type_traits>
+
 #include "ctx.hpp"
 #include "device_math.cuh"
 
@@ -54,6 +56,10 @@ struct ScatterArgs {
     const float* r_mlp;  // network output per pair (surrogate modes)
     AcceptedPair* accepted;
     uint32_t* n_accepted;
+    // plain mode: each probability warp appends its accepted pairs to its own
+    // region of the list (from its first pair index on) and leaves the count
+    // in warp_acc[warp]; the collision kernel walks the regions
+    uint32_t* warp_acc;
     CandPair* cand;
     uint32_t* n_cand;
     MlpDev mlp;  // the network's training range (surrogate modes)
@@ -86,6 +92,7 @@ __device__ __forceinline__ int find_cell(const CellInfo* win, int nwin, int64_t 
     return lo;
 }
 
+// The collision of one accepted pair, written back in place.
 __device__ __forceinline__ void resolve(const ScatterArgs& a, const AcceptedPair& e)
 {
     float ux = e.u[0], uy = e.u[1], uz = e.u[2];
@@ -100,10 +107,7 @@ __device__ __forceinline__ void resolve(const ScatterArgs& a, const AcceptedPair
     const float F2 = kn_F2(x);
     const Philox4 rnd = draw(a.seed, a.step, kStreamAngle, e.p);
     const Angle ang = kn_sample_angle(x, rnd.r0 >> 8, F2);
-    // FP64 where FP32 cancellation would exceed the tolerance (gamma eps large)
-    const float ge2 = fmaf(ux, ux, fmaf(uy, uy, fmaf(uz, uz, 1.0f))) * fmaf(kx, kx, fmaf(ky, ky, kz * kz));
-    if (ge2 > a.collide64_sq) collide_f64(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(rnd.r1));
-    else collide_f32(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(rnd.r1));
+    collide_pair(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(rnd.r1), a.collide64_sq);
     bool upd_e = true, upd_g = true;
     if (a.weighted) {
         // weight rejection: the heavier partner takes its new momentum with
@@ -134,8 +138,8 @@ __device__ __forceinline__ float analytic_P(const ScatterArgs& a, float ux, floa
     return analytic_prob(ux, uy, uz, kx, ky, kz, dens, a.dt, a.gamma64, x_out);
 }
 
-// Probability, Bernoulli trial and list of accepted pairs of one tile of
-// 1024 pairs (256 threads x 4 consecutive pairs).
+
+// Probability, Bernoulli trial and list of accepted pairs.
 //
 // Candidate filter: sigma_KN <= sigma_T and v = 1 - beta cos psi <= 2 bound
 // every pair's probability by P_b = 1 - exp(-2 n dt) (the P_max of the
@@ -146,209 +150,307 @@ __device__ __forceinline__ float analytic_P(const ScatterArgs& a, float ux, floa
 // evaluation would take, bit for bit.  With prob_out requested every pair is
 // evaluated.
 //
-// Phase A (all pairs): locate each pair's cell in the tile's CellInfo window
-// (binary search, then forward steps), draw one Philox block for the four
-// Bernoulli uniforms, test u0 < P_b and append the candidates to the warp's
-// shared-memory list.  Phase B (the lists of all warps of the CTA pooled,
-// one candidate per lane, so whole warps stay busy): load both momenta,
-// evaluate P (FP32 invariants and series sigma_KN; FP64 invariants above the
-// gamma threshold, closed-form sigma_KN above the series range; or the
-// network output), decide, append the accepted pairs to the global list
+// Every warp works on its own: it owns a contiguous run of 128-pair chunks
+// (32 lanes x 4 consecutive pairs, one Philox block per lane), stages the
+// cells of the current pair tile in its own shared-memory window, and keeps
+// its own queue of candidates, so no warp ever waits for another at a barrier.
+// Per chunk (phase A): locate each pair's cell, draw the four Bernoulli words,
+// test them against the cell's integer threshold (the exact image of
+// u0 < P_b on the 24-bit uniform) and append the candidates to the queue.
+// Candidates are evaluated 32 at a time, one per lane (phase B): a batch is
+// taken from the queue and its momenta loads are issued before the next
+// chunk's phase A, and evaluated after it, so that the scattered loads
+// overlap the filtering; accepted pairs go to the global list
 // (warp-aggregated atomics).
-constexpr int kCandPerWarp = 32 * kPairsPerThread;
+constexpr int kProbWarps = kProbThreads / 32;
+constexpr int kChunkPairs = 32 * kPairsPerThread;  // pairs of one warp step
+constexpr int kWarpCells = 64;                     // cells of a pair tile a warp stages
+constexpr int kQueueCap = 192;                     // queued candidates per warp (see k_pair_prob)
 
-struct Cand {
-    int32_t ie, ig;
-    float dens, u0;
-    uint32_t p;
+struct WarpWindow {
+    int32_t off[kWarpCells];  // first pair of each cell
+    int32_t es[kWarpCells];   // first sorted electron
+    int32_t gs[kWarpCells];   // first sorted photon
+    float dens[kWarpCells];   // pair density
+    uint32_t thr[kWarpCells]; // candidate threshold on the 24-bit uniform
+    // per group of four pairs of the tile (256): the window cell of its first
+    // pair, bit 7 set when the group runs past the end of that cell
+    uint8_t grp[kPairsPerTile / 4];
 };
 
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
-{
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+struct WarpQueue {
+    int32_t ie[kQueueCap], ig[kQueueCap];
+    float dens[kQueueCap], u0[kQueueCap];
+    uint32_t p[kQueueCap];
+};
 
-// Persistent CTAs, each taking tiles blockIdx.x, blockIdx.x + gridDim.x, ...:
-// the CellInfo window of the next tile is copied into the other of two
-// shared-memory buffers while the current tile is processed, and the tile
-// map entries of the tile after that are loaded into registers, so the two
-// dependent global round trips of a tile (tile map, then window) overlap the
-// work of the tile before.
+// The candidate test u0 < P_b on u0 = m 2^-24 (m = word >> 8) as m < T with
+// T = ceil(P_b 2^24): P_b 2^24 is exact in FP32 (a power-of-two scaling) and
+// m is an integer, so the two tests agree for every word.  The 2.0002 factor
+// keeps P_b above any FP32 rounding of P.
+__device__ __forceinline__ uint32_t cand_threshold(float dens, float dt)
+{
+    return (uint32_t)ceilf(one_minus_exp_neg(2.0002f * dens * dt) * 16777216.0f);
+}
+
+// One evaluation batch: up to 32 queue entries from slot `first` on, one
+// per lane, whose momenta loads have been issued into registers.
+struct Batch {
+    int n, first;  // entries, first slot (the same in every lane)
+    float u[3], k[3];
+};
+
 template <bool kBinned, bool kWeighted>
 __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
 {
-    __shared__ __align__(16) CellInfo win[2][kCellWindow];
-    __shared__ Cand cand[kProbThreads / 32][kCandPerWarp];
-    __shared__ int warp_nq[kProbThreads / 32];
-    __shared__ unsigned red[2];
-    const int tid = threadIdx.x;
-    const unsigned lane = tid & 31u;
-    const int w = tid >> 5;
-    const int64_t total = kBinned ? *a.n_pairs : a.p_end;
-    const int64_t pbase = kBinned ? 0 : a.p_begin;
-    const int64_t n_tiles = total > pbase ? (total - pbase + kPairsPerTile - 1) / kPairsPerTile : 0;
-    const int64_t G = gridDim.x;
-    if (tid < 2) red[tid] = 0;
+    __shared__ WarpWindow s_win[kProbWarps];
+    __shared__ WarpQueue s_queue[kProbWarps];
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int w = threadIdx.x >> 5;
+    WarpWindow& W = s_win[w];
+    WarpQueue& Q = s_queue[w];
+    // pair indices: 32-bit for the binned pair list (its offsets are int32),
+    // 64-bit for explicit pair lists
+    using pidx = typename std::conditional<kBinned, int32_t, int64_t>::type;
+    const pidx total = kBinned ? (pidx)*a.n_pairs : (pidx)a.p_end;
+    const pidx pbase = kBinned ? 0 : (pidx)a.p_begin;
+    const int64_t n_chunks = total > pbase ? ((int64_t)total - pbase + kChunkPairs - 1) / kChunkPairs : 0;
+    const int64_t n_warps = (int64_t)gridDim.x * kProbWarps;
+    const int64_t gw = (int64_t)blockIdx.x * kProbWarps + w;
+    const int ch_begin = (int)(n_chunks * gw / n_warps), ch_end = (int)(n_chunks * (gw + 1) / n_warps);
     const bool all = a.prob_out != nullptr;
-    unsigned n_pairs = 0, n_hit = 0;
+    unsigned n_pairs = 0;
+    int qh = 0, qn = 0;     // queue head and length (the same in every lane)
+    // this warp's region of the accepted list: one slot per pair it owns
+    const uint32_t acc_base = (uint32_t)ch_begin * kChunkPairs;
+    uint32_t n_acc = 0;
+    int win_tile = -1;  // pair tile whose cells the window holds
+    int c_first = 0, nw = 0;
 
-    // window of tile tt: its first cell and the number of staged CellInfo
-    int cf = 0, nw = 0, cf_n = 0, nw_n = 0;
-    auto meta = [&](int64_t tt, int& c_first, int& nwin) {
-        c_first = a.tile_cell[tt];
-        nwin = a.tile_cell[tt + 1] - c_first + 1;
-    };
-    auto stage = [&](int buf, int c_first, int nwin) {
-        if (nwin <= kCellWindow)
-            for (int i = tid; i < nwin; i += kProbThreads) cp_async16(&win[buf][i], a.cinfo + c_first + i);
-        cp_async_commit();
-    };
-    int64_t t = blockIdx.x;
-    if (kBinned) {
-        if (t < n_tiles) {
-            meta(t, cf, nw);
-            stage(0, cf, nw);
+    // Take up to 32 candidates off the queue and issue their momenta loads.
+    // The entries stay in their slots until the batch is evaluated: a batch
+    // is taken with fewer than 32 entries left behind it, and the next chunk
+    // appends at most 128, so with 192 slots nothing overwrites it.
+    auto take = [&](Batch& b) {
+        b.n = qn < 32 ? qn : 32;
+        b.first = qh;
+        int slot = qh + (int)lane;
+        if (slot >= kQueueCap) slot -= kQueueCap;
+        if ((int)lane < b.n) {
+            const int32_t ie = Q.ie[slot], ig = Q.ig[slot];
+            b.u[0] = a.u[0][ie];
+            b.u[1] = a.u[1][ie];
+            b.u[2] = a.u[2][ie];
+            b.k[0] = a.k[0][ig];
+            b.k[1] = a.k[1][ig];
+            b.k[2] = a.k[2][ig];
         }
-        if (t + G < n_tiles) meta(t + G, cf_n, nw_n);
-    }
-    for (int buf = 0; t < n_tiles; t += G, buf ^= 1) {
-        int cf_nn = 0, nw_nn = 0;
-        if (kBinned) {
-            cp_async_wait_all();
-            __syncthreads();  // this tile's window is in; the previous tile is done with the other buffer
-            if (t + G < n_tiles) stage(buf ^ 1, cf_n, nw_n);
-            if (t + 2 * G < n_tiles) meta(t + 2 * G, cf_nn, nw_nn);
-        } else {
-            __syncthreads();  // the previous tile is done with the candidate lists
+        qh += b.n;
+        if (qh >= kQueueCap) qh -= kQueueCap;
+        qn -= b.n;
+    };
+    // probability, decision and accepted-list entry of a batch
+    auto evaluate = [&](const Batch& b) {
+        bool hit = false;
+        float x = -1.0f;
+        int32_t ie = 0, ig = 0;
+        uint32_t p = 0;
+        if ((int)lane < b.n) {
+            int slot = b.first + (int)lane;
+            if (slot >= kQueueCap) slot -= kQueueCap;
+            ie = Q.ie[slot];
+            ig = Q.ig[slot];
+            p = Q.p[slot];
+            const float dens = Q.dens[slot], u0 = Q.u0[slot];
+            const Invariants inv = invariants_f32(b.u[0], b.u[1], b.u[2], b.k[0], b.k[1], b.k[2]);
+            x = inv.x;
+            float P;
+            if (inv.gamma > a.gamma64 || !(inv.x < 0.99f)) {
+                P = analytic_P(a, b.u[0], b.u[1], b.u[2], b.k[0], b.k[1], b.k[2], dens, &x);
+            } else {
+                const float Pr = one_minus_exp_neg(dens * a.dt * 0.375f * kn_F2_series(inv.x) * inv.v);
+                P = inv.eps > 0.0f ? Pr : 0.0f;
+            }
+            hit = u0 < P;
+            if (a.prob_out) a.prob_out[p] = P;
+            if (a.flag_out) a.flag_out[p] = hit ? 1 : 0;
         }
-        const int64_t p0 = pbase + t * kPairsPerTile;
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit)
+            a.accepted[acc_base + n_acc + __popc(m & lt_mask)] =
+                AcceptedPair{ie, ig, x, p, {b.u[0], b.u[1], b.u[2]}, {b.k[0], b.k[1], b.k[2]}, {0u, 0u}};
+        n_acc += __popc(m);
+    };
 
-        // ---------------- phase A: every pair ----------------
-        const int64_t pb = p0 + (int64_t)tid * kPairsPerThread;
+    Batch pend;
+    pend.n = 0;
+    for (int ch = ch_begin; ch < ch_end; ++ch) {
+        // ---------------- phase A: the chunk's 128 pairs ----------------
+        const pidx q0 = pbase + (pidx)ch * kChunkPairs;
+        const pidx pb = q0 + 4 * (pidx)lane;
         const Philox4 rnd4 = draw(a.seed, a.step, kStreamScatter, (uint32_t)(pb >> 2));
         const uint32_t words[4] = {rnd4.r0, rnd4.r1, rnd4.r2, rnd4.r3};
-        const CellInfo* cw = nw <= kCellWindow ? win[buf] : a.cinfo + cf;
-        int ci = (kBinned && pb < total) ? find_cell(cw, nw, pb) : 0;
-        int ci_bound = -1;  // the cell whose candidate bound `bound` holds
-        float bound = 0.0f;
-        int nq = 0;
+        if (kBinned) {
+            const int t = (int)(q0 / kPairsPerTile);
+            if (t != win_tile) {
+                __syncwarp();  // every lane is done with the previous window
+                win_tile = t;
+                c_first = a.tile_cell[t];
+                nw = a.tile_cell[t + 1] - c_first + 1;
+                if (nw <= kWarpCells) {
+                    for (int i = (int)lane; i < nw; i += 32) {
+                        const CellInfo c = a.cinfo[c_first + i];
+                        W.off[i] = c.pair_off;
+                        W.es[i] = c.e_start;
+                        W.gs[i] = c.g_start;
+                        W.dens[i] = c.dens;
+                        if (!kWeighted) W.thr[i] = cand_threshold(c.dens, a.dt);
+                    }
+                    __syncwarp();
+                    // the group map: cell i owns the groups whose first pair
+                    // lies in it, [ceil((o_i - q_t)/4), ceil((o_{i+1} - q_t)/4))
+                    // clipped to the tile; the last of them runs past the cell
+                    // unless the cell ends on a group boundary
+                    const int q_t = t * kPairsPerTile;
+                    for (int i = (int)lane; i < nw; i += 32) {
+                        const int o0 = W.off[i] - q_t;
+                        const int o1 = (i + 1 < nw ? W.off[i + 1] : q_t + kPairsPerTile + 4) - q_t;
+                        int g0 = (o0 + 3) >> 2, g1 = (o1 + 3) >> 2;
+                        g0 = g0 < 0 ? 0 : g0;
+                        g1 = g1 > kPairsPerTile / 4 ? kPairsPerTile / 4 : g1;
+                        for (int g = g0; g < g1; ++g)
+                            W.grp[g] = (uint8_t)(i | (4 * g + 4 > o1 ? 0x80 : 0));
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        const bool local = nw <= kWarpCells;
+        const CellInfo* cw = a.cinfo + c_first;  // the tile's cells in global memory (wide tiles)
+        int ci = 0;
+        bool straddle = true;  // the lane's four pairs may span several cells
+        if (kBinned && pb < total) {
+            if (local) {
+                const uint32_t e = W.grp[(pb - (pidx)win_tile * kPairsPerTile) >> 2];
+                ci = (int)(e & 0x7Fu);
+                straddle = (e & 0x80u) != 0;
+            } else {
+                int lo = 0, hi = nw - 1;  // last cell whose first pair is <= pb
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (cw[mid].pair_off <= pb) lo = mid; else hi = mid - 1;
+                }
+                ci = lo;
+            }
+        }
+        int cur = -1;
+        int32_t c_off = 0, c_es = 0, c_gs = 0;
+        float c_dens = 0.0f;
+        uint32_t c_thr = 0;
 #pragma unroll
         for (int r = 0; r < kPairsPerThread; ++r) {
-            const int64_t p = pb + r;
+            const pidx p = pb + r;
             const bool valid = p < total;
             int ie = 0, ig = 0;
             float dens = 0.0f;
+            uint32_t thr = 0;
             if (valid) {
                 if (kBinned) {
-                    while (ci + 1 < nw && (int64_t)cw[ci + 1].pair_off <= p) ++ci;
-                    const CellInfo c = cw[ci];
-                    const int j = (int)(p - c.pair_off);
-                    ie = c.e_start + j;
-                    ig = c.g_start + j;
-                    dens = pair_density<kWeighted>(a, c.dens, ie, ig);
-                    // equal weights: one bound per cell, recomputed only when
-                    // this thread's pairs reach the next cell
-                    if (kWeighted || ci != ci_bound) {
-                        ci_bound = ci;
-                        bound = one_minus_exp_neg(2.0002f * dens * a.dt);
+                    if (straddle) {
+                        if (local) {
+                            while (ci + 1 < nw && W.off[ci + 1] <= p) ++ci;
+                        } else {
+                            while (ci + 1 < nw && cw[ci + 1].pair_off <= p) ++ci;
+                        }
                     }
+                    if (ci != cur) {
+                        cur = ci;
+                        if (local) {
+                            c_off = W.off[ci];
+                            c_es = W.es[ci];
+                            c_gs = W.gs[ci];
+                            c_dens = W.dens[ci];
+                            if (!kWeighted) c_thr = W.thr[ci];
+                        } else {
+                            const CellInfo c = cw[ci];
+                            c_off = c.pair_off;
+                            c_es = c.e_start;
+                            c_gs = c.g_start;
+                            c_dens = c.dens;
+                            if (!kWeighted) c_thr = cand_threshold(c.dens, a.dt);
+                        }
+                    }
+                    const int j = (int)(p - c_off);
+                    ie = c_es + j;
+                    ig = c_gs + j;
+                    dens = pair_density<kWeighted>(a, c_dens, ie, ig);
+                    thr = kWeighted ? cand_threshold(dens, a.dt) : c_thr;
                 } else {
                     ie = (int)p;
                     ig = (int)p;
                     dens = a.n_dens[p];
-                    bound = one_minus_exp_neg(2.0002f * dens * a.dt);
+                    thr = cand_threshold(dens, a.dt);
                 }
                 ++n_pairs;
             }
-            const float u0 = u24_closed0(words[r]);
-            const bool is_cand = valid && (all || u0 < bound);
+            const bool is_cand = valid && (all || (words[r] >> 8) < thr);
             if (valid && !is_cand && a.flag_out) a.flag_out[p] = 0;
             const unsigned m = __ballot_sync(0xffffffffu, is_cand);
-            if (is_cand) cand[w][nq + __popc(m & ((1u << lane) - 1u))] = Cand{ie, ig, dens, u0, (uint32_t)p};
-            nq += __popc(m);
-        }
-        if (lane == 0) warp_nq[w] = nq;
-        __syncthreads();
-        // the warps' lists as one list of the CTA's candidates, so that phase
-        // B keeps whole warps busy (about a tenth of the pairs are candidates)
-        int pre[kProbThreads / 32 + 1];
-        pre[0] = 0;
-#pragma unroll
-        for (int v = 0; v < kProbThreads / 32; ++v) pre[v + 1] = pre[v] + warp_nq[v];
-        const int n_tot = pre[kProbThreads / 32];
-
-        // ---------------- phase B: candidates, one per lane ----------------
-        for (int base = w * 32; base < n_tot; base += kProbThreads) {
-            const int j = base + (int)lane;
-            bool hit = false;
-            Cand c{0, 0, 0.0f, 1.0f, 0u};
-            float x = -1.0f;
-            float ux = 0.0f, uy = 0.0f, uz = 0.0f, kx = 0.0f, ky = 0.0f, kz = 0.0f;
-            if (j < n_tot) {
-                int v = 0, first = 0;
-#pragma unroll
-                for (int q = 1; q < kProbThreads / 32; ++q)
-                    if (pre[q] <= j) {
-                        v = q;
-                        first = pre[q];
-                    }
-                c = cand[v][j - first];
-                ux = a.u[0][c.ie];
-                uy = a.u[1][c.ie];
-                uz = a.u[2][c.ie];
-                kx = a.k[0][c.ig];
-                ky = a.k[1][c.ig];
-                kz = a.k[2][c.ig];
-                const Invariants inv = invariants_f32(ux, uy, uz, kx, ky, kz);
-                x = inv.x;
-                float P;
-                if (inv.gamma > a.gamma64 || !(inv.x < 0.99f)) {
-                    P = analytic_P(a, ux, uy, uz, kx, ky, kz, c.dens, &x);
-                } else {
-                    const float Pr = one_minus_exp_neg(c.dens * a.dt * 0.375f * kn_F2_series(inv.x) * inv.v);
-                    P = inv.eps > 0.0f ? Pr : 0.0f;
-                }
-                hit = c.u0 < P;
-                if (a.prob_out) a.prob_out[c.p] = P;
-                if (a.flag_out) a.flag_out[c.p] = hit ? 1 : 0;
+            if (is_cand) {
+                int slot = qh + qn + __popc(m & lt_mask);
+                if (slot >= kQueueCap) slot -= kQueueCap;
+                Q.ie[slot] = ie;
+                Q.ig[slot] = ig;
+                Q.dens[slot] = dens;
+                Q.u0[slot] = u24_closed0(words[r]);
+                Q.p[slot] = (uint32_t)p;
             }
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (m) {
-                uint32_t at = 0;
-                if (lane == 0) at = atomicAdd(a.n_accepted, (uint32_t)__popc(m));
-                at = __shfl_sync(0xffffffffu, at, 0);
-                if (hit) {
-                    a.accepted[at + __popc(m & ((1u << lane) - 1u))] =
-                        AcceptedPair{c.ie, c.ig, x, c.p, {ux, uy, uz}, {kx, ky, kz}, {0u, 0u}};
-                    ++n_hit;
-                }
-            }
+            qn += __popc(m);
         }
-        cf = cf_n;
-        nw = nw_n;
-        cf_n = cf_nn;
-        nw_n = nw_nn;
-    }
-    cp_async_wait_all();
+        __syncwarp();  // the queue entries are visible to every lane
 
-    // counters: warp sums, then one atomic per block
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        n_pairs += __shfl_xor_sync(0xffffffffu, n_pairs, d);
-        n_hit += __shfl_xor_sync(0xffffffffu, n_hit, d);
+        // ---------------- phase B: candidates, 32 at a time ----------------
+        if (pend.n) evaluate(pend);  // its loads were issued before this chunk
+        while (qn >= 64) {           // only when most pairs are candidates
+            Batch b;
+            take(b);
+            evaluate(b);
+        }
+        if (qn >= 32) take(pend);  // evaluated after the next chunk
+        else pend.n = 0;
+        __syncwarp();  // slots evaluated above may be refilled by other lanes next
     }
-    __syncthreads();
+    if (pend.n) evaluate(pend);
+    while (qn > 0) {
+        Batch b;
+        take(b);
+        evaluate(b);
+    }
+
+    // counters: the warp's accepted count for the collision kernel, warp
+    // sums of the statistics, one atomic per warp
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) n_pairs += __shfl_xor_sync(0xffffffffu, n_pairs, d);
     if (lane == 0) {
-        atomicAdd(&red[0], n_pairs);
-        atomicAdd(&red[1], n_hit);
+        a.warp_acc[gw] = n_acc;
+        if (n_pairs) atomicAdd(&a.stats->pairs_tested, (unsigned long long)n_pairs);
+        if (n_acc) atomicAdd(&a.stats->scatters, (unsigned long long)n_acc);
     }
-    __syncthreads();
-    if (tid == 0) {
-        if (red[0]) atomicAdd(&a.stats->pairs_tested, (unsigned long long)red[0]);
-        if (red[1]) atomicAdd(&a.stats->scatters, (unsigned long long)red[1]);
+}
+
+// The collisions of the accepted pairs of k_pair_prob: one CTA per warp
+// region of the list (prob_warps regions, region w from pair index
+// chunk_begin(w) * 128 on, warp_acc[w] entries).
+__global__ void __launch_bounds__(128) k_collide_regions(ScatterArgs a, int prob_warps)
+{
+    const int64_t total = a.n_pairs ? *a.n_pairs : a.p_end;
+    const int64_t pbase = a.n_pairs ? 0 : a.p_begin;
+    const int64_t n_chunks = total > pbase ? (total - pbase + kChunkPairs - 1) / kChunkPairs : 0;
+    for (int w = blockIdx.x; w < prob_warps; w += gridDim.x) {
+        const uint32_t base = (uint32_t)(n_chunks * w / prob_warps) * kChunkPairs;
+        const uint32_t n = a.warp_acc[w];
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) resolve(a, a.accepted[base + i]);
     }
 }
 
@@ -607,9 +709,7 @@ __global__ void __launch_bounds__(256) k_ntc(NtcArgs a)
                 if (!(u24_closed0(q.r2) < ratio)) continue;
                 const Philox4 z = draw(a.seed, a.step, 7u | ((uint32_t)j << 8), (uint32_t)c);
                 const Angle ang = kn_sample_angle(x, q.r3 >> 8, F2);
-                const float ge2 = fmaf(ux, ux, fmaf(uy, uy, fmaf(uz, uz, 1.0f))) * fmaf(kx, kx, fmaf(ky, ky, kz * kz));
-                if (ge2 > a.collide64_sq) collide_f64(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(z.r0));
-                else collide_f32(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(z.r0));
+                collide_pair(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(z.r0), a.collide64_sq);
                 a.u[0][ie] = ux;
                 a.u[1][ie] = uy;
                 a.u[2][ie] = uz;
@@ -666,6 +766,7 @@ unsigned prob_grid(unsigned tiles)
     int dev = 0, n_sm = 1;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm < 1) n_sm = 1;
+    if (n_sm > kMaxProbWarps / (4 * kProbWarps)) n_sm = kMaxProbWarps / (4 * kProbWarps);
     const unsigned cap = (unsigned)n_sm * 4u;
     return tiles < 1u ? 1u : (tiles < cap ? tiles : cap);
 }
@@ -693,6 +794,7 @@ void fill_common(ScatterArgs& a, compton_ctx* ctx, uint64_t seed, uint64_t step,
     a.r_mlp = ctx->r_buf;
     a.accepted = ctx->accepted;
     a.n_accepted = ctx->n_accepted;
+    a.warp_acc = ctx->warp_acc;
     a.cand = ctx->cand;
     a.n_cand = ctx->n_cand;
     a.mlp = ctx->mlp;
@@ -700,6 +802,17 @@ void fill_common(ScatterArgs& a, compton_ctx* ctx, uint64_t seed, uint64_t step,
     a.w_g = nullptr;
     a.w_const = (float)ctx->cfg.w_over_v;
     a.weighted = false;
+}
+
+// The collisions of the accepted pairs.
+compton_status launch_collide(compton_ctx* ctx, ScatterArgs& a, int64_t rows, cudaStream_t stream)
+{
+    {
+        TimedScope ts_(ctx, COMPTON_K_COLLIDE, stream);
+        k_collide<<<collide_grid(rows), 256, 0, stream>>>(a);
+    }
+    COMPTON_LAUNCH_CHECK(ctx, "k_collide");
+    return COMPTON_OK;
 }
 
 // The step after the pair list is known: probability and trial of every
@@ -712,8 +825,20 @@ compton_status launch_step(compton_ctx* ctx, ScatterArgs& a, compton_mode mode, 
 {
     COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->n_accepted, 0, sizeof(uint32_t), stream));
     if (mode == COMPTON_MODE_PLAIN) {
-        TimedScope ts_(ctx, COMPTON_K_PROB, stream);
-        k_pair_prob<kBinned, kWeighted><<<prob_grid(tiles), kProbThreads, 0, stream>>>(a);
+        const unsigned grid = prob_grid(tiles);
+        {
+            TimedScope ts_(ctx, COMPTON_K_PROB, stream);
+            k_pair_prob<kBinned, kWeighted><<<grid, kProbThreads, 0, stream>>>(a);
+        }
+        COMPTON_LAUNCH_CHECK(ctx, "k_pair_prob");
+        const int prob_warps = (int)grid * kProbWarps;
+        {
+            TimedScope ts_(ctx, COMPTON_K_COLLIDE, stream);
+            const int cgrid = collide_grid((int64_t)prob_warps * 128);
+            k_collide_regions<<<cgrid < prob_warps ? cgrid : prob_warps, 128, 0, stream>>>(a, prob_warps);
+        }
+        COMPTON_LAUNCH_CHECK(ctx, "k_collide_regions");
+        return COMPTON_OK;
     } else {
         COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->n_cand, 0, sizeof(uint32_t), stream));
         {
@@ -727,12 +852,7 @@ compton_status launch_step(compton_ctx* ctx, ScatterArgs& a, compton_mode mode, 
         if (mode == COMPTON_MODE_PNET) {
             const compton_status sp = launch_pnet_decide(ctx, rows, dec, a.w_e, a.w_g, stream);
             if (sp != COMPTON_OK) return sp;
-            {
-                TimedScope ts_(ctx, COMPTON_K_COLLIDE, stream);
-                k_collide<<<collide_grid(rows), 256, 0, stream>>>(a);
-            }
-            COMPTON_LAUNCH_CHECK(ctx, "k_collide");
-            return COMPTON_OK;
+            return launch_collide(ctx, a, rows, stream);
         }
         const bool fused = mode != COMPTON_MODE_MLP_FP32;
         compton_status st = launch_mlp_infer(ctx, a.u[0], a.u[1], a.u[2], a.k[0], a.k[1], a.k[2], rows, mode,
@@ -744,12 +864,7 @@ compton_status launch_step(compton_ctx* ctx, ScatterArgs& a, compton_mode mode, 
         }
     }
     COMPTON_LAUNCH_CHECK(ctx, "k_pair_prob");
-    {
-        TimedScope ts_(ctx, COMPTON_K_COLLIDE, stream);
-        k_collide<<<collide_grid(rows), 256, 0, stream>>>(a);
-    }
-    COMPTON_LAUNCH_CHECK(ctx, "k_collide");
-    return COMPTON_OK;
+    return launch_collide(ctx, a, rows, stream);
 }
 
 }  // namespace

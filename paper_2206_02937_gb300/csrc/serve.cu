@@ -81,9 +81,7 @@ __device__ __forceinline__ void serve_resolve(const ReqDev* reqs, const SQEntry&
     }
     const Philox4 rnd = draw(R.seed, R.step, kStreamAngle, (uint32_t)e.p);
     const Angle ang = kn_sample_angle(x, rnd.r0 >> 8, F2);
-    const float ge2 = fmaf(ux, ux, fmaf(uy, uy, fmaf(uz, uz, 1.0f))) * fmaf(kx, kx, fmaf(ky, ky, kz * kz));
-    if (ge2 > c64sq) collide_f64(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(rnd.r1));
-    else collide_f32(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(rnd.r1));
+    collide_pair(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(rnd.r1), c64sq);
     R.u[0][e.p] = ux;
     R.u[1][e.p] = uy;
     R.u[2][e.p] = uz;
@@ -434,7 +432,7 @@ compton_status serve_start(compton_ctx* ctx, uint64_t pool_bytes, int32_t max_ac
     E->device = ctx->cfg.device;
     E->pool_bytes = pool_bytes;
     E->max_active = max_active;
-    cudaError_t e = cudaMalloc(&E->pool, pool_bytes);
+    cudaError_t e = inject_fault() ? cudaErrorMemoryAllocation : cudaMalloc(&E->pool, pool_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&E->reqs_dev, sizeof(ReqDev) * max_active);
     if (e == cudaSuccess) e = cudaMalloc(&E->counters, sizeof(unsigned long long) * max_active);
     if (e == cudaSuccess) e = cudaMalloc(&E->tiles_dev, sizeof(TileDev) * kMaxTilesPerLaunch * kTileRing);

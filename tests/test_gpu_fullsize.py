@@ -5,16 +5,14 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_2206_02937_gb300 import workloads as wl
 from tests.gpu_util import energy_scale, gpu_step
 
 pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
-def full():
-    w = wl.c2(512, 512, 64, seed=2)
-    return w, gpu_step(w, step=3)
+def full(c2_full):
+    return c2_full, gpu_step(c2_full, step=3)
 
 
 def test_full_size_binning_properties(full):

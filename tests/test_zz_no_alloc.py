@@ -2,8 +2,10 @@
 device memory when they need it (a particle-in-cell code whose memory manager
 owns all device memory, or a step loop that must not allocate).  Its output
 must equal the offsets the context path (compton_bin_pairs) produces, on two
-calls in a row (the shared static scratch is cleared by each call).  This
-file is collected last on purpose."""
+calls in a row (the shared static scratch is cleared by each call), and a
+numpy histogram and cumulative sum at the edges: no particles, the largest
+accepted cell count, and indices outside [0, n_cells), which are skipped.
+This file is collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -25,6 +27,19 @@ def _context_offsets(cg, torch, w):
         cg.compton_destroy(ctx)
 
 
+def _numpy_offsets(cell, n_cells):
+    c = cell[(cell >= 0) & (cell < n_cells)]
+    return np.concatenate([[0], np.cumsum(np.bincount(c, minlength=n_cells))]).astype(np.int32)
+
+
+def _noalloc(cg, torch, cell_np, n_cells):
+    cell = torch.from_numpy(np.ascontiguousarray(cell_np, dtype=np.int32)).cuda()
+    off = torch.full((n_cells + 1,), -7, dtype=torch.int32, device="cuda")
+    cg.compton_cell_offsets_noalloc(cell, n_cells, off)
+    torch.cuda.synchronize()
+    return off.cpu().numpy()
+
+
 def test_noalloc_offsets_match_context_path_twice():
     import paper_2206_02937_gb300 as cg
     torch = torch_cuda()
@@ -33,19 +48,41 @@ def test_noalloc_offsets_match_context_path_twice():
         w = wl.c2(nx, nx, 48, seed=seed)
         ref_e, ref_g = _context_offsets(cg, torch, w)
         for sp, ref in ((w.e, ref_e), (w.g, ref_g)):
-            cell = torch.from_numpy(sp["cell"]).cuda()
-            off = torch.full((w.n_cells + 1,), -7, dtype=torch.int32, device="cuda")
-            cg.compton_cell_offsets_noalloc(cell, w.n_cells, off)
-            torch.cuda.synchronize()
-            assert np.array_equal(off.cpu().numpy(), ref), f"call {call}"
+            assert np.array_equal(_noalloc(cg, torch, sp["cell"], w.n_cells), ref), f"call {call}"
 
 
-def test_noalloc_rejects_too_many_cells():
+def test_noalloc_edges_against_numpy():
+    import paper_2206_02937_gb300 as cg
+    torch = torch_cuda()
+    cg.build()
+    rng = np.random.default_rng(11)
+    # no particles at all
+    off = _noalloc(cg, torch, np.zeros(0, dtype=np.int32), 1000)
+    assert np.array_equal(off, np.zeros(1001, dtype=np.int32))
+    # the largest accepted cell count, with a ragged last strip of the scan
+    for n_cells in (1 << 20, (1 << 20) - 4093, 4097, 1):
+        cell = rng.integers(0, n_cells, 3_000_000, dtype=np.int64).astype(np.int32)
+        assert np.array_equal(_noalloc(cg, torch, cell, n_cells), _numpy_offsets(cell, n_cells)), n_cells
+    # indices outside [0, n_cells) are skipped; off[n_cells] counts the rest
+    n_cells = 70001
+    cell = rng.integers(-5000, n_cells + 5000, 1_000_000, dtype=np.int64).astype(np.int32)
+    cell[:3] = [-(2 ** 31), 2 ** 31 - 1, n_cells]
+    off = _noalloc(cg, torch, cell, n_cells)
+    assert np.array_equal(off, _numpy_offsets(cell, n_cells))
+    assert off[-1] == int(((cell >= 0) & (cell < n_cells)).sum()) < cell.size
+
+
+def test_noalloc_rejects_bad_arguments():
     import paper_2206_02937_gb300 as cg
     torch = torch_cuda()
     cg.build()
     cell = torch.zeros(10, dtype=torch.int32, device="cuda")
     off = torch.zeros(16, dtype=torch.int32, device="cuda")
+    big = torch.zeros((1 << 20) + 2, dtype=torch.int32, device="cuda")
     with pytest.raises(cg.ComptonError) as e:
-        cg.compton_cell_offsets_noalloc(cell, (1 << 20) + 1, off)
+        cg.compton_cell_offsets_noalloc(cell, (1 << 20) + 1, big)
     assert e.value.status == cg.COMPTON_ERANGE
+    with pytest.raises(ValueError):   # off_out shorter than n_cells + 1
+        cg.compton_cell_offsets_noalloc(cell, 16, off)
+    with pytest.raises(ValueError):   # wrong dtype
+        cg.compton_cell_offsets_noalloc(cell.to(torch.int64), 8, off)
