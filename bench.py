@@ -39,7 +39,6 @@ MEASURED_TRAFFIC = {
     "k_sort_gather": ((134.694144e6 + 111.26272e6) / 8372876, "particle",
                       "profiles/k_sort_gather_in_place_256x256.md"),
     "k_count": (34.025984e6 / 8372876, "particle", "profiles/k_count_256x256.md"),
-    "k_pair_prob": ((96.822528e6 + 3.64672e6) / 4186438, "pair", "profiles/k_pair_prob_256x256.md"),
 }
 
 
@@ -59,6 +58,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--train-steps", type=int, default=8000)
     ap.add_argument("--train-balanced", action="store_true")
+    ap.add_argument("--train-precision", default="bf16", choices=["bf16", "fp32"],
+                    help="training arithmetic of the surrogate: tcgen05 BF16 (default) or FP32 CUDA cores")
     ap.add_argument("--workload", default="c2", choices=["c2", "c5", "ic"],
                     help="c2: the 2D 512x512 step (default); c5: the 3D power-law precision sweep; "
                          "ic: the inverse-Compton benchmark with a transfer-learned surrogate")
@@ -283,9 +284,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     bin_avg = sum(bin_ms) / len(bin_ms)
 
     # per-kernel device times: the same steps once more with the library's
-    # event timing on (kept out of the headline region above)
+    # event timing on (kept out of the headline region above).  The library
+    # keeps the last 64 launches of each kernel slot and the scan slot
+    # launches three kernels per step, so 20 steps keep every launch.
+    kt_steps = min(args.steps, 20)
     cg.compton_kernel_timing(ctx, True)
-    for i in range(args.steps):
+    for i in range(kt_steps):
         one_step(step, bufs[step % 2], bufs[(step + 1) % 2])
         step += 1
     torch.cuda.synchronize()
@@ -299,8 +303,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "k_scan": 48.0 * w.n_cells,                    # counts in, offsets + CellInfo out
         "k_place": 0.0,                                # returns at once on ordered input
         "k_sort_gather": 36.0 * n_part,                # id + momentum read, sorted copy written
-        "k_pair_prob": 24.0 * pairs_per_step + 16.0 * acc_per_step + 16.0 * w.n_cells,
-        "k_collide": 64.0 * acc_per_step,              # list entry, both momenta read and written
+        # both momenta of every pair (charged as if read; only the candidates
+        # below the probability bound read theirs), the 48-byte accepted-list
+        # entry written, the 16-byte CellInfo of every cell
+        "k_pair_prob": 24.0 * pairs_per_step + 48.0 * acc_per_step + 16.0 * w.n_cells,
+        "k_collide": 72.0 * acc_per_step,              # 48-byte list entry read, both momenta written
     }
     kernels = {}
     for name, v in kt.items():
@@ -308,7 +315,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             continue
         avg = v["ms"] / v["launches"]
         gbs = algo_bytes[name] / (avg * 1e-3) / 1e9
-        kernels[name] = {"avg_launch_ms": avg, "launches_per_step": v["launches"] / args.steps,
+        kernels[name] = {"avg_launch_ms": avg, "launches_per_step": v["launches"] / kt_steps,
                          "algorithmic_bytes_per_launch": algo_bytes[name], "achieved_gbs": gbs,
                          "frac_of_hbm": gbs / hbm_peak}
     dom = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"] * kernels[k]["launches_per_step"])
@@ -326,7 +333,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "note": "dominant kernel of the step by device time; durations from CUDA events the library "
                         "records on the launch stream around each kernel"}
     # whole binning and scattering calls (events around the C-ABI calls)
-    bytes_scatter = pairs_per_step * 24.0 + acc_per_step * 80.0 + w.n_cells * 16.0
+    # the two kernels of the call: k_pair_prob's bytes and k_collide's
+    bytes_scatter = pairs_per_step * 24.0 + acc_per_step * (48.0 + 72.0) + w.n_cells * 16.0
     achieved_sc = bytes_scatter / (sc_avg * 1e-3) / 1e9
     # binning of input already in cell order (every step after the first: the
     # particles keep their cells): per particle 4 (count) + 4 + 12 (id and
@@ -396,11 +404,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     mlp = None
     if not args.no_mlp:
-        mlp = run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step, peaks)
-        step += args.warmup + args.steps + 2
-        # the surrogate step's rate over the plain step's on the same pairs
-        # (below 1: the network step is slower)
-        mlp["gain_vs_plain"] = (total_ms / args.steps) / mlp["ms_per_step"]
+        mlp = run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step, peaks,
+                      with_oracle=rank == 0 and not args.no_cpu_baseline)
+        step += 2 * (args.warmup + args.steps) + 2
 
     serving = None
     if not args.no_serving and rank == 0:
@@ -445,7 +451,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         dist.destroy_process_group()
 
 
-def train_surrogate(cg, torch, ctx, dev, n_samples=10_000_000, steps=8000, batch=8192, lr=1e-2, balanced=False):
+def train_surrogate(cg, torch, ctx, dev, n_samples=10_000_000, steps=8000, batch=8192, lr=1e-2, balanced=False,
+                    precision="bf16"):
     """Train the network on the GPU on analytic targets over the surrogate's
     range (gamma log-uniform on [1, 1e3], eps log-uniform on [1e-4, 1]):
     Adam with the learning rate decayed from lr to 0 on a cosine, MAE loss,
@@ -453,8 +460,10 @@ def train_surrogate(cg, torch, ctx, dev, n_samples=10_000_000, steps=8000, batch
     and held-out sets.  balanced=True weights the loss by the
     data-balancing weights (32 log bins of r on [1e-6, 1]); with the MAE
     loss that pulls the network towards the rare tiny targets and costs
-    accuracy everywhere else, so it is off by default.  Not timed as part of
-    the step; its own wall time is reported."""
+    accuracy everywhere else, so it is off by default.  precision "bf16"
+    runs every contraction of the training step on the tcgen05 tensor cores,
+    "fp32" on the CUDA cores.  Not timed as part of the step; its own wall
+    time is reported."""
     from paper_2206_02937_gb300 import workloads as wl
     rng = np.random.default_rng(0)
     theta = np.zeros(12993, dtype=np.float32)
@@ -464,6 +473,7 @@ def train_surrogate(cg, torch, ctx, dev, n_samples=10_000_000, steps=8000, batch
         theta[at:at + o * i] = rng.uniform(-lim, lim, o * i)
         at += o * i + o
     cg.compton_mlp_set_params(ctx, theta)
+    cg.compton_mlp_set_train_precision(ctx, cg.MODE_MLP_BF16 if precision == "bf16" else cg.MODE_MLP_FP32)
     u, k = wl.c3(n_samples, seed=30)
     ut, kt = torch.from_numpy(u).to(dev), torch.from_numpy(k).to(dev)
     r = torch.zeros(n_samples, device=dev)
@@ -501,10 +511,58 @@ def train_surrogate(cg, torch, ctx, dev, n_samples=10_000_000, steps=8000, batch
                       "mean_rel_r_above_1e-3": float((err[big] / rh[big].double()).mean()),
                       "max_rel_r_above_1e-3": float((err[big] / rh[big].double()).max())}
     torch.cuda.synchronize()
-    return {"steps": steps, "batch": batch, "lr": f"{lr} cosine-decayed to 0", "samples": n_samples,
+    return {"precision": precision, "steps": steps, "batch": batch, "lr": f"{lr} cosine-decayed to 0",
+            "samples": n_samples,
             "split": "80 % training / 20 % held out",
             "loss": "MAE" + (" weighted by 32 log bins of r" if balanced else ""),
             "loss_first": losses[0], "loss_last": losses[-1], "train_s": train_s, "held_out": held}
+
+
+TRAIN_FLOPS_PER_SAMPLE = 2.0 * (6 * 64 + 3 * 64 * 64 + 64) * 2 + 2.0 * 3 * 64 * 64
+# forward z = a W^T (25,472) + weight gradients delta^T a (25,472) + input
+# gradients delta W of the three 64x64 layers (24,576) = 75,520 per sample
+
+
+def train_throughput(cg, torch, dev, peaks, batch=1 << 20, reps=5):
+    """One training step (forward, backward, Adam) on a large batch, both
+    precisions, timed with CUDA events: algorithmic FLOPs per second of the
+    whole train-step call against the bf16 tensor peak."""
+    from paper_2206_02937_gb300 import workloads as wl
+    out = {}
+    u, k = wl.c3(batch, seed=31)
+    ut, kt = torch.from_numpy(u).to(dev), torch.from_numpy(k).to(dev)
+    ctx = cg.compton_init(1, 0, 1.0, 0.05, 1, device=dev.index or 0, max_train_batch=batch)
+    try:
+        rng = np.random.default_rng(1)
+        theta = (rng.uniform(-0.2, 0.2, 12993)).astype(np.float32)
+        cg.compton_mlp_set_params(ctx, theta)
+        r = torch.zeros(batch, device=dev)
+        cg.compton_kn_ratio(ctx, ut, kt, r)
+        peak = float(peaks.get("bf16_tflops", 1900.0))
+        for prec, mode in (("bf16", cg.MODE_MLP_BF16), ("fp32", cg.MODE_MLP_FP32)):
+            cg.compton_mlp_set_train_precision(ctx, mode)
+            for _ in range(2):
+                cg.compton_mlp_train_step(ctx, ut, kt, r, None, 1e-4, want_loss=False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                cg.compton_mlp_train_step(ctx, ut, kt, r, None, 1e-4, want_loss=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            tf = TRAIN_FLOPS_PER_SAMPLE * batch / (ms * 1e-3) / 1e12
+            out[prec] = {"ms_per_step": ms, "samples_per_s": batch / (ms * 1e-3), "tflops": tf,
+                         "frac_of_bf16_peak": tf / peak}
+        assert cg.compton_check(ctx) == cg.COMPTON_OK
+    finally:
+        cg.compton_destroy(ctx)
+    out["batch"] = batch
+    out["flops_per_sample"] = TRAIN_FLOPS_PER_SAMPLE
+    out["note"] = ("whole compton_mlp_train_step call (gradient kernels, Adam, repacking) on one batch; bf16 = "
+                   "tcgen05 tensor cores with BF16 operands and FP32 accumulation, fp32 = CUDA cores; peak: "
+                   "measured bf16 burst")
+    return out
 
 
 def train_pnet(cg, torch, ctx, dev, w_cell, p_max_cells, n_samples=1 << 20, steps=8000, batch=8192, lr=1e-2):
@@ -539,16 +597,37 @@ def train_pnet(cg, torch, ctx, dev, w_cell, p_max_cells, n_samples=1 << 20, step
         if loss is not None:
             losses.append(loss)
     torch.cuda.synchronize()
-    return {"steps": steps, "batch": batch, "lr": f"{lr} cosine-decayed to 0", "samples": n_samples,
+    return {"steps": steps, "batch": batch, "lr": f"{lr} cosine-decayed to 0",
+            "samples": n_samples,
             "loss": "MAE", "loss_first": losses[0], "loss_last": losses[-1], "train_s": time.time() - t0,
             "p_max": "per step, that of a random cell of the workload"}
 
 
-def run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step0, peaks):
+def dev_int32(torch, ptr, n):
+    """n int32 values at a raw device pointer, copied to the host."""
+    import ctypes
+    t = torch.empty(n, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    path = None
+    with open("/proc/self/maps") as f:
+        for line in f:
+            if "libcudart.so" in line:
+                path = line.split()[-1]
+                break
+    rt = ctypes.CDLL(path or "libcudart.so.13")
+    rc = rt.cudaMemcpy(ctypes.c_void_p(t.data_ptr()), ctypes.c_void_p(ptr), ctypes.c_size_t(4 * n), 3)
+    if rc != 0:
+        raise RuntimeError(f"cudaMemcpy failed: {rc}")
+    return t.cpu().numpy()
+
+
+def run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step0, peaks, with_oracle=False):
     """The whole step with the surrogate probability (BF16 tensor cores), its
     network kernel alone, and its error against the analytic path on the same
     pairs and draws."""
-    train = train_surrogate(cg, torch, ctx, dev, steps=args.train_steps, balanced=args.train_balanced)
+    train = train_surrogate(cg, torch, ctx, dev, steps=args.train_steps, balanced=args.train_balanced,
+                            precision=args.train_precision)
+    train["throughput"] = train_throughput(cg, torch, dev, peaks)
     mode = cg.MODE_MLP_BF16
     step = step0
 
@@ -557,20 +636,34 @@ def run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step0, peaks):
         cg.compton_scatter_step(ctx, dst[0], dst[1], pairs, md, st, prob, None, stream)
         return pairs
 
-    for _ in range(args.warmup):
-        one(bufs[step % 2], bufs[(step + 1) % 2], step, mode)
-        step += 1
-    torch.cuda.synchronize()
-    cg.compton_get_stats(ctx, reset=True)
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for _ in range(args.steps):
-        one(bufs[step % 2], bufs[(step + 1) % 2], step, mode)
-        step += 1
-    t1.record(stream)
-    torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
-    st = cg.compton_get_stats(ctx, reset=True)
+    # the plain and the surrogate step timed from the same particle state and
+    # step numbers (so the same pair lists and draws), with the same events
+    snap = [cg.Species(*(t.clone() for t in (sp.ux, sp.uy, sp.uz, sp.cell, sp.id))) for sp in bufs[step % 2]]
+
+    def restore():
+        for sp, sn in zip(bufs[step0 % 2], snap):
+            for a_, b_ in ((sp.ux, sn.ux), (sp.uy, sn.uy), (sp.uz, sn.uz), (sp.cell, sn.cell), (sp.id, sn.id)):
+                a_.copy_(b_)
+
+    def timed(md):
+        st_ = step0
+        for _ in range(args.warmup):
+            one(bufs[st_ % 2], bufs[(st_ + 1) % 2], st_, md)
+            st_ += 1
+        torch.cuda.synchronize()
+        cg.compton_get_stats(ctx, reset=True)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            one(bufs[st_ % 2], bufs[(st_ + 1) % 2], st_, md)
+            st_ += 1
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1), cg.compton_get_stats(ctx, reset=True), st_
+
+    ms_plain_same, st_plain_same, _ = timed(cg.MODE_PLAIN)
+    restore()
+    ms, st, step = timed(mode)
     # network kernel alone on 16.8M samples (electron/photon arrays as pairs)
     src = bufs[step % 2]
     n = min(src[0].n, src[1].n)
@@ -598,28 +691,51 @@ def run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step0, peaks):
                            for c in ("ux", "uy", "uz", "cell", "id")]) for d in (w.e, w.g)]
     scratch = [cg.Species.empty_like(sp) for sp in a_copy]
 
-    def scattered_spectrum(md, P_out, st=777):
+    n_sub = 1 << 20  # pairs compared with the FP64 oracle
+    sub = {}
+
+    def scattered_spectrum(md, P_out, st=777, name=None):
         pairs = cg.compton_bin_pairs(ctx, a_copy[0], a_copy[1], scratch[0], scratch[1], st, stream)
         torch.cuda.synchronize()
         before_g = torch.stack([scratch[1].ux, scratch[1].uy, scratch[1].uz]).clone()
+        if name is not None and "ig" not in sub:
+            # the first n_sub pairs of the step: their particles and densities
+            off_e = dev_int32(torch, pairs.off_e_dev, w.n_cells + 1).astype(np.int64)
+            off_g = dev_int32(torch, pairs.off_g_dev, w.n_cells + 1).astype(np.int64)
+            m = np.minimum(np.diff(off_e), np.diff(off_g))
+            pair_off = np.concatenate([[0], np.cumsum(m)])
+            ns = int(min(n_sub, pair_off[-1]))
+            cell = np.searchsorted(pair_off, np.arange(ns), side="right") - 1
+            j = np.arange(ns) - pair_off[cell]
+            sub["ie"], sub["ig"] = off_e[cell] + j, off_g[cell] + j
+            sub["dens"] = (np.maximum(np.diff(off_e), np.diff(off_g))[cell] * w.w_over_v).astype(np.float32)
+            ie_t = torch.from_numpy(sub["ie"]).to(dev)
+            ig_t = torch.from_numpy(sub["ig"]).to(dev)
+            sub["u"] = torch.stack([scratch[0].ux[ie_t], scratch[0].uy[ie_t], scratch[0].uz[ie_t]]).cpu().numpy()
+            sub["k"] = before_g[:, ig_t].cpu().numpy()
         cg.compton_scatter_step(ctx, scratch[0], scratch[1], pairs, md, st, P_out, None, stream)
         torch.cuda.synchronize()
         k_after = torch.stack([scratch[1].ux, scratch[1].uy, scratch[1].uz])
         hit = (k_after != before_g).any(dim=0)
+        if name is not None:
+            ig_t = torch.from_numpy(sub["ig"]).to(dev)
+            ns = sub["ig"].shape[0]
+            sub[name] = (P_out[:ns].double().cpu().numpy(), k_after[:, ig_t].double().cpu().numpy(),
+                         hit[ig_t].cpu().numpy())
         eps = k_after[:, hit].norm(dim=0).double().clamp_min(1e-12)
         h = torch.histc(eps.log10(), bins=64, min=-5.0, max=1.0)
         return h / h.sum().clamp_min(1.0), int(hit.sum())
 
     P_pl = torch.empty(n, device=dev)
     cg.compton_get_stats(ctx, reset=True)
-    h_pl, n_pl = scattered_spectrum(cg.MODE_PLAIN, P_pl)
+    h_pl, n_pl = scattered_spectrum(cg.MODE_PLAIN, P_pl, name="plain")
     np_pairs = int(cg.compton_get_stats(ctx, reset=True)["pairs_tested"])
     pl = P_pl[:np_pairs].double()
     err = {}
     for md, name in ((cg.MODE_MLP_BF16, "bf16"), (cg.MODE_MLP_FP8, "fp8"), (cg.MODE_MLP_FP32, "fp32")):
         P_ml = torch.empty(n, device=dev)
         cg.compton_get_stats(ctx, reset=True)
-        h_ml, n_ml = scattered_spectrum(md, P_ml)
+        h_ml, n_ml = scattered_spectrum(md, P_ml, name=name)
         fb_ml = cg.compton_get_stats(ctx, reset=True)["mlp_fallbacks"] / max(1, np_pairs)
         mlv = P_ml[:np_pairs].double()
         rel = ((mlv - pl).abs() / pl.clamp_min(1e-30))
@@ -631,6 +747,35 @@ def run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step0, peaks):
                                       "surrogate vs plain run on the same pairs and draws, the workload's initial "
                                       "particles"}
     err["mean_P_plain"] = float(pl.mean())
+    # every path against the FP64 oracle on the first 2^20 pairs of the same
+    # step and draws (part of the cpu_baseline leg: the oracle runs on the host)
+    vs_oracle = None
+    if with_oracle:
+        import oracle
+        t_or = time.time()
+        uo_o, ko_o, P_o, flag_o = oracle.pairs(sub["u"], sub["k"], sub["dens"], w.dt, w.seed, 777)
+        t_or = time.time() - t_or
+        hit_o = flag_o == 1
+
+        def spec(kk, hh):
+            e = np.linalg.norm(kk[:, hh], axis=0)
+            h, _ = np.histogram(np.log10(np.maximum(e, 1e-12)), bins=64, range=(-5.0, 1.0))
+            return h / max(1, h.sum())
+
+        s_o = spec(ko_o, hit_o)
+        vs_oracle = {"pairs": int(P_o.shape[0]), "oracle_seconds_one_core": t_or,
+                     "oracle_collisions": int(hit_o.sum()),
+                     "note": "the first 2^20 pairs of the workload's initial particles, same pair list, step and "
+                             "Philox draws; the oracle is FP64 on the host; flips = decisions that differ from "
+                             "the oracle's; spectrum = L1 of normalised 64-bin log10(eps) histograms of the "
+                             "scattered photons"}
+        for name in ("plain", "fp32", "bf16", "fp8"):
+            Pg, kg, hg = sub[name]
+            rel_o = np.abs(Pg - P_o) / np.maximum(P_o, 1e-30)
+            vs_oracle[name] = {"mean_rel_P": float(rel_o.mean()), "median_rel_P": float(np.median(rel_o)),
+                               "p99_rel_P": float(np.quantile(rel_o, 0.99)), "max_rel_P": float(rel_o.max()),
+                               "decision_flips": int((hg != hit_o).sum()), "collisions": int(hg.sum()),
+                               "spectrum_L1": float(np.abs(spec(kg, hg) - s_o).sum())}
     # sampling noise of the spectrum distance: two plain runs with other draws
     h_pl2, _ = scattered_spectrum(cg.MODE_PLAIN, torch.empty(n, device=dev), st=778)
     err["spectrum_L1_plain_vs_plain_other_draws"] = float((h_pl2 - h_pl).abs().sum())
@@ -639,7 +784,8 @@ def run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step0, peaks):
     # instead of momenta; the momentum network is restored afterwards
     blob = cg.compton_mlp_save(ctx)
     cg.compton_mlp_set_features(ctx, cg.FEATURES_INVARIANTS)
-    train_inv = train_surrogate(cg, torch, ctx, dev, steps=args.train_steps, balanced=args.train_balanced)
+    train_inv = train_surrogate(cg, torch, ctx, dev, steps=args.train_steps, balanced=args.train_balanced,
+                                precision=args.train_precision)
     P_iv = torch.empty(n, device=dev)
     h_iv, n_iv = scattered_spectrum(mode, P_iv)
     iv = P_iv[:np_pairs].double()
@@ -707,27 +853,29 @@ def run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step0, peaks):
             "spectrum_L1": float((h_pn - h_pl).abs().sum()), "train": train_pn}
     return {"mode": "bf16", "metric": METRIC, "value": st["pairs_tested"] / (ms * 1e-3), "unit": UNIT,
             "ms_per_step": ms / args.steps, "fallback_fraction": st["mlp_fallbacks"] / max(1, st["pairs_tested"]),
+            "gain_vs_plain": ms_plain_same / ms,
+            "gain_vs_plain_note": "plain step time over surrogate step time, both timed over the same steps from "
+                                  "the same particle state (same pair lists and draws), after the headline region "
+                                  f"(start step {step0}); the surrogate's fallback fraction is fallback_fraction",
+            "plain_ms_per_step_same_state": ms_plain_same / args.steps,
+            "plain_collisions_same_state": st_plain_same["scatters"], "collisions": st["scatters"],
             "network_kernel_ms": kern, "network_samples": n,
             "roofline": {"kernel": "k_mlp_tc<bf16>", "bound": "tensor", "achieved": achieved, "peak": peak_bf16,
                          "unit": "TFLOP/s", "frac": achieved / peak_bf16,
                          "note": "algorithmic FLOPs 2(6*64+3*64*64+64) per sample; peak: measured bf16 burst"},
-            "error_vs_plain": err, "train": train, "invariant_features": invariant, "paper_network": pnet}
+            "error_vs_plain": err, "error_vs_oracle": vs_oracle, "train": train, "invariant_features": invariant,
+            "paper_network": pnet}
 
 
-def run_serving(args, cg, torch, ctx, src, dev):
-    """Continuous batching: requests arrive as a Poisson stream at 200/s with
-    sizes log-uniform in [1e3, 1e7] pairs, each a slice of the device-resident
-    sorted particle arrays, half plain and half BF16 surrogate, admitted under
-    a 40 GB budget.  Latency = completion - scheduled arrival."""
-    rng = np.random.default_rng(4)
-    n_req = args.serve_requests
-    arrivals = np.cumsum(rng.exponential(1.0 / 200.0, n_req))
+def serve_stream(cg, torch, ctx, dev, u_pool, k_pool, rate, n_req, seed):
+    """Drive the serving engine with n_req requests arriving as a Poisson
+    stream at `rate` per second, sizes log-uniform in [1e3, 1e7] pairs, each a
+    slice of the device-resident particle pool, alternately plain and BF16
+    surrogate.  Latency = completion observed by poll - scheduled arrival."""
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
     sizes = np.floor(10 ** rng.uniform(3, 7, n_req)).astype(np.int64)
-    n_pool = min(src[0].n, src[1].n)
-    u_pool = torch.stack([src[0].ux[:n_pool], src[0].uy[:n_pool], src[0].uz[:n_pool]])
-    k_pool = torch.stack([src[1].ux[:n_pool], src[1].uy[:n_pool], src[1].uz[:n_pool]])
-    budget = 40 << 30
-    cg.compton_serve_start(ctx, budget, 1024)
+    n_pool = u_pool.shape[1]
     outs, pending, lat, pairs_done = {}, {}, [], 0
     t_start = time.perf_counter()
     i = 0
@@ -753,15 +901,55 @@ def run_serving(args, cg, torch, ctx, src, dev):
                 outs.pop(t)
         time.sleep(0.0002)
     wall = time.perf_counter() - t_start
-    info = cg.compton_serve_info(ctx)
-    cg.compton_serve_stop(ctx)
     lat_ms = np.array(lat) * 1e3
-    return {"requests": n_req, "arrival_rate_per_s": 200, "sizes": "log-uniform [1e3, 1e7] pairs",
-            "modes": "50/50 plain / bf16 surrogate", "budget_gb": budget / 2**30,
-            "peak_pool_gb": info["peak"] / 2**30, "p50_ms": float(np.percentile(lat_ms, 50)),
+    return {"arrival_rate_per_s": rate, "requests": n_req, "p50_ms": float(np.percentile(lat_ms, 50)),
             "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
             "pairs": int(pairs_done), "wall_s": wall, "pairs_per_s": pairs_done / wall,
             "offered_pairs_per_s": float(sizes.sum() / arrivals[-1])}
+
+
+def run_serving(args, cg, torch, ctx, src, dev):
+    """Continuous batching: requests arrive as a Poisson stream at 200/s with
+    sizes log-uniform in [1e3, 1e7] pairs, each a slice of the device-resident
+    sorted particle arrays, half plain and half BF16 surrogate, admitted under
+    a 40 GB budget.  Then a saturation sweep: the arrival rate doubles (400
+    requests per rate) until the engine no longer keeps up (served below 90 %
+    of the offered pairs/s) or p99 exceeds ten times the 200/s p99; the knee
+    is the highest rate that still kept up."""
+    n_pool = min(src[0].n, src[1].n)
+    u_pool = torch.stack([src[0].ux[:n_pool], src[0].uy[:n_pool], src[0].uz[:n_pool]])
+    k_pool = torch.stack([src[1].ux[:n_pool], src[1].uy[:n_pool], src[1].uz[:n_pool]])
+    budget = 40 << 30
+    cg.compton_serve_start(ctx, budget, 1024)
+    base = serve_stream(cg, torch, ctx, dev, u_pool, k_pool, 200.0, args.serve_requests, 4)
+    sweep, knee = [], None
+    if args.serve_requests >= 400:
+        rate = 400.0
+        while rate <= 51200.0:
+            r = serve_stream(cg, torch, ctx, dev, u_pool, k_pool, rate, 400, 40 + len(sweep))
+            r["kept_up"] = r["pairs_per_s"] >= 0.9 * r["offered_pairs_per_s"] and r["p99_ms"] <= 10.0 * base["p99_ms"]
+            sweep.append(r)
+            if not r["kept_up"]:
+                break
+            knee = r
+            rate *= 2.0
+    info = cg.compton_serve_info(ctx)
+    cg.compton_serve_stop(ctx)
+    out = {"requests": base["requests"], "arrival_rate_per_s": 200, "sizes": "log-uniform [1e3, 1e7] pairs",
+           "modes": "50/50 plain / bf16 surrogate", "budget_gb": budget / 2**30,
+           "peak_pool_gb": info["peak"] / 2**30}
+    out.update({k: base[k] for k in ("p50_ms", "p99_ms", "mean_ms", "pairs", "wall_s", "pairs_per_s",
+                                     "offered_pairs_per_s")})
+    out["saturation"] = {
+        "sweep": [{k: r[k] for k in ("arrival_rate_per_s", "offered_pairs_per_s", "pairs_per_s", "p50_ms", "p99_ms",
+                                     "kept_up")} for r in sweep],
+        "knee_rate_per_s": None if knee is None else knee["arrival_rate_per_s"],
+        "knee_pairs_per_s": None if knee is None else knee["pairs_per_s"],
+        "max_served_pairs_per_s": max([r["pairs_per_s"] for r in sweep], default=None),
+        "rule": "rate doubles from 400/s (400 requests each) until served < 0.9 x offered pairs/s or "
+                "p99 > 10 x the 200/s p99; knee = last rate that kept up; requests are driven by one host "
+                "thread polling every 0.2 ms"}
+    return out
 
 
 def run_e2e(args, cg, torch, ctx, w, stream, dev):
@@ -940,7 +1128,8 @@ def run_c5(args, rank: int, world: int, local_rank: int):
     total_ms, pairs_all = reduce_timing(total_ms, stats["pairs_tested"], dev)
     value = pairs_all / (total_ms * 1e-3)
 
-    train = train_surrogate(cg, torch, ctx, dev, steps=args.train_steps, balanced=args.train_balanced)
+    train = train_surrogate(cg, torch, ctx, dev, steps=args.train_steps, balanced=args.train_balanced,
+                            precision=args.train_precision)
 
     # the sweep: every mode takes the same state, pairing and draws
     X, Y = bufs[step % 2], bufs[(step + 1) % 2]
