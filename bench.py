@@ -213,7 +213,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    # weak scaling: rank r owns slab r of a grid of world * nx * ny cells
+    # (shard_cells), nx x ny cells drawn from the slab's own seed 2 + r; the
+    # slabs exchange nothing inside a step
+    from paper_2206_02937_gb300.dist import shard_cells
+    slab = shard_cells(world * args.nx * args.ny, rank, world)
     w = wl.c2(args.nx, args.ny, args.ppc, seed=2 + rank)
+    assert w.n_cells == slab[1] - slab[0]
     dev = torch.device("cuda", local_rank)
 
     def species(d):
@@ -1472,8 +1478,23 @@ def run_ic(args, rank: int, world: int, local_rank: int):
         print(json.dumps(line), flush=True)
 
 
+def spawn_ranks(n: int) -> int:
+    """`--gpus N` run without a launcher: start N ranks of this script with
+    torch.distributed.run on this node (127.0.0.1, a free port) and return
+    its exit status; rank 0 prints the line."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(spawn_ranks(args.gpus))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

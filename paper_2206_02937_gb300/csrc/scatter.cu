@@ -168,14 +168,11 @@ constexpr int kWarpCells = 64;                     // cells of a pair tile a war
 constexpr int kQueueCap = 192;                     // queued candidates per warp (see k_pair_prob)
 
 struct WarpWindow {
-    int32_t off[kWarpCells];  // first pair of each cell
-    int32_t es[kWarpCells];   // first sorted electron
-    int32_t gs[kWarpCells];   // first sorted photon
-    float dens[kWarpCells];   // pair density
-    uint32_t thr[kWarpCells]; // candidate threshold on the 24-bit uniform
-    // per group of four pairs of the tile (256): the window cell of its first
-    // pair, bit 7 set when the group runs past the end of that cell
-    uint8_t grp[kPairsPerTile / 4];
+    int32_t off[kWarpCells];    // first pair of each cell
+    int2 shift[kWarpCells];     // first sorted electron and photon minus the first pair
+    float dens[kWarpCells];     // pair density
+    uint32_t thr[kWarpCells];   // candidate threshold on the 24-bit uniform
+    uint8_t cell[kPairsPerTile];  // the window cell of each pair of the tile
 };
 
 struct WarpQueue {
@@ -302,25 +299,25 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
                     for (int i = (int)lane; i < nw; i += 32) {
                         const CellInfo c = a.cinfo[c_first + i];
                         W.off[i] = c.pair_off;
-                        W.es[i] = c.e_start;
-                        W.gs[i] = c.g_start;
+                        W.shift[i] = make_int2(c.e_start - c.pair_off, c.g_start - c.pair_off);
                         W.dens[i] = c.dens;
                         if (!kWeighted) W.thr[i] = cand_threshold(c.dens, a.dt);
                     }
                     __syncwarp();
-                    // the group map: cell i owns the groups whose first pair
-                    // lies in it, [ceil((o_i - q_t)/4), ceil((o_{i+1} - q_t)/4))
-                    // clipped to the tile; the last of them runs past the cell
-                    // unless the cell ends on a group boundary
+                    // the cell map: cell i owns the tile's pairs from its first
+                    // pair to the next cell's (clipped to the tile); the last
+                    // cell of the window owns the rest of the tile
                     const int q_t = t * kPairsPerTile;
                     for (int i = (int)lane; i < nw; i += 32) {
-                        const int o0 = W.off[i] - q_t;
-                        const int o1 = (i + 1 < nw ? W.off[i + 1] : q_t + kPairsPerTile + 4) - q_t;
-                        int g0 = (o0 + 3) >> 2, g1 = (o1 + 3) >> 2;
-                        g0 = g0 < 0 ? 0 : g0;
-                        g1 = g1 > kPairsPerTile / 4 ? kPairsPerTile / 4 : g1;
-                        for (int g = g0; g < g1; ++g)
-                            W.grp[g] = (uint8_t)(i | (4 * g + 4 > o1 ? 0x80 : 0));
+                        int o0 = W.off[i] - q_t;
+                        int o1 = i + 1 < nw ? W.off[i + 1] - q_t : kPairsPerTile;
+                        o0 = o0 < 0 ? 0 : o0;
+                        o1 = o1 > kPairsPerTile ? kPairsPerTile : o1;
+                        int q = o0;
+                        for (; q < o1 && (q & 3); ++q) W.cell[q] = (uint8_t)i;
+                        for (; q + 4 <= o1; q += 4)
+                            *reinterpret_cast<uint32_t*>(&W.cell[q]) = 0x01010101u * (uint32_t)i;
+                        for (; q < o1; ++q) W.cell[q] = (uint8_t)i;
                     }
                 }
                 __syncwarp();
@@ -328,21 +325,17 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
         }
         const bool local = nw <= kWarpCells;
         const CellInfo* cw = a.cinfo + c_first;  // the tile's cells in global memory (wide tiles)
+        // the window cells of the lane's four pairs, one byte each
+        const uint32_t cells4 =
+            (kBinned && local) ? *reinterpret_cast<const uint32_t*>(&W.cell[pb - (pidx)win_tile * kPairsPerTile]) : 0u;
         int ci = 0;
-        bool straddle = true;  // the lane's four pairs may span several cells
-        if (kBinned && pb < total) {
-            if (local) {
-                const uint32_t e = W.grp[(pb - (pidx)win_tile * kPairsPerTile) >> 2];
-                ci = (int)(e & 0x7Fu);
-                straddle = (e & 0x80u) != 0;
-            } else {
-                int lo = 0, hi = nw - 1;  // last cell whose first pair is <= pb
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (cw[mid].pair_off <= pb) lo = mid; else hi = mid - 1;
-                }
-                ci = lo;
+        if (kBinned && !local && pb < total) {
+            int lo = 0, hi = nw - 1;  // last cell whose first pair is <= pb
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (cw[mid].pair_off <= pb) lo = mid; else hi = mid - 1;
             }
+            ci = lo;
         }
         int cur = -1;
         int32_t c_off = 0, c_es = 0, c_gs = 0;
@@ -356,30 +349,25 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
             float dens = 0.0f;
             uint32_t thr = 0;
             if (valid) {
-                if (kBinned) {
-                    if (straddle) {
-                        if (local) {
-                            while (ci + 1 < nw && W.off[ci + 1] <= p) ++ci;
-                        } else {
-                            while (ci + 1 < nw && cw[ci + 1].pair_off <= p) ++ci;
-                        }
-                    }
+                if (kBinned && local) {
+                    // the same loads in every lane: no per-lane cell bookkeeping
+                    const int cr = (int)((cells4 >> (8 * r)) & 0xFFu);
+                    const int2 sh = W.shift[cr];
+                    ie = sh.x + (int)p;
+                    ig = sh.y + (int)p;
+                    dens = pair_density<kWeighted>(a, W.dens[cr], ie, ig);
+                    thr = kWeighted ? cand_threshold(dens, a.dt) : W.thr[cr];
+                } else if (kBinned) {
+                    // a tile of more cells than the window: cells in global memory
+                    while (ci + 1 < nw && cw[ci + 1].pair_off <= p) ++ci;
                     if (ci != cur) {
                         cur = ci;
-                        if (local) {
-                            c_off = W.off[ci];
-                            c_es = W.es[ci];
-                            c_gs = W.gs[ci];
-                            c_dens = W.dens[ci];
-                            if (!kWeighted) c_thr = W.thr[ci];
-                        } else {
-                            const CellInfo c = cw[ci];
-                            c_off = c.pair_off;
-                            c_es = c.e_start;
-                            c_gs = c.g_start;
-                            c_dens = c.dens;
-                            if (!kWeighted) c_thr = cand_threshold(c.dens, a.dt);
-                        }
+                        const CellInfo c = cw[ci];
+                        c_off = c.pair_off;
+                        c_es = c.e_start;
+                        c_gs = c.g_start;
+                        c_dens = c.dens;
+                        if (!kWeighted) c_thr = cand_threshold(c.dens, a.dt);
                     }
                     const int j = (int)(p - c_off);
                     ie = c_es + j;

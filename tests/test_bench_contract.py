@@ -43,3 +43,16 @@ def test_reference_arm_other_ranks_exit_without_work():
                   "--steps", "1", "--warmup", "3")
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [x for x in r.stdout.splitlines() if x.strip().startswith("{")]
+
+
+def test_gpus_n_without_launcher_starts_n_ranks():
+    """`--gpus 2` run directly starts two ranks itself (torch.distributed.run
+    on 127.0.0.1); exactly one line comes back, from rank 0, for two GPUs."""
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "3"], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.strip().startswith("{")]
+    assert len(lines) == 1
+    assert json.loads(lines[0])["n_gpus"] == 2
