@@ -796,19 +796,13 @@ def run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step0, peaks, with_oracl
     h_iv, n_iv = scattered_spectrum(mode, P_iv)
     iv = P_iv[:np_pairs].double()
     rel_iv = ((iv - pl).abs() / pl.clamp_min(1e-30))
-    for _ in range(args.warmup):
-        one(bufs[step % 2], bufs[(step + 1) % 2], step, mode)
-        step += 1
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        one(bufs[step % 2], bufs[(step + 1) % 2], step, mode)
-        step += 1
-    e1.record(stream)
-    torch.cuda.synchronize()
+    # timed like the momentum network: same state, steps and draws as the
+    # plain steps above
+    restore()
+    ms_iv, st_iv, step = timed(mode)
     invariant = {"features": "ln(x)/8, ln(v)/8 from the FP32 invariants", "mode": "bf16",
-                 "ms_per_step": e0.elapsed_time(e1) / args.steps,
+                 "ms_per_step": ms_iv / args.steps, "gain_vs_plain": ms_plain_same / ms_iv,
+                 "fallback_fraction": st_iv["mlp_fallbacks"] / max(1, st_iv["pairs_tested"]),
                  "mean_rel_P": float(rel_iv.mean()), "median_rel_P": float(rel_iv.median()),
                  "p99_rel_P": float(rel_iv[::4].float().quantile(0.99)),
                  "collision_rate_ratio": n_iv / max(1, n_pl),
