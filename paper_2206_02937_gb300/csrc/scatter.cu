@@ -427,18 +427,20 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
     }
 }
 
-// The collisions of the accepted pairs of k_pair_prob: one CTA per warp
-// region of the list (prob_warps regions, region w from pair index
-// chunk_begin(w) * 128 on, warp_acc[w] entries).
+// The collisions of the accepted pairs of k_pair_prob: one warp per region
+// of the list (prob_warps regions, region w from pair index
+// chunk_begin(w) * 128 on, warp_acc[w] entries), 32 at a time.
 __global__ void __launch_bounds__(128) k_collide_regions(ScatterArgs a, int prob_warps)
 {
     const int64_t total = a.n_pairs ? *a.n_pairs : a.p_end;
     const int64_t pbase = a.n_pairs ? 0 : a.p_begin;
     const int64_t n_chunks = total > pbase ? (total - pbase + kChunkPairs - 1) / kChunkPairs : 0;
-    for (int w = blockIdx.x; w < prob_warps; w += gridDim.x) {
+    const unsigned lane = threadIdx.x & 31u;
+    const int warps = (int)(gridDim.x * (blockDim.x >> 5));
+    for (int w = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); w < prob_warps; w += warps) {
         const uint32_t base = (uint32_t)(n_chunks * w / prob_warps) * kChunkPairs;
         const uint32_t n = a.warp_acc[w];
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) resolve(a, a.accepted[base + i]);
+        for (uint32_t i = lane; i < n; i += 32) resolve(a, a.accepted[base + i]);
     }
 }
 
@@ -822,8 +824,8 @@ compton_status launch_step(compton_ctx* ctx, ScatterArgs& a, compton_mode mode, 
         const int prob_warps = (int)grid * kProbWarps;
         {
             TimedScope ts_(ctx, COMPTON_K_COLLIDE, stream);
-            const int cgrid = collide_grid((int64_t)prob_warps * 128);
-            k_collide_regions<<<cgrid < prob_warps ? cgrid : prob_warps, 128, 0, stream>>>(a, prob_warps);
+            // one warp per region, four to a CTA
+            k_collide_regions<<<(prob_warps + 3) / 4, 128, 0, stream>>>(a, prob_warps);
         }
         COMPTON_LAUNCH_CHECK(ctx, "k_collide_regions");
         return COMPTON_OK;
