@@ -10,18 +10,17 @@
 //                each warp owns a contiguous run of 128-pair chunks (32 lanes
 //                x 4 consecutive pairs, one Philox block per lane for the
 //                four Bernoulli uniforms), stages the current pair tile's
-//                cells in its own shared-memory window, locates each pair's
-//                cell, and appends the pairs whose uniform lies below the
-//                probability bound (candidates, about a tenth) to its own
-//                queue; candidates are evaluated 32 at a time, one per lane,
-//                with a batch's momenta loads issued one chunk ahead:
-//                straight-line FP32 (x and v without cancellation, sigma_KN
-//                from its series, 1 - exp(-n dt s v)), with a second pass for
-//                the rare pairs (FP64 invariants above the gamma threshold,
-//                closed-form sigma_KN above the series range).  Accepted
-//                pairs are appended to a list in global memory
-//                (warp-aggregated atomics).  No CTA-wide barrier.
-//   k_collide    every accepted pair (a few percent of all pairs) at full
+//                cells and a per-pair cell map in its own shared-memory
+//                window, and queues the pairs whose uniform lies below the
+//                probability bound (candidates, about a tenth); candidates
+//                are evaluated 32 at a time, one per lane: straight-line FP32
+//                (x and v without cancellation, sigma_KN from its series or
+//                its closed form above x = 1, 1 - exp(-n dt s v)); the rare
+//                candidates above the FP64 gamma threshold are decided after
+//                the warp's last chunk.  Accepted pairs go to the warp's own
+//                region of the list.  No CTA-wide barrier, no shared counter.
+//   k_collide_regions (plain mode) / k_collide (surrogate modes)
+//                every accepted pair (a few percent of all pairs) at full
 //                warp width: inverse-CDF angle, rest-frame boost and momentum
 //                update (FP32, or FP64 above the configured gamma eps),
 //                write-back of both momenta in place.
@@ -60,6 +59,7 @@ struct ScatterArgs {
     // region of the list (from its first pair index on) and leaves the count
     // in warp_acc[warp]; the collision kernel walks the regions
     uint32_t* warp_acc;
+    CandPair* cand_rare;  // plain mode: the rare candidates of each warp's region
     CandPair* cand;
     uint32_t* n_cand;
     MlpDev mlp;  // the network's training range (surrogate modes)
@@ -154,18 +154,18 @@ __device__ __forceinline__ float analytic_P(const ScatterArgs& a, float ux, floa
 // (32 lanes x 4 consecutive pairs, one Philox block per lane), stages the
 // cells of the current pair tile in its own shared-memory window, and keeps
 // its own queue of candidates, so no warp ever waits for another at a barrier.
-// Per chunk (phase A): locate each pair's cell, draw the four Bernoulli words,
-// test them against the cell's integer threshold (the exact image of
-// u0 < P_b on the 24-bit uniform) and append the candidates to the queue.
-// Candidates are evaluated 32 at a time, one per lane (phase B): a batch is
-// taken from the queue and its momenta loads are issued before the next
-// chunk's phase A, and evaluated after it, so that the scattered loads
-// overlap the filtering; accepted pairs go to the global list
-// (warp-aggregated atomics).
+// Per chunk (phase A): locate each pair's cell (a per-pair cell map staged
+// with the tile), draw the four Bernoulli words, test them against the cell's
+// integer threshold (the exact image of u0 < P_b on the 24-bit uniform) and
+// append the candidates to the queue.  Candidates are evaluated 32 at a time,
+// one per lane (phase B), as soon as 32 are queued; other warps hide the
+// scattered loads.  Accepted pairs go to the warp's own region of the
+// accepted list.  Candidates above the FP64 gamma threshold are set aside and
+// decided after the warp's last chunk.
 constexpr int kProbWarps = kProbThreads / 32;
 constexpr int kChunkPairs = 32 * kPairsPerThread;  // pairs of one warp step
 constexpr int kWarpCells = 64;                     // cells of a pair tile a warp stages
-constexpr int kQueueCap = 192;                     // queued candidates per warp (see k_pair_prob)
+constexpr int kQueueCap = 160;                     // queued candidates per warp (31 + one chunk's 128)
 
 struct WarpWindow {
     int32_t off[kWarpCells];    // first pair of each cell
@@ -191,7 +191,7 @@ __device__ __forceinline__ uint32_t cand_threshold(float dens, float dt)
 }
 
 // One evaluation batch: up to 32 queue entries from slot `first` on, one
-// per lane, whose momenta loads have been issued into registers.
+// per lane, with their momenta.
 struct Batch {
     int n, first;  // entries, first slot (the same in every lane)
     float u[3], k[3];
@@ -221,14 +221,13 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
     int qh = 0, qn = 0;     // queue head and length (the same in every lane)
     // this warp's region of the accepted list: one slot per pair it owns
     const uint32_t acc_base = (uint32_t)ch_begin * kChunkPairs;
-    uint32_t n_acc = 0;
+    uint32_t n_acc = 0, n_rare = 0;
     int win_tile = -1;  // pair tile whose cells the window holds
     int c_first = 0, nw = 0;
 
-    // Take up to 32 candidates off the queue and issue their momenta loads.
-    // The entries stay in their slots until the batch is evaluated: a batch
-    // is taken with fewer than 32 entries left behind it, and the next chunk
-    // appends at most 128, so with 192 slots nothing overwrites it.
+    // Take up to 32 candidates off the queue and load their momenta.  The
+    // entries stay in their slots until the batch is evaluated; a chunk
+    // starts with fewer than 32 entries queued and appends at most 128.
     auto take = [&](Batch& b) {
         b.n = qn < 32 ? qn : 32;
         b.first = qh;
@@ -247,32 +246,41 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
         if (qh >= kQueueCap) qh -= kQueueCap;
         qn -= b.n;
     };
-    // probability, decision and accepted-list entry of a batch
+    // probability, decision and accepted-list entry of a batch; the rare
+    // candidates whose electron lies above the FP64 gamma threshold are set
+    // aside in the warp's region of the candidate list and decided after the
+    // warp's last chunk, so that the FP64 invariants stay out of the loop
     auto evaluate = [&](const Batch& b) {
-        bool hit = false;
+        bool hit = false, rare = false;
         float x = -1.0f;
         int32_t ie = 0, ig = 0;
         uint32_t p = 0;
+        float dens = 0.0f, u0 = 1.0f;
         if ((int)lane < b.n) {
             int slot = b.first + (int)lane;
             if (slot >= kQueueCap) slot -= kQueueCap;
             ie = Q.ie[slot];
             ig = Q.ig[slot];
             p = Q.p[slot];
-            const float dens = Q.dens[slot], u0 = Q.u0[slot];
+            dens = Q.dens[slot];
+            u0 = Q.u0[slot];
             const Invariants inv = invariants_f32(b.u[0], b.u[1], b.u[2], b.k[0], b.k[1], b.k[2]);
             x = inv.x;
-            float P;
-            if (inv.gamma > a.gamma64 || !(inv.x < 0.99f)) {
-                P = analytic_P(a, b.u[0], b.u[1], b.u[2], b.k[0], b.k[1], b.k[2], dens, &x);
-            } else {
-                const float Pr = one_minus_exp_neg(dens * a.dt * 0.375f * kn_F2_series(inv.x) * inv.v);
-                P = inv.eps > 0.0f ? Pr : 0.0f;
+            rare = inv.gamma > a.gamma64;
+            if (!rare) {
+                // sigma_KN from its series below x = 1, the closed form above
+                const float Pr = one_minus_exp_neg(dens * a.dt * 0.375f * kn_F2(inv.x) * inv.v);
+                const float P = inv.eps > 0.0f ? Pr : 0.0f;
+                hit = u0 < P;
+                if (a.prob_out) a.prob_out[p] = P;
+                if (a.flag_out) a.flag_out[p] = hit ? 1 : 0;
             }
-            hit = u0 < P;
-            if (a.prob_out) a.prob_out[p] = P;
-            if (a.flag_out) a.flag_out[p] = hit ? 1 : 0;
         }
+        const unsigned mr = __ballot_sync(0xffffffffu, rare);
+        if (rare)
+            a.cand_rare[acc_base + n_rare + __popc(mr & lt_mask)] =
+                CandPair{ie, ig, dens, u0, p, {b.u[0], b.u[1], b.u[2]}, {b.k[0], b.k[1], b.k[2]}, 0u};
+        n_rare += __popc(mr);
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit)
             a.accepted[acc_base + n_acc + __popc(m & lt_mask)] =
@@ -280,8 +288,6 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
         n_acc += __popc(m);
     };
 
-    Batch pend;
-    pend.n = 0;
     for (int ch = ch_begin; ch < ch_end; ++ch) {
         // ---------------- phase A: the chunk's 128 pairs ----------------
         const pidx q0 = pbase + (pidx)ch * kChunkPairs;
@@ -399,21 +405,39 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
         __syncwarp();  // the queue entries are visible to every lane
 
         // ---------------- phase B: candidates, 32 at a time ----------------
-        if (pend.n) evaluate(pend);  // its loads were issued before this chunk
-        while (qn >= 64) {           // only when most pairs are candidates
+        while (qn >= 32) {
             Batch b;
             take(b);
             evaluate(b);
         }
-        if (qn >= 32) take(pend);  // evaluated after the next chunk
-        else pend.n = 0;
         __syncwarp();  // slots evaluated above may be refilled by other lanes next
     }
-    if (pend.n) evaluate(pend);
     while (qn > 0) {
         Batch b;
         take(b);
         evaluate(b);
+    }
+
+    // the rare candidates set aside: the analytic probability with the FP64
+    // invariants and the closed-form cross section as they need
+    __syncwarp();
+    for (uint32_t i0 = 0; i0 < n_rare; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        bool hit = false;
+        float x = -1.0f;
+        CandPair c{};
+        if (i < n_rare) {
+            c = a.cand_rare[acc_base + i];
+            const float P = analytic_P(a, c.u[0], c.u[1], c.u[2], c.k[0], c.k[1], c.k[2], c.dens, &x);
+            hit = c.u0 < P;
+            if (a.prob_out) a.prob_out[c.p] = P;
+            if (a.flag_out) a.flag_out[c.p] = hit ? 1 : 0;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit)
+            a.accepted[acc_base + n_acc + __popc(m & lt_mask)] =
+                AcceptedPair{c.ie, c.ig, x, c.p, {c.u[0], c.u[1], c.u[2]}, {c.k[0], c.k[1], c.k[2]}, {0u, 0u}};
+        n_acc += __popc(m);
     }
 
     // counters: the warp's accepted count for the collision kernel, warp
@@ -785,6 +809,7 @@ void fill_common(ScatterArgs& a, compton_ctx* ctx, uint64_t seed, uint64_t step,
     a.accepted = ctx->accepted;
     a.n_accepted = ctx->n_accepted;
     a.warp_acc = ctx->warp_acc;
+    a.cand_rare = ctx->cand;
     a.cand = ctx->cand;
     a.n_cand = ctx->n_cand;
     a.mlp = ctx->mlp;
