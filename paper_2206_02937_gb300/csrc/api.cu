@@ -117,7 +117,6 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     size_t o_acc = cv.take<compton::AcceptedPair>(ctx->accepted_cap);
     size_t o_nacc = cv.take<uint32_t>(1);
     size_t o_wacc = cv.take<uint32_t>(compton::kMaxProbWarps);
-    size_t o_wcand = cv.take<uint32_t>(compton::kMaxProbWarps);
     size_t o_cand = cv.take<compton::CandPair>(ctx->accepted_cap);
     size_t o_ncand = cv.take<uint32_t>(1);
     size_t o_st = cv.take<compton::DeviceStats>(1);
@@ -162,7 +161,6 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     ctx->accepted = reinterpret_cast<compton::AcceptedPair*>(base + o_acc);
     ctx->n_accepted = reinterpret_cast<uint32_t*>(base + o_nacc);
     ctx->warp_acc = reinterpret_cast<uint32_t*>(base + o_wacc);
-    ctx->warp_cand = reinterpret_cast<uint32_t*>(base + o_wcand);
     ctx->cand = reinterpret_cast<compton::CandPair*>(base + o_cand);
     ctx->n_cand = reinterpret_cast<uint32_t*>(base + o_ncand);
     ctx->stats = reinterpret_cast<compton::DeviceStats*>(base + o_st);

@@ -168,7 +168,6 @@ struct compton_ctx {
     compton::AcceptedPair* accepted = nullptr;   // [accepted_cap] pairs that passed their trial
     uint32_t* n_accepted = nullptr;              // device scalar
     uint32_t* warp_acc = nullptr;                // [kMaxProbWarps] accepted pairs per probability region
-    uint32_t* warp_cand = nullptr;               // [kMaxProbWarps] candidates per probability region
     int64_t accepted_cap = 0;                    // max(max_particles, 2^20)
     compton::CandPair* cand = nullptr;           // [accepted_cap] candidates of the surrogate modes
     uint32_t* n_cand = nullptr;                  // device scalar
