@@ -39,7 +39,7 @@ MEASURED_TRAFFIC = {
     "k_sort_gather": ((134.694144e6 + 111.26272e6) / 8372876, "particle",
                       "profiles/k_sort_gather_in_place_256x256.md"),
     "k_count": (34.025984e6 / 8372876, "particle", "profiles/k_count_256x256.md"),
-    "k_pair_prob": ((97.662464e6 + 6.342656e6) / 4186438, "pair", "profiles/k_pair_prob_256x256.md"),
+    "k_pair_prob": ((97.137152e6 + 4.566784e6) / 4186438, "pair", "profiles/k_pair_prob_256x256.md"),
 }
 
 
