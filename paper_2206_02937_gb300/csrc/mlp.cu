@@ -25,6 +25,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include "act_math.cuh"
 #include "ctx.hpp"
 #include "device_math.cuh"
 #include "features.cuh"
@@ -49,8 +50,11 @@ constexpr uint32_t kOffSlot = kOffBar + 8 * kMlpGroups;  // TMEM address
 constexpr uint32_t kSmemTc = kOffSlot + 8 + 1024;       // + alignment slack
 
 constexpr uint64_t kWaitNs = 2000000000ull;             // 2 s bound on every wait
+// Of each 32 activations a thread finishes at once, the first 2 * kSiluFmaPairs
+// take SiLU on the FMA pipe (act::silu2_fma), the others tanh on the
+// multi-function unit (act::silu2_mufu), so that both units share the work.
+constexpr int kSiluFmaPairs = 0;
 
-__device__ __forceinline__ float silu_fast(float z) { return 0.5f * z * (1.0f + tc::tanh_approx(0.5f * z)); }
 __device__ __forceinline__ float silu_exact(float z) { return z / (1.0f + expf(-z)); }
 __device__ __forceinline__ float sigmoid_exact(float z) { return 1.0f / (1.0f + expf(-z)); }
 
@@ -271,7 +275,7 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_tc(MlpArgs a)
     const int g = tid >> 7;     // row group: its own tile, A buffer, TMEM columns and mbarrier
     const int lt = tid & 127;   // row within the group's tile
     uint8_t* Ah = sm + kOffA + g * 16384;
-    float* bias = reinterpret_cast<float*>(sm + kOffBias);
+    float* hbias = reinterpret_cast<float*>(sm + kOffBias);  // half the biases
     float* w4 = reinterpret_cast<float*>(sm + kOffW4);
     float* scale = reinterpret_cast<float*>(sm + kOffScale);  // [0..3] w scales, [4..7] 1/activation scales
     uint64_t* bar0 = reinterpret_cast<uint64_t*>(sm + kOffBar);
@@ -284,7 +288,7 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_tc(MlpArgs a)
     for (int i = tid; i < (int)(4 * kWTileBytes / 16); i += kMlpThreads) reinterpret_cast<uint4*>(Wt)[i] = wsrc[i];
     for (int i = tid; i < kMlpGroups * 16384 / 16; i += kMlpThreads)
         reinterpret_cast<uint4*>(sm + kOffA)[i] = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < 256; i += kMlpThreads) bias[i] = m.bias[i];
+    for (int i = tid; i < 256; i += kMlpThreads) hbias[i] = 0.5f * m.bias[i];  // SiLU takes h = z / 2
     if (tid < 64) w4[tid] = m.w4[tid];
     if (tid < 4) {
         scale[tid] = m.scale_w[tid];
@@ -341,7 +345,7 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_tc(MlpArgs a)
         group_sync(g);
         tc::fence_after_sync();
 
-        float acc_out = 0.0f;
+        uint64_t acc2 = act::pk2(0.0f, 0.0f);  // output layer, two partial sums
         for (int l = 0; l < 4; ++l) {
             if (lt == 0) {
                 const uint64_t ad = tc::sw128_kmajor_desc(sA);
@@ -360,22 +364,33 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_tc(MlpArgs a)
             phase ^= 1u;
             tc::fence_after_sync();
             if (ok) {
-                const float deq = kFp8 ? scale[l] / scale[4 + l] : 1.0f;  // w scale x activation scale
+                // h = z / 2 = (deq acc + b) / 2, SiLU in pairs of columns
+                const float hq = 0.5f * (kFp8 ? scale[l] / scale[4 + l] : 1.0f);  // w scale x activation scale
+                const uint64_t hq2 = act::pk2(hq, hq);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     float v[32];
                     tc::tmem_ld32(trow + 32 * h, v);
+                    const float4* hb = reinterpret_cast<const float4*>(hbias + l * 64 + 32 * h);
                     if (l < 3) {
                         const float snext = kFp8 ? scale[4 + l + 1] : 1.0f;
                         uint32_t pk[16];
 #pragma unroll
-                        for (int c = 0; c < 32; c += 2) {
-                            const float s0 = silu_fast(fmaf(v[c], deq, bias[l * 64 + 32 * h + c]));
-                            const float s1 = silu_fast(fmaf(v[c + 1], deq, bias[l * 64 + 32 * h + c + 1]));
-                            pk[c / 2] = pack_bf16x2(s0, s1);
-                            if (kFp8) {
-                                v[c] = s0 * snext;
-                                v[c + 1] = s1 * snext;
+                        for (int c4 = 0; c4 < 8; ++c4) {
+                            const float4 b = hb[c4];
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                const int c = 4 * c4 + 2 * q;
+                                const uint64_t h2 = act::fma2(act::pk2(v[c], v[c + 1]), hq2,
+                                                              q ? act::pk2(b.z, b.w) : act::pk2(b.x, b.y));
+                                const uint64_t y2 = (c / 2 < kSiluFmaPairs) ? act::silu2_fma(h2) : act::silu2_mufu(h2);
+                                float s0, s1;
+                                act::upk2(y2, s0, s1);
+                                pk[c / 2] = pack_bf16x2(s0, s1);
+                                if (kFp8) {
+                                    v[c] = s0 * snext;
+                                    v[c + 1] = s1 * snext;
+                                }
                             }
                         }
                         if (kFp8) {
@@ -396,10 +411,18 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_tc(MlpArgs a)
                                     make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
                         }
                     } else {
+                        const float4* w4v = reinterpret_cast<const float4*>(w4 + 32 * h);
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) {
-                            const float s = silu_fast(fmaf(v[c], deq, bias[3 * 64 + 32 * h + c]));
-                            acc_out = fmaf(s, w4[32 * h + c], acc_out);
+                        for (int c4 = 0; c4 < 8; ++c4) {
+                            const float4 b = hb[c4], w = w4v[c4];
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                const int c = 4 * c4 + 2 * q;
+                                const uint64_t h2 = act::fma2(act::pk2(v[c], v[c + 1]), hq2,
+                                                              q ? act::pk2(b.z, b.w) : act::pk2(b.x, b.y));
+                                const uint64_t y2 = (c / 2 < kSiluFmaPairs) ? act::silu2_fma(h2) : act::silu2_mufu(h2);
+                                acc2 = act::fma2(y2, q ? act::pk2(w.z, w.w) : act::pk2(w.x, w.y), acc2);
+                            }
                         }
                     }
                 }
@@ -413,6 +436,9 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_tc(MlpArgs a)
                 break;
             }
         }
+        float acc_lo, acc_hi;
+        act::upk2(acc2, acc_lo, acc_hi);
+        const float acc_out = acc_lo + acc_hi;
         if (a.decide) decide_row(a, row, !failed && row < n_rows, acc_out + b4, cur);
         else if (!failed && row < n_rows) a.r_out[row] = __fdividef(1.0f, 1.0f + __expf(-(acc_out + b4)));
     }
