@@ -387,7 +387,7 @@ __device__ __forceinline__ void collide_f32(float& ux, float& uy, float& uz, flo
     const float gamma = (1.0f + uu) * rg;
     const float ig2 = rg * rg;           // 1/gamma^2 = 1 - beta^2
     const float rk = rsqrtf(kk);
-    const float eps = kk * rk;
+    // the photon energy eps = kk rk enters only through x and the unit vector e
     const bool moving = uu > 0.0f;
     const float ru = moving ? rsqrtf(uu) : 0.0f;
     const float un = uu * ru;

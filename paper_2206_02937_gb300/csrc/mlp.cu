@@ -35,14 +35,23 @@ namespace compton {
 
 namespace {
 
-constexpr int kMlpGroups = 2;  // row groups (warpgroups) per CTA: one 128-row tile each, shared weights
+// Eight row groups (warpgroups) per CTA, one CTA per SM: each group its own
+// 128-row tile, A buffer, 64 TMEM columns and mbarrier, all sharing one copy
+// of the weights; 32 warps per SM at 64 registers hide the per-layer chain
+// (MMA, TMEM read, SiLU, A store, group barrier) best among the measured
+// shapes (2 groups x 3 CTAs 1.48 ms, 4 x 2 1.44, 6 x 1 1.34, 8 x 1 1.31 ms
+// for 16.8M samples in BF16).
+constexpr int kMlpGroups = 8;
+constexpr int kMlpMinCtas = 1;  // CTAs per SM the registers are budgeted for
 constexpr int kMlpThreads = 128 * kMlpGroups;
+constexpr uint32_t kMlpTmemCols = kMlpGroups <= 2 ? 128 : (kMlpGroups <= 4 ? 256 : 512);  // 64 per group, a power of 2
 constexpr int kTileM = 128;
 // shared-memory layout of the tensor-core kernels (base aligned to 1024 B)
 constexpr uint32_t kOffW = 0;                           // 4 weight tiles
 constexpr uint32_t kWTileBytes = 8192;                  // 64 rows x 128 B
 constexpr uint32_t kOffA = kOffW + 4 * kWTileBytes;     // A tiles (128 x 128 B each, one per group)
-constexpr uint32_t kOffBias = kOffA + 16384 * kMlpGroups;  // 4 x 64 floats
+constexpr uint32_t kOffRaw = kOffA + 16384 * kMlpGroups;  // next tile's momenta per group, [6][128] floats
+constexpr uint32_t kOffBias = kOffRaw + 6 * kTileM * 4 * kMlpGroups;  // 4 x 64 floats
 constexpr uint32_t kOffW4 = kOffBias + 1024;            // 64 floats
 constexpr uint32_t kOffScale = kOffW4 + 256;            // 8 floats
 constexpr uint32_t kOffBar = kOffScale + 32;            // one mbarrier per group
@@ -156,12 +165,12 @@ struct MlpArgs {
 };
 
 // Probability and decision of candidate row `row` from its network output
-// (pre-sigmoid z) and momenta q: P = 1 - exp(-2 n dt r) inside the network's
+// (pre-sigmoid z) and the momenta of its record: P = 1 - exp(-2 n dt r) inside the network's
 // training range (compton_mlp_set_range; by default gamma <= 1e3, eps in
 // [1e-4, 1]), else the analytic
 // probability (counted); accepted rows go to the list with their momenta.
 // Called by every thread of a warp.
-__device__ __forceinline__ void decide_row(const MlpArgs& a, int64_t row, bool live, float z, const float* q)
+__device__ __forceinline__ void decide_row(const MlpArgs& a, int64_t row, bool live, float z)
 {
     const unsigned lane = threadIdx.x & 31u;
     bool hit = false, fb = false;
@@ -170,14 +179,14 @@ __device__ __forceinline__ void decide_row(const MlpArgs& a, int64_t row, bool l
     if (live) {
         c = a.cand[row];
         const float r = __fdividef(1.0f, 1.0f + __expf(-z));
-        const float g2 = fmaf(q[0], q[0], fmaf(q[1], q[1], fmaf(q[2], q[2], 1.0f)));
-        const float e2 = fmaf(q[3], q[3], fmaf(q[4], q[4], q[5] * q[5]));
+        const float g2 = fmaf(c.u[0], c.u[0], fmaf(c.u[1], c.u[1], fmaf(c.u[2], c.u[2], 1.0f)));
+        const float e2 = fmaf(c.k[0], c.k[0], fmaf(c.k[1], c.k[1], c.k[2] * c.k[2]));
         float P;
         if (mlp_in_range(a.m, g2, e2)) {
             P = one_minus_exp_neg(2.0f * c.dens * a.dec.dt * r);
         } else {
             fb = true;
-            P = analytic_prob(q[0], q[1], q[2], q[3], q[4], q[5], c.dens, a.dec.dt, a.dec.gamma64, &x);
+            P = analytic_prob(c.u[0], c.u[1], c.u[2], c.k[0], c.k[1], c.k[2], c.dens, a.dec.dt, a.dec.gamma64, &x);
         }
         hit = c.u0 < P;
         if (a.dec.prob_out) a.dec.prob_out[c.p] = P;
@@ -191,7 +200,7 @@ __device__ __forceinline__ void decide_row(const MlpArgs& a, int64_t row, bool l
         at = __shfl_sync(0xffffffffu, at, 0);
         if (hit)
             a.accepted[at + __popc(m & ((1u << lane) - 1u))] =
-                AcceptedPair{c.ie, c.ig, x, c.p, {q[0], q[1], q[2]}, {q[3], q[4], q[5]}, {0u, 0u}};
+                AcceptedPair{c.ie, c.ig, x, c.p, {c.u[0], c.u[1], c.u[2]}, {c.k[0], c.k[1], c.k[2]}, {0u, 0u}};
     }
     if (lane == 0) {
         if (m) atomicAdd(&a.stats->scatters, (unsigned long long)__popc(m));
@@ -250,6 +259,37 @@ __device__ __forceinline__ void load_pair_features(const MlpArgs& a, int64_t row
     features(a.m, q[0], q[1], q[2], q[3], q[4], q[5], f);
 }
 
+// Asynchronous copy of pair `row`'s momenta (electron u, photon k) into the
+// staging column st[0], st[128], ..., st[640]; nothing past the end.
+__device__ __forceinline__ void stage_pair_raw(const MlpArgs& a, int64_t row, int64_t n_rows, float* st)
+{
+    if (row >= n_rows) return;
+    const float* src[6];
+    if (a.cand) {
+        const CandPair* c = a.cand + row;
+        src[0] = &c->u[0];
+        src[1] = &c->u[1];
+        src[2] = &c->u[2];
+        src[3] = &c->k[0];
+        src[4] = &c->k[1];
+        src[5] = &c->k[2];
+    } else {
+        int ie = (int)row, ig = (int)row;
+        if (a.cinfo) binned_pair(a, row, ie, ig);
+        src[0] = a.u[0] + ie;
+        src[1] = a.u[1] + ie;
+        src[2] = a.u[2] + ie;
+        src[3] = a.k[0] + ig;
+        src[4] = a.k[1] + ig;
+        src[5] = a.k[2] + ig;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const uint32_t d = tc::smem_u32(st + i * kTileM);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src[i]) : "memory");
+    }
+}
+
 // Barrier of the 128 threads of row group g (named barrier 1 + g), and the
 // same with an OR over their flags.
 __device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
@@ -266,7 +306,7 @@ __device__ __forceinline__ bool group_sync_or(int g, bool flag)
 }
 
 template <bool kFp8>
-__global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_tc(MlpArgs a)
+__global__ void __launch_bounds__(kMlpThreads, kMlpMinCtas) k_mlp_tc(MlpArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -275,6 +315,7 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_tc(MlpArgs a)
     const int g = tid >> 7;     // row group: its own tile, A buffer, TMEM columns and mbarrier
     const int lt = tid & 127;   // row within the group's tile
     uint8_t* Ah = sm + kOffA + g * 16384;
+    float* st = reinterpret_cast<float*>(sm + kOffRaw) + g * 6 * kTileM + lt;  // this row's staged momenta
     float* hbias = reinterpret_cast<float*>(sm + kOffBias);  // half the biases
     float* w4 = reinterpret_cast<float*>(sm + kOffW4);
     float* scale = reinterpret_cast<float*>(sm + kOffScale);  // [0..3] w scales, [4..7] 1/activation scales
@@ -300,7 +341,7 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_tc(MlpArgs a)
         tc::fence_barrier_init();
     }
     if (warp == 0) {
-        tc::tmem_alloc(slot, 64 * kMlpGroups);
+        tc::tmem_alloc(slot, kMlpTmemCols);
         tc::tmem_relinquish();
     }
     tc::fence_proxy_async_smem();
@@ -317,17 +358,18 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_tc(MlpArgs a)
     const int64_t n_rows = a.cand ? (int64_t)*a.n_cand : (a.cinfo ? *a.n_pairs : a.n);
     const int64_t n_tiles = (n_rows + kTileM - 1) / kTileM;
 
-    // the next tile's momenta are loaded while the current tile runs its layers
+    // the next tile's momenta are copied (cp.async, each thread its own row)
+    // into the group's staging columns while the current tile runs its layers
     const int64_t tile0 = (int64_t)blockIdx.x * kMlpGroups + g;
     const int64_t tstride = (int64_t)gridDim.x * kMlpGroups;
-    float raw[6];
-    load_pair_raw(a, tile0 * kTileM + lt, n_rows, raw);
+    if (tile0 < n_tiles) stage_pair_raw(a, tile0 * kTileM + lt, n_rows, st);
     for (int64_t tile = tile0; tile < n_tiles && !failed; tile += tstride) {
         const int64_t row = tile * kTileM + lt;
         float f[6] = {0, 0, 0, 0, 0, 0};
-        const float cur[6] = {raw[0], raw[1], raw[2], raw[3], raw[4], raw[5]};
-        if (row < n_rows) features(m, cur[0], cur[1], cur[2], cur[3], cur[4], cur[5], f);
-        if (tile + tstride < n_tiles) load_pair_raw(a, (tile + tstride) * kTileM + lt, n_rows, raw);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        if (row < n_rows)
+            features<true>(m, st[0], st[kTileM], st[2 * kTileM], st[3 * kTileM], st[4 * kTileM], st[5 * kTileM], f);
+        if (tile + tstride < n_tiles) stage_pair_raw(a, (tile + tstride) * kTileM + lt, n_rows, st);
         // layer-0 input: the 6 features in chunk 0 of the row, chunk 1 zeroed
         // (the single K step of layer 0 reads bytes 0..31 of the row)
         if (kFp8) {
@@ -364,68 +406,72 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_tc(MlpArgs a)
             phase ^= 1u;
             tc::fence_after_sync();
             if (ok) {
-                // h = z / 2 = (deq acc + b) / 2, SiLU in pairs of columns
+                // h = z / 2 = (deq acc + b) / 2, SiLU in pairs of columns; the
+                // accumulator is read 16 columns at a time, the next quarter's
+                // load in flight while the current one is finished
                 const float hq = 0.5f * (kFp8 ? scale[l] / scale[4 + l] : 1.0f);  // w scale x activation scale
                 const uint64_t hq2 = act::pk2(hq, hq);
+                const float snext = (kFp8 && l < 3) ? scale[4 + l + 1] : 1.0f;
+                const float* hb = hbias + l * 64;
+                // columns 16 qc .. 16 qc + 15 of the layer, from registers r
+                auto quarter = [&](int qc, uint32_t (&r)[16]) {
+                    const float4* hb4 = reinterpret_cast<const float4*>(hb + 16 * qc);
+                    uint32_t pk[8];
+                    float y[16];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    float v[32];
-                    tc::tmem_ld32(trow + 32 * h, v);
-                    const float4* hb = reinterpret_cast<const float4*>(hbias + l * 64 + 32 * h);
-                    if (l < 3) {
-                        const float snext = kFp8 ? scale[4 + l + 1] : 1.0f;
-                        uint32_t pk[16];
+                    for (int c4 = 0; c4 < 4; ++c4) {
+                        const float4 b = hb4[c4];
 #pragma unroll
-                        for (int c4 = 0; c4 < 8; ++c4) {
-                            const float4 b = hb[c4];
-#pragma unroll
-                            for (int q = 0; q < 2; ++q) {
-                                const int c = 4 * c4 + 2 * q;
-                                const uint64_t h2 = act::fma2(act::pk2(v[c], v[c + 1]), hq2,
-                                                              q ? act::pk2(b.z, b.w) : act::pk2(b.x, b.y));
-                                const uint64_t y2 = (c / 2 < kSiluFmaPairs) ? act::silu2_fma(h2) : act::silu2_mufu(h2);
-                                float s0, s1;
-                                act::upk2(y2, s0, s1);
-                                pk[c / 2] = pack_bf16x2(s0, s1);
-                                if (kFp8) {
-                                    v[c] = s0 * snext;
-                                    v[c + 1] = s1 * snext;
-                                }
-                            }
-                        }
-                        if (kFp8) {
-                            // 32 values -> 32 bytes = chunks 2h, 2h+1 of the 64-byte real half of the row
-#pragma unroll
-                            for (int q = 0; q < 2; ++q) {
-                                const uint4 val = make_uint4(
-                                    pack_e4m3x4(v[16 * q + 0], v[16 * q + 1], v[16 * q + 2], v[16 * q + 3]),
-                                    pack_e4m3x4(v[16 * q + 4], v[16 * q + 5], v[16 * q + 6], v[16 * q + 7]),
-                                    pack_e4m3x4(v[16 * q + 8], v[16 * q + 9], v[16 * q + 10], v[16 * q + 11]),
-                                    pack_e4m3x4(v[16 * q + 12], v[16 * q + 13], v[16 * q + 14], v[16 * q + 15]));
-                                *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(lt, 2 * h + q)) = val;
-                            }
-                        } else {
-#pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(lt, 4 * h + q)) =
-                                    make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-                        }
-                    } else {
-                        const float4* w4v = reinterpret_cast<const float4*>(w4 + 32 * h);
-#pragma unroll
-                        for (int c4 = 0; c4 < 8; ++c4) {
-                            const float4 b = hb[c4], w = w4v[c4];
-#pragma unroll
-                            for (int q = 0; q < 2; ++q) {
-                                const int c = 4 * c4 + 2 * q;
-                                const uint64_t h2 = act::fma2(act::pk2(v[c], v[c + 1]), hq2,
-                                                              q ? act::pk2(b.z, b.w) : act::pk2(b.x, b.y));
-                                const uint64_t y2 = (c / 2 < kSiluFmaPairs) ? act::silu2_fma(h2) : act::silu2_mufu(h2);
-                                acc2 = act::fma2(y2, q ? act::pk2(w.z, w.w) : act::pk2(w.x, w.y), acc2);
-                            }
+                        for (int q = 0; q < 2; ++q) {
+                            const int c = 4 * c4 + 2 * q;
+                            const uint64_t h2 =
+                                act::fma2(act::pk2(__uint_as_float(r[c]), __uint_as_float(r[c + 1])), hq2,
+                                          q ? act::pk2(b.z, b.w) : act::pk2(b.x, b.y));
+                            const uint64_t y2 =
+                                ((8 * qc + c / 2) % 16 < kSiluFmaPairs) ? act::silu2_fma(h2) : act::silu2_mufu(h2);
+                            act::upk2(y2, y[c], y[c + 1]);
                         }
                     }
-                }
+                    if (l < 3) {
+                        if (kFp8) {
+                            // 16 values -> 16 bytes = chunk qc of the 64-byte real half of the row
+                            *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(lt, qc)) = make_uint4(
+                                pack_e4m3x4(y[0] * snext, y[1] * snext, y[2] * snext, y[3] * snext),
+                                pack_e4m3x4(y[4] * snext, y[5] * snext, y[6] * snext, y[7] * snext),
+                                pack_e4m3x4(y[8] * snext, y[9] * snext, y[10] * snext, y[11] * snext),
+                                pack_e4m3x4(y[12] * snext, y[13] * snext, y[14] * snext, y[15] * snext));
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) pk[c] = pack_bf16x2(y[2 * c], y[2 * c + 1]);
+                            // 16 BF16 values = chunks 2 qc, 2 qc + 1 of the row
+                            *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(lt, 2 * qc)) =
+                                make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                            *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(lt, 2 * qc + 1)) =
+                                make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                        }
+                    } else {
+                        const float4* w4v = reinterpret_cast<const float4*>(w4 + 16 * qc);
+#pragma unroll
+                        for (int c4 = 0; c4 < 4; ++c4) {
+                            const float4 w = w4v[c4];
+                            acc2 = act::fma2(act::pk2(y[4 * c4], y[4 * c4 + 1]), act::pk2(w.x, w.y), acc2);
+                            acc2 = act::fma2(act::pk2(y[4 * c4 + 2], y[4 * c4 + 3]), act::pk2(w.z, w.w), acc2);
+                        }
+                    }
+                };
+                uint32_t ra[16], rb[16];
+                tc::tmem_ld16(trow + 0, ra);
+                tc::tmem_wait16(ra);
+                tc::tmem_ld16(trow + 16, rb);
+                quarter(0, ra);
+                tc::tmem_wait16(rb);
+                tc::tmem_ld16(trow + 32, ra);
+                quarter(1, rb);
+                tc::tmem_wait16(ra);
+                tc::tmem_ld16(trow + 48, rb);
+                quarter(2, ra);
+                tc::tmem_wait16(rb);
+                quarter(3, rb);
             }
             if (l < 3) tc::fence_proxy_async_smem();
             tc::fence_before_sync();
@@ -439,14 +485,15 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_tc(MlpArgs a)
         float acc_lo, acc_hi;
         act::upk2(acc2, acc_lo, acc_hi);
         const float acc_out = acc_lo + acc_hi;
-        if (a.decide) decide_row(a, row, !failed && row < n_rows, acc_out + b4, cur);
+        if (a.decide) decide_row(a, row, !failed && row < n_rows, acc_out + b4);
         else if (!failed && row < n_rows) a.r_out[row] = __fdividef(1.0f, 1.0f + __expf(-(acc_out + b4)));
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     if (failed && lt == 0) atomicOr(&a.stats->error_flags, (unsigned long long)kErrTimeout);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(*slot, 64 * kMlpGroups);
+    if (warp == 0) tc::tmem_dealloc(*slot, kMlpTmemCols);
 }
 
 // ---------------------------------------------------------------------------
