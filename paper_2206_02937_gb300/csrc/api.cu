@@ -124,6 +124,7 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     size_t o_th = cv.take<float>(NP), o_gr = cv.take<float>(NP), o_am = cv.take<float>(NP),
            o_av = cv.take<float>(NP);
     size_t o_wb = cv.take<uint8_t>(4 * 8192), o_w8 = cv.take<uint8_t>(4 * 8192), o_wt = cv.take<float>(4 * 4096);
+    size_t o_wh = cv.take<uint8_t>(4 * 8192 + 3 * 2048);
     size_t o_bi = cv.take<float>(256), o_w4 = cv.take<float>(64), o_b4 = cv.take<float>(1);
     size_t o_sw = cv.take<float>(4), o_swi = cv.take<float>(4), o_sai = cv.take<float>(4), o_lo = cv.take<float>(2),
            o_ax = cv.take<float>(4), o_ed = cv.take<float>(257), o_hi = cv.take<int>(256);
@@ -170,6 +171,7 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     m.adam_m = reinterpret_cast<float*>(base + o_am);
     m.adam_v = reinterpret_cast<float*>(base + o_av);
     m.wbf16 = base + o_wb;
+    m.whalf = base + o_wh;
     m.wfp8 = base + o_w8;
     m.wt32 = reinterpret_cast<float*>(base + o_wt);
     m.bias = reinterpret_cast<float*>(base + o_bi);

@@ -96,6 +96,9 @@ struct MlpDev {
     float* adam_m;       // [kMlpParams]
     float* adam_v;       // [kMlpParams]
     void* wbf16;         // 4 x 8 KB BF16 tiles, 128-byte swizzled K-major
+    void* whalf;         // inference image: 4 x 8 KB BF16 tiles of W / 2 (layer 0 with b / 2 as
+                         // hi + lo in K columns 6, 7), then 3 x 2 KB blocks of b / 2 (hi, lo in K
+                         // columns 0, 1) of layers 1-3, 32-byte swizzled K-major
     void* wfp8;          // 4 x 8 KB E4M3 tiles (K padded to 128)
     float* wt32;         // 4 x 64 x 64 transposed FP32 weights
     float* bias;         // 4 x 64

@@ -51,7 +51,9 @@ constexpr uint32_t kOffW = 0;                           // 4 weight tiles
 constexpr uint32_t kWTileBytes = 8192;                  // 64 rows x 128 B
 constexpr uint32_t kOffA = kOffW + 4 * kWTileBytes;     // A tiles (128 x 128 B each, one per group)
 constexpr uint32_t kOffRaw = kOffA + 16384 * kMlpGroups;  // next tile's momenta per group, [6][128] floats
-constexpr uint32_t kOffBias = kOffRaw + 6 * kTileM * 4 * kMlpGroups;  // 4 x 64 floats
+constexpr uint32_t kOffBB = kOffRaw + 6 * kTileM * 4 * kMlpGroups;  // BF16: half-bias blocks of layers 1-3
+constexpr uint32_t kOffOnes = kOffBB + 3 * 2048;        // BF16: A block of the bias step (1, 1 in K 0, 1)
+constexpr uint32_t kOffBias = kOffOnes + 4096;          // 4 x 64 floats (FP8: half biases)
 constexpr uint32_t kOffW4 = kOffBias + 1024;            // 64 floats
 constexpr uint32_t kOffScale = kOffW4 + 256;            // 8 floats
 constexpr uint32_t kOffBar = kOffScale + 32;            // one mbarrier per group
@@ -102,6 +104,26 @@ __global__ void k_mlp_pack(MlpDev m)
         *reinterpret_cast<__nv_bfloat16*>(base + tc::sw128_offset(n, k >> 3) + (k & 7) * 2) = v;
         // transposed FP32 copy for the CUDA-core path: wt[l][k][n]
         m.wt32[l * 4096 + k * 64 + n] = theta_w(th, l, n, k);
+        // inference image: W / 2 (exact), and in layer 0's padding columns
+        // 6, 7 the half bias as hi + lo (the A rows carry 1, 1 there)
+        uint8_t* hbase = reinterpret_cast<uint8_t*>(m.whalf) + l * kWTileBytes;
+        float hv = 0.5f * theta_w(th, l, n, k);
+        if (l == 0 && (k == 6 || k == 7)) {
+            const float hb = 0.5f * th[mlp_off_b(0) + n];
+            const float hi = __bfloat162float(__float2bfloat16_rn(hb));
+            hv = k == 6 ? hi : hb - hi;
+        }
+        *reinterpret_cast<__nv_bfloat16*>(hbase + tc::sw128_offset(n, k >> 3) + (k & 7) * 2) =
+            __float2bfloat16_rn(hv);
+    }
+    // half-bias blocks of layers 1-3: row n, K columns 0 (hi) and 1 (lo), zeros to 15
+    if (i < 3 * 64 * 16) {
+        const int l = 1 + i / 1024, n = (i / 16) % 64, k = i % 16;
+        uint8_t* bb = reinterpret_cast<uint8_t*>(m.whalf) + 4 * kWTileBytes + (l - 1) * 2048;
+        const float hb = 0.5f * th[mlp_off_b(l) + n];
+        const float hi = __bfloat162float(__float2bfloat16_rn(hb));
+        const float v = k == 0 ? hi : (k == 1 ? hb - hi : 0.0f);
+        *reinterpret_cast<__nv_bfloat16*>(bb + tc::sw32_offset(n, k >> 3) + (k & 7) * 2) = __float2bfloat16_rn(v);
     }
     // FP8 tiles: 4 x 64 rows x 128 B (K = 64 real + 64 zero)
     if (i < 4 * 64 * 128) {
@@ -325,8 +347,20 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpMinCtas) k_mlp_tc(MlpArgs a)
 
     const int warp = tid >> 5;
     const MlpDev& m = a.m;
-    const uint4* wsrc = reinterpret_cast<const uint4*>(kFp8 ? m.wfp8 : m.wbf16);
+    // BF16: the half-weight image with its half-bias blocks (the bias enters
+    // the MMA as one more K step against a block of ones, and the
+    // accumulator is h = z / 2 directly); FP8: weights, biases in the epilogue
+    const uint4* wsrc = reinterpret_cast<const uint4*>(kFp8 ? m.wfp8 : m.whalf);
     for (int i = tid; i < (int)(4 * kWTileBytes / 16); i += kMlpThreads) reinterpret_cast<uint4*>(Wt)[i] = wsrc[i];
+    if (!kFp8) {
+        for (int i = tid; i < 3 * 2048 / 16; i += kMlpThreads)
+            reinterpret_cast<uint4*>(sm + kOffBB)[i] = wsrc[4 * kWTileBytes / 16 + i];
+        // rows of the ones block: BF16 1.0 in K columns 0 and 1 (chunk 0 before the swizzle)
+        for (int r = tid; r < kTileM; r += kMlpThreads) {
+            *reinterpret_cast<uint4*>(sm + kOffOnes + tc::sw32_offset(r, 0)) = make_uint4(0x3F803F80u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(sm + kOffOnes + tc::sw32_offset(r, 1)) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
     for (int i = tid; i < kMlpGroups * 16384 / 16; i += kMlpThreads)
         reinterpret_cast<uint4*>(sm + kOffA)[i] = make_uint4(0, 0, 0, 0);
     for (int i = tid; i < 256; i += kMlpThreads) hbias[i] = 0.5f * m.bias[i];  // SiLU takes h = z / 2
@@ -378,8 +412,9 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpMinCtas) k_mlp_tc(MlpArgs a)
                 make_uint4(pack_e4m3x4(f[0] * s, f[1] * s, f[2] * s, f[3] * s), pack_e4m3x4(f[4] * s, f[5] * s, 0, 0),
                            0u, 0u);
         } else {
+            // K columns 6, 7 carry 1, 1: layer 0's half bias (hi, lo) sits there in W
             *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(lt, 0)) =
-                make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]), 0u);
+                make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]), 0x3F803F80u);
         }
         *reinterpret_cast<uint4*>(Ah + tc::sw128_offset(lt, 1)) = make_uint4(0u, 0u, 0u, 0u);
         tc::fence_proxy_async_smem();
@@ -388,6 +423,7 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpMinCtas) k_mlp_tc(MlpArgs a)
         tc::fence_after_sync();
 
         uint64_t acc2 = act::pk2(0.0f, 0.0f);  // output layer, two partial sums
+#pragma unroll
         for (int l = 0; l < 4; ++l) {
             if (lt == 0) {
                 const uint64_t ad = tc::sw128_kmajor_desc(sA);
@@ -400,6 +436,9 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpMinCtas) k_mlp_tc(MlpArgs a)
                     if (kFp8) tc::mma_f8(tmem, ad + 2 * ks, bd + 2 * ks, idesc, ks > 0);
                     else tc::mma_bf16(tmem, ad + 2 * ks, bd + 2 * ks, idesc, ks > 0);
                 }
+                if (!kFp8 && l > 0)  // the half bias: ones (K 0, 1) against (hi, lo)
+                    tc::mma_bf16(tmem, tc::sw32_kmajor_desc(sW + (kOffOnes - kOffW)),
+                                 tc::sw32_kmajor_desc(sW + (kOffBB - kOffW) + (l - 1) * 2048), idesc, 1u);
                 tc::mma_commit(bar);
             }
             const bool ok = tc::mbar_wait(bar, phase, kWaitNs);
@@ -420,13 +459,14 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpMinCtas) k_mlp_tc(MlpArgs a)
                     float y[16];
 #pragma unroll
                     for (int c4 = 0; c4 < 4; ++c4) {
-                        const float4 b = hb4[c4];
+                        const float4 b = kFp8 ? hb4[c4] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
                         for (int q = 0; q < 2; ++q) {
                             const int c = 4 * c4 + 2 * q;
+                            const uint64_t acc = act::pk2(__uint_as_float(r[c]), __uint_as_float(r[c + 1]));
+                            // BF16: the accumulator is h already; FP8: h = (deq acc + b) / 2
                             const uint64_t h2 =
-                                act::fma2(act::pk2(__uint_as_float(r[c]), __uint_as_float(r[c + 1])), hq2,
-                                          q ? act::pk2(b.z, b.w) : act::pk2(b.x, b.y));
+                                kFp8 ? act::fma2(acc, hq2, q ? act::pk2(b.z, b.w) : act::pk2(b.x, b.y)) : acc;
                             const uint64_t y2 =
                                 ((8 * qc + c / 2) % 16 < kSiluFmaPairs) ? act::silu2_fma(h2) : act::silu2_mufu(h2);
                             act::upk2(y2, y[c], y[c + 1]);

@@ -93,6 +93,22 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr)
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+// The same for a K-major tile in the 32-byte swizzle layout: rows of 32 bytes
+// (one K step of BF16), 8-row atoms of 256 bytes (stride byte offset 256),
+// the two 16-byte chunks of a row exchanged in rows 4-7 of each atom
+// (swizzle mode 6); the tile base must be 256-byte aligned.
+__device__ __forceinline__ uint64_t sw32_kmajor_desc(uint32_t saddr)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(256 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
+}
+
+// Byte offset of the 16-byte chunk c (0 or 1) of row r in a 32-byte-swizzled tile.
+__host__ __device__ __forceinline__ uint32_t sw32_offset(uint32_t r, uint32_t c)
+{
+    return r * 32u + (((c ^ (r >> 2)) & 1u) << 4);
+}
+
 // Byte offset of the 16-byte chunk c of row r in a 128-byte-swizzled tile.
 __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t c)
 {
