@@ -88,10 +88,12 @@ compton_status compton_init(const compton_config* cfg, compton_ctx** out)
     ctx->cfg = *cfg;
     ctx->last_error[0] = '\0';
     cudaError_t e = cudaSetDevice(cfg->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, cfg->device);
     if (e != cudaSuccess) {
         delete ctx;
         return COMPTON_ECUDA;
     }
+    if (ctx->n_sm < 1) ctx->n_sm = 1;
     const int64_t C = cfg->n_cells;
     const int64_t P = cfg->max_particles;
     ctx->max_scan_tiles = (C + compton::kScanTile - 1) / compton::kScanTile;

@@ -761,6 +761,9 @@ __global__ void __launch_bounds__(kSortThreads, 10) k_sort_gather(SortGatherArgs
     }
 }
 
+constexpr int kCountCtasPerSm = 16;
+constexpr int kPlaceCtasPerSm = 4;
+
 int grid_for(int64_t n, int threads, int max_blocks)
 {
     int64_t b = (n + threads - 1) / threads;
@@ -783,7 +786,10 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
                                           stream));
 
     const int64_t nmax = ne > ng ? ne : ng;
-    const dim3 cgrid(grid_for((nmax + 3) / 4, 256, 152 * 16), 2);  // four particles per thread
+    // grid-stride kernels: CTAs per SM of the histogram and the placement
+    // (one wave of 256-thread CTAs at full occupancy for the placement, whose
+    // early exit for input in cell order then costs one short wave)
+    const dim3 cgrid(grid_for((nmax + 3) / 4, 256, ctx->n_sm * kCountCtasPerSm), 2);  // four particles per thread
     {
         TimedScope ts_(ctx, COMPTON_K_COUNT, stream);
         k_count<<<cgrid, 256, 0, stream>>>(e_in->cell_dev, ne, g_in->cell_dev, ng, C, ctx->count[0], ctx->count[1],
@@ -824,7 +830,7 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
     scan_scope.end();
     COMPTON_LAUNCH_CHECK(ctx, "k_scan_final");
 
-    const dim3 pgrid(grid_for(nmax, 256, 152 * 16), 2);
+    const dim3 pgrid(grid_for(nmax, 256, ctx->n_sm * kPlaceCtasPerSm), 2);
     PlaceArgs pa;
     const compton_species* ins[2] = {e_in, g_in};
     compton_species* outs[2] = {e_out, g_out};

@@ -155,6 +155,7 @@ struct KernelTiming {
 struct compton_ctx {
     compton_config cfg;
     char last_error[256];
+    int n_sm = 1;  // multiprocessors of the context's device (grid sizes)
     // single device allocation carved into the buffers below
     void* arena = nullptr;
     size_t arena_bytes = 0;

@@ -295,7 +295,7 @@ compton_status launch_balance_weights(compton_ctx* ctx, const float* r, int64_t 
                                           cudaMemcpyHostToDevice, stream));
     COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->mlp.hist, 0, sizeof(int) * n_bins, stream));
     int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > (int64_t)ctx->n_sm * 8) blocks = (int64_t)ctx->n_sm * 8;
     k_balance_hist<<<(unsigned)blocks, 256, 0, stream>>>(r, n, ctx->mlp.edges, n_bins, ctx->mlp.hist);
     COMPTON_LAUNCH_CHECK(ctx, "k_balance_hist");
     k_balance_weights<<<(unsigned)blocks, 256, 0, stream>>>(r, n, ctx->mlp.edges, n_bins, ctx->mlp.hist, w_out);

@@ -451,9 +451,13 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
     }
 }
 
-// The collisions of the accepted pairs of k_pair_prob: one warp per region
-// of the list (prob_warps regions, region w from pair index
-// chunk_begin(w) * 128 on, warp_acc[w] entries), 32 at a time.
+// The collisions of the accepted pairs of k_pair_prob: the list has
+// prob_warps regions (region w from pair index chunk_begin(w) * 128 on,
+// warp_acc[w] entries); kCollideWarps warps share a region, taking its
+// entries 32 at a time in turn (one, two and four warps per region: 0.083,
+// 0.072 and 0.066 ms on the 512^2 step; the regions' lengths vary, and with
+// one warp each the longest set the kernel's time).
+constexpr int kCollideWarps = 4;
 __global__ void __launch_bounds__(128) k_collide_regions(ScatterArgs a, int prob_warps)
 {
     const int64_t total = a.n_pairs ? *a.n_pairs : a.p_end;
@@ -461,10 +465,13 @@ __global__ void __launch_bounds__(128) k_collide_regions(ScatterArgs a, int prob
     const int64_t n_chunks = total > pbase ? (total - pbase + kChunkPairs - 1) / kChunkPairs : 0;
     const unsigned lane = threadIdx.x & 31u;
     const int warps = (int)(gridDim.x * (blockDim.x >> 5));
-    for (int w = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); w < prob_warps; w += warps) {
+    for (int v = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); v < kCollideWarps * prob_warps;
+         v += warps) {
+        const int w = v / kCollideWarps;
         const uint32_t base = (uint32_t)(n_chunks * w / prob_warps) * kChunkPairs;
         const uint32_t n = a.warp_acc[w];
-        for (uint32_t i = lane; i < n; i += 32) resolve(a, a.accepted[base + i]);
+        for (uint32_t i = lane + 32u * (uint32_t)(v % kCollideWarps); i < n; i += 32u * kCollideWarps)
+            resolve(a, a.accepted[base + i]);
     }
 }
 
@@ -849,8 +856,8 @@ compton_status launch_step(compton_ctx* ctx, ScatterArgs& a, compton_mode mode, 
         const int prob_warps = (int)grid * kProbWarps;
         {
             TimedScope ts_(ctx, COMPTON_K_COLLIDE, stream);
-            // one warp per region, four to a CTA
-            k_collide_regions<<<(prob_warps + 3) / 4, 128, 0, stream>>>(a, prob_warps);
+            // kCollideWarps warps per region, four to a CTA
+            k_collide_regions<<<(kCollideWarps * prob_warps + 3) / 4, 128, 0, stream>>>(a, prob_warps);
         }
         COMPTON_LAUNCH_CHECK(ctx, "k_collide_regions");
         return COMPTON_OK;
@@ -981,7 +988,7 @@ compton_status launch_kn_ratio(compton_ctx* ctx, const float* ux, const float* u
                                cudaStream_t stream)
 {
     int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks > (int64_t)ctx->n_sm * 32) blocks = (int64_t)ctx->n_sm * 32;
     k_kn_ratio<<<(unsigned)blocks, 256, 0, stream>>>(ux, uy, uz, kx, ky, kz, n, ctx->cfg.gamma_fp64_threshold,
                                                      r_out);
     COMPTON_LAUNCH_CHECK(ctx, "k_kn_ratio");
@@ -992,7 +999,7 @@ compton_status launch_sample_angle(compton_ctx* ctx, const float* x, const uint3
                                    float* sth, float* ratio, cudaStream_t stream)
 {
     int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks > (int64_t)ctx->n_sm * 32) blocks = (int64_t)ctx->n_sm * 32;
     k_sample_angle<<<(unsigned)blocks, 256, 0, stream>>>(x, r, n, cth, sth, ratio);
     COMPTON_LAUNCH_CHECK(ctx, "k_sample_angle");
     return COMPTON_OK;
