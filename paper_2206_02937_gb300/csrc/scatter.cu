@@ -698,55 +698,88 @@ struct NtcArgs {
     uint64_t seed, step;
     float gamma64, collide64_sq;
     DeviceStats* stats;
+    uint32_t* next;  // next cell to take (zeroed before the launch)
 };
 
 __device__ __forceinline__ int pick_index(uint32_t w, int n) { return (int)(((uint64_t)w * (uint64_t)n) >> 32); }
 
+// NTC: every lane works through the candidates of whole cells in order,
+// taking the next cell from a shared counter when its cell is done, so that
+// a warp's lanes stay busy however unequal the cells' candidate counts are
+// (with one cell per thread the warp waited for its largest cell: the
+// candidate count grows with N_e N_g).  A cell's candidates run in sequence
+// in one lane, so the results do not depend on which lane takes the cell.
 __global__ void __launch_bounds__(256) k_ntc(NtcArgs a)
 {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
     unsigned long long n_cand = 0, n_coll = 0;
-    if (c < a.n_cells) {
-        const int e0 = a.off_e[c], ne = a.off_e[c + 1] - e0;
-        const int g0 = a.off_g[c], ng = a.off_g[c + 1] - g0;
-        if (ne > 0 && ng > 0) {
-            const Philox4 rc = draw(a.seed, a.step, 5u, (uint32_t)c);
-            const double expect = __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn((double)ne, (double)ng), a.w_over_v), 2.0),
-                                            a.dt);
-            const double uc = (double)(rc.r0 >> 8) * (1.0 / 16777216.0);
-            const int64_t nc = (int64_t)floor(__dadd_rn(expect, uc));
-            n_cand = (unsigned long long)nc;
-            for (int64_t j = 0; j < nc; ++j) {
-                const Philox4 q = draw(a.seed, a.step, 6u | ((uint32_t)j << 8), (uint32_t)c);
-                const int ie = e0 + pick_index(q.r0, ne);
-                const int ig = g0 + pick_index(q.r1, ng);
-                float ux = a.u[0][ie], uy = a.u[1][ie], uz = a.u[2][ie];
-                float kx = a.k[0][ig], ky = a.k[1][ig], kz = a.k[2][ig];
-                const Invariants inv = invariants_f32(ux, uy, uz, kx, ky, kz);
-                float x = inv.x, v = inv.v;
-                if (inv.gamma > a.gamma64) invariants_f64(ux, uy, uz, kx, ky, kz, &x, &v);
-                const float F2 = kn_F2(x);
-                const float ratio = inv.eps > 0.0f ? 0.5f * 0.375f * F2 * v : 0.0f;
-                if (!(u24_closed0(q.r2) < ratio)) continue;
-                const Philox4 z = draw(a.seed, a.step, 7u | ((uint32_t)j << 8), (uint32_t)c);
-                const Angle ang = kn_sample_angle(x, q.r3 >> 8, F2);
-                collide_pair(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(z.r0), a.collide64_sq);
-                a.u[0][ie] = ux;
-                a.u[1][ie] = uy;
-                a.u[2][ie] = uz;
-                a.k[0][ig] = kx;
-                a.k[1][ig] = ky;
-                a.k[2][ig] = kz;
-                ++n_coll;
+    int64_t c = 0, nc = 0, j = 0;
+    int e0 = 0, ne = 0, g0 = 0, ng = 0;
+    bool done = false;
+    for (;;) {
+        // lanes with no candidate left take the next cells, one atomic per warp
+        const bool need = !done && j >= nc;
+        const unsigned want = __ballot_sync(0xffffffffu, need);
+        if (want) {
+            const int leader = __ffs(want) - 1;
+            uint32_t base = 0;
+            if ((int)lane == leader) base = atomicAdd(a.next, (uint32_t)__popc(want));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (need) {
+                c = (int64_t)base + __popc(want & lt_mask);
+                j = 0;
+                nc = 0;
+                if (c >= a.n_cells) {
+                    done = true;
+                } else {
+                    e0 = a.off_e[c];
+                    ne = a.off_e[c + 1] - e0;
+                    g0 = a.off_g[c];
+                    ng = a.off_g[c + 1] - g0;
+                    if (ne > 0 && ng > 0) {
+                        const Philox4 rc = draw(a.seed, a.step, 5u, (uint32_t)c);
+                        const double expect =
+                            __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn((double)ne, (double)ng), a.w_over_v), 2.0), a.dt);
+                        const double uc = (double)(rc.r0 >> 8) * (1.0 / 16777216.0);
+                        nc = (int64_t)floor(__dadd_rn(expect, uc));
+                        n_cand += (unsigned long long)nc;
+                    }
+                }
             }
         }
+        if (__all_sync(0xffffffffu, done)) break;
+        if (done || j >= nc) continue;
+        const Philox4 q = draw(a.seed, a.step, 6u | ((uint32_t)j << 8), (uint32_t)c);
+        const int ie = e0 + pick_index(q.r0, ne);
+        const int ig = g0 + pick_index(q.r1, ng);
+        float ux = a.u[0][ie], uy = a.u[1][ie], uz = a.u[2][ie];
+        float kx = a.k[0][ig], ky = a.k[1][ig], kz = a.k[2][ig];
+        const Invariants inv = invariants_f32(ux, uy, uz, kx, ky, kz);
+        float x = inv.x, v = inv.v;
+        if (inv.gamma > a.gamma64) invariants_f64(ux, uy, uz, kx, ky, kz, &x, &v);
+        const float F2 = kn_F2(x);
+        const float ratio = inv.eps > 0.0f ? 0.5f * 0.375f * F2 * v : 0.0f;
+        if (u24_closed0(q.r2) < ratio) {
+            const Philox4 z = draw(a.seed, a.step, 7u | ((uint32_t)j << 8), (uint32_t)c);
+            const Angle ang = kn_sample_angle(x, q.r3 >> 8, F2);
+            collide_pair(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(z.r0), a.collide64_sq);
+            a.u[0][ie] = ux;
+            a.u[1][ie] = uy;
+            a.u[2][ie] = uz;
+            a.k[0][ig] = kx;
+            a.k[1][ig] = ky;
+            a.k[2][ig] = kz;
+            ++n_coll;
+        }
+        ++j;
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         n_cand += __shfl_xor_sync(0xffffffffu, n_cand, d);
         n_coll += __shfl_xor_sync(0xffffffffu, n_coll, d);
     }
-    if ((threadIdx.x & 31u) == 0) {
+    if (lane == 0) {
         if (n_cand) atomicAdd(&a.stats->pairs_tested, n_cand);
         if (n_coll) atomicAdd(&a.stats->scatters, n_coll);
     }
@@ -975,9 +1008,18 @@ compton_status launch_scatter_ntc(compton_ctx* ctx, compton_species* e, compton_
     a.gamma64 = ctx->cfg.gamma_fp64_threshold;
     a.collide64_sq = ctx->cfg.collide_fp64_threshold * ctx->cfg.collide_fp64_threshold;
     a.stats = ctx->stats;
+    a.next = ctx->n_cand;  // the candidate counter of the surrogate modes, free here
+    COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(a.next, 0, sizeof(uint32_t), stream));
+    // persistent: the CTAs resident at once (work is taken cell by cell)
+    int per_sm = 0;
+    COMPTON_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ntc, 256, 0));
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (int64_t)ctx->n_sm * per_sm;
+    const int64_t need = (pairs->n_cells + 255) / 256;
+    if (blocks > need) blocks = need;
     {
         TimedScope ts_(ctx, COMPTON_K_NTC, stream);
-        k_ntc<<<(unsigned)((pairs->n_cells + 255) / 256), 256, 0, stream>>>(a);
+        k_ntc<<<(unsigned)blocks, 256, 0, stream>>>(a);
     }
     COMPTON_LAUNCH_CHECK(ctx, "k_ntc");
     return COMPTON_OK;
