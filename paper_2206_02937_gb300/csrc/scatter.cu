@@ -699,7 +699,8 @@ struct NtcArgs {
     float gamma64, collide64_sq;
     DeviceStats* stats;
     uint32_t* next;      // next cell to take (zeroed before the launch)
-    int32_t* big;        // cells of at least kNtcBig candidates, for k_ntc_big
+    uint32_t* next_big;  // next listed cell to take (zeroed before the launch)
+    int32_t* big;        // cells of at least kNtcBig candidates
     uint32_t* n_big;     // their count (zeroed before the launch)
 };
 
@@ -713,22 +714,121 @@ __device__ __forceinline__ int32_t ntc_count(const NtcArgs& a, int32_t c, int ne
     return (int32_t)floor(__dadd_rn(expect, uc));
 }
 
-// Cells with at least this many candidates go to the warp-cooperative pass.
+// Cells with at least this many candidates are taken by a whole warp.
 constexpr int kNtcBig = 32;
 
 __device__ __forceinline__ int pick_index(uint32_t w, int n) { return (int)(((uint64_t)w * (uint64_t)n) >> 32); }
 
-// NTC: every lane works through the candidates of whole cells in order,
-// taking the next cell from a shared counter when its cell is done, so that
-// a warp's lanes stay busy however unequal the cells' candidate counts are
-// (with one cell per thread the warp waited for its largest cell: the
-// candidate count grows with N_e N_g).  A cell's candidates run in sequence
-// in one lane, so the results do not depend on which lane takes the cell.
+// NTC, first pass: every cell's candidate count; the cells of at least
+// kNtcBig candidates go to the list the warps of k_ntc take first.
+__global__ void __launch_bounds__(256) k_ntc_scan(NtcArgs a)
+{
+    unsigned long long n_cand = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.n_cells; c += stride) {
+        const int e0 = a.off_e[c], ne = a.off_e[c + 1] - e0;
+        const int g0 = a.off_g[c], ng = a.off_g[c + 1] - g0;
+        if (ne > 0 && ng > 0) {
+            const int32_t nc = ntc_count(a, (int32_t)c, ne, ng);
+            n_cand += (unsigned long long)nc;
+            if (nc >= kNtcBig) a.big[atomicAdd(a.n_big, 1u)] = (int32_t)c;
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) n_cand += __shfl_xor_sync(0xffffffffu, n_cand, d);
+    if ((threadIdx.x & 31u) == 0 && n_cand) atomicAdd(&a.stats->pairs_tested, n_cand);
+}
+
+// The candidates of cell c from candidate j0 on, by the whole warp, exact
+// and in order: the warp evaluates the next 32 candidates at once on the
+// momenta as they are; candidate k's evaluation is what the sequence would
+// give unless an earlier candidate of the batch was accepted and shares its
+// electron or photon.  The candidates before the first such k are final:
+// their accepted ones (which share no particle) collide and write back, and
+// the next batch starts at k with the updated momenta.
+__device__ __forceinline__ unsigned long long ntc_cell_warp(const NtcArgs& a, int32_t c)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned long long n_coll = 0;
+    const int e0 = a.off_e[c], ne = a.off_e[c + 1] - e0;
+    const int g0 = a.off_g[c], ng = a.off_g[c + 1] - g0;
+    const int32_t nc = ntc_count(a, c, ne, ng);
+    for (int32_t j0 = 0; j0 < nc;) {
+        const int32_t j = j0 + (int32_t)lane;
+        const bool valid = j < nc;
+        int ie = -1, ig = -1;
+        bool acc = false;
+        float ux = 0.0f, uy = 0.0f, uz = 0.0f, kx = 0.0f, ky = 0.0f, kz = 0.0f, x = 0.0f, F2 = 0.0f;
+        uint32_t r3 = 0;
+        if (valid) {
+            const Philox4 q = draw(a.seed, a.step, 6u | ((uint32_t)j << 8), (uint32_t)c);
+            ie = e0 + pick_index(q.r0, ne);
+            ig = g0 + pick_index(q.r1, ng);
+            ux = a.u[0][ie];
+            uy = a.u[1][ie];
+            uz = a.u[2][ie];
+            kx = a.k[0][ig];
+            ky = a.k[1][ig];
+            kz = a.k[2][ig];
+            const Invariants inv = invariants_f32(ux, uy, uz, kx, ky, kz);
+            float v = inv.v;
+            x = inv.x;
+            if (inv.gamma > a.gamma64) invariants_f64(ux, uy, uz, kx, ky, kz, &x, &v);
+            F2 = kn_F2(x);
+            const float ratio = inv.eps > 0.0f ? 0.5f * 0.375f * F2 * v : 0.0f;
+            acc = u24_closed0(q.r2) < ratio;
+            r3 = q.r3;
+        }
+        // the first candidate whose evaluation an earlier accepted one of the
+        // batch may have changed
+        bool stale = false;
+        const unsigned accm = __ballot_sync(0xffffffffu, acc);
+#pragma unroll 4
+        for (int i = 0; i < 31; ++i) {
+            const int iei = __shfl_sync(0xffffffffu, ie, i), igi = __shfl_sync(0xffffffffu, ig, i);
+            stale |= (int)lane > i && ((accm >> i) & 1u) && (iei == ie || igi == ig);
+        }
+        const unsigned sm = __ballot_sync(0xffffffffu, stale && valid);
+        const int nv = nc - j0 < 32 ? nc - j0 : 32;
+        const int kf = sm ? __ffs(sm) - 1 : nv;  // candidates j0 .. j0 + kf - 1 are final
+        if ((int)lane < kf && acc) {
+            const Philox4 z = draw(a.seed, a.step, 7u | ((uint32_t)j << 8), (uint32_t)c);
+            const Angle ang = kn_sample_angle(x, r3 >> 8, F2);
+            collide_pair(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(z.r0), a.collide64_sq);
+            a.u[0][ie] = ux;
+            a.u[1][ie] = uy;
+            a.u[2][ie] = uz;
+            a.k[0][ig] = kx;
+            a.k[1][ig] = ky;
+            a.k[2][ig] = kz;
+            ++n_coll;
+        }
+        __syncwarp();  // the next batch reads the momenta written here
+        j0 += kf;
+    }
+    return n_coll;
+}
+
+// NTC, second pass.  Warps first take the cells of many candidates from the
+// list, one cell per warp (ntc_cell_warp), so that the longest sequences
+// start at once; then every lane works through the candidates of the other
+// cells in order, taking the next cell from a shared counter when its cell
+// is done, so that a warp's lanes stay busy however unequal the cells'
+// candidate counts are.  A cell's candidates run in sequence, so the results
+// do not depend on which warp or lane takes the cell.
 __global__ void __launch_bounds__(256) k_ntc(NtcArgs a)
 {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
-    unsigned long long n_cand = 0, n_coll = 0;
+    unsigned long long n_coll = 0;
+    const uint32_t n_big = *a.n_big;
+    for (;;) {
+        uint32_t w = 0;
+        if (lane == 0) w = atomicAdd(a.next_big, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= n_big) break;
+        n_coll += ntc_cell_warp(a, a.big[w]);
+    }
     int64_t c = 0, nc = 0, j = 0;
     int e0 = 0, ne = 0, g0 = 0, ng = 0;
     bool done = false;
@@ -754,12 +854,7 @@ __global__ void __launch_bounds__(256) k_ntc(NtcArgs a)
                     ng = a.off_g[c + 1] - g0;
                     if (ne > 0 && ng > 0) {
                         nc = ntc_count(a, (int32_t)c, ne, ng);
-                        n_cand += (unsigned long long)nc;
-                        if (nc >= kNtcBig) {
-                            // a long sequence: the cooperative pass takes it
-                            a.big[atomicAdd(a.n_big, 1u)] = (int32_t)c;
-                            nc = 0;
-                        }
+                        if (nc >= kNtcBig) nc = 0;  // a listed cell: done above
                     }
                 }
             }
@@ -789,89 +884,6 @@ __global__ void __launch_bounds__(256) k_ntc(NtcArgs a)
             ++n_coll;
         }
         ++j;
-    }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        n_cand += __shfl_xor_sync(0xffffffffu, n_cand, d);
-        n_coll += __shfl_xor_sync(0xffffffffu, n_coll, d);
-    }
-    if (lane == 0) {
-        if (n_cand) atomicAdd(&a.stats->pairs_tested, n_cand);
-        if (n_coll) atomicAdd(&a.stats->scatters, n_coll);
-    }
-}
-
-// NTC for the cells of many candidates: one warp per cell, exact and in
-// order.  The warp evaluates the next 32 candidates at once on the momenta
-// as they are; candidate k's evaluation is what the sequence would give
-// unless an earlier candidate of the batch was accepted and shares its
-// electron or photon.  The candidates before the first such k are final:
-// their accepted ones (which share no particle) collide and write back, and
-// the next batch starts at k with the updated momenta.
-__global__ void __launch_bounds__(128) k_ntc_big(NtcArgs a)
-{
-    const unsigned lane = threadIdx.x & 31u;
-    const uint32_t n_big = *a.n_big;
-    unsigned long long n_coll = 0;
-    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
-    for (uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n_big; w += warps) {
-        const int32_t c = a.big[w];
-        const int e0 = a.off_e[c], ne = a.off_e[c + 1] - e0;
-        const int g0 = a.off_g[c], ng = a.off_g[c + 1] - g0;
-        const int32_t nc = ntc_count(a, c, ne, ng);
-        for (int32_t j0 = 0; j0 < nc;) {
-            const int32_t j = j0 + (int32_t)lane;
-            const bool valid = j < nc;
-            int ie = -1, ig = -1;
-            bool acc = false;
-            float ux = 0.0f, uy = 0.0f, uz = 0.0f, kx = 0.0f, ky = 0.0f, kz = 0.0f, x = 0.0f, F2 = 0.0f;
-            uint32_t r3 = 0;
-            if (valid) {
-                const Philox4 q = draw(a.seed, a.step, 6u | ((uint32_t)j << 8), (uint32_t)c);
-                ie = e0 + pick_index(q.r0, ne);
-                ig = g0 + pick_index(q.r1, ng);
-                ux = a.u[0][ie];
-                uy = a.u[1][ie];
-                uz = a.u[2][ie];
-                kx = a.k[0][ig];
-                ky = a.k[1][ig];
-                kz = a.k[2][ig];
-                const Invariants inv = invariants_f32(ux, uy, uz, kx, ky, kz);
-                float v = inv.v;
-                x = inv.x;
-                if (inv.gamma > a.gamma64) invariants_f64(ux, uy, uz, kx, ky, kz, &x, &v);
-                F2 = kn_F2(x);
-                const float ratio = inv.eps > 0.0f ? 0.5f * 0.375f * F2 * v : 0.0f;
-                acc = u24_closed0(q.r2) < ratio;
-                r3 = q.r3;
-            }
-            // the first candidate whose evaluation an earlier accepted one of
-            // the batch may have changed
-            bool stale = false;
-            const unsigned accm = __ballot_sync(0xffffffffu, acc);
-#pragma unroll 4
-            for (int i = 0; i < 31; ++i) {
-                const int iei = __shfl_sync(0xffffffffu, ie, i), igi = __shfl_sync(0xffffffffu, ig, i);
-                stale |= (int)lane > i && ((accm >> i) & 1u) && (iei == ie || igi == ig);
-            }
-            const unsigned sm = __ballot_sync(0xffffffffu, stale && valid);
-            const int nv = nc - j0 < 32 ? nc - j0 : 32;
-            const int kf = sm ? __ffs(sm) - 1 : nv;  // candidates j0 .. j0 + kf - 1 are final
-            if ((int)lane < kf && acc) {
-                const Philox4 z = draw(a.seed, a.step, 7u | ((uint32_t)j << 8), (uint32_t)c);
-                const Angle ang = kn_sample_angle(x, r3 >> 8, F2);
-                collide_pair(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(z.r0), a.collide64_sq);
-                a.u[0][ie] = ux;
-                a.u[1][ie] = uy;
-                a.u[2][ie] = uz;
-                a.k[0][ig] = kx;
-                a.k[1][ig] = ky;
-                a.k[2][ig] = kz;
-                ++n_coll;
-            }
-            __syncwarp();  // the next batch reads the momenta written here
-            j0 += kf;
-        }
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) n_coll += __shfl_xor_sync(0xffffffffu, n_coll, d);
@@ -1101,13 +1113,14 @@ compton_status launch_scatter_ntc(compton_ctx* ctx, compton_species* e, compton_
     a.gamma64 = ctx->cfg.gamma_fp64_threshold;
     a.collide64_sq = ctx->cfg.collide_fp64_threshold * ctx->cfg.collide_fp64_threshold;
     a.stats = ctx->stats;
-    // scratch free in this mode: the candidate and accepted counters of the
-    // scatter step, and an electron count array (zeroed by the next binning)
-    a.next = ctx->n_cand;
-    a.n_big = ctx->n_accepted;
+    // scratch free in this mode: the count arrays of the binning (zeroed by
+    // the next binning), each of at least max(C, 64) entries: the listed
+    // cells in the electron array, three counters in the photon array
+    a.next = reinterpret_cast<uint32_t*>(ctx->count[1]);
+    a.next_big = a.next + 1;
+    a.n_big = a.next + 2;
     a.big = ctx->count[0];
-    COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(a.next, 0, sizeof(uint32_t), stream));
-    COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(a.n_big, 0, sizeof(uint32_t), stream));
+    COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(a.next, 0, 3 * sizeof(uint32_t), stream));
     // persistent: the CTAs resident at once (work is taken cell by cell)
     int per_sm = 0;
     COMPTON_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ntc, 256, 0));
@@ -1117,9 +1130,10 @@ compton_status launch_scatter_ntc(compton_ctx* ctx, compton_species* e, compton_
     if (blocks > need) blocks = need;
     {
         TimedScope ts_(ctx, COMPTON_K_NTC, stream);
+        int64_t sb = (pairs->n_cells + 255) / 256;
+        if (sb > (int64_t)ctx->n_sm * 8) sb = (int64_t)ctx->n_sm * 8;
+        k_ntc_scan<<<(unsigned)sb, 256, 0, stream>>>(a);
         k_ntc<<<(unsigned)blocks, 256, 0, stream>>>(a);
-        // the cells of many candidates, a warp each (grid: a few warps per SM)
-        k_ntc_big<<<(unsigned)(ctx->n_sm * 8), 128, 0, stream>>>(a);
     }
     COMPTON_LAUNCH_CHECK(ctx, "k_ntc");
     return COMPTON_OK;
