@@ -384,7 +384,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
            "candidates_per_s": st_ntc["pairs_tested"] / args.steps / (ntc_ms * 1e-3),
            "collisions_per_step": st_ntc["scatters"] / args.steps,
            "collision_ratio_ntc_to_pairing_same_state": same["ntc"] / max(1, same["pairing"]),
-           "note": "bin + NTC candidates per cell (one thread per cell, sequential in-cell updates); the ratio "
+           "note": "bin + NTC candidates per cell (each cell's candidates in order: cells of 32 or more a warp each, the others a lane each from a shared queue); the ratio "
                    "compares both schemes on the same binned particles over 3 draws (NTC uses the linear "
                    "probability, pairing 1 - exp(-a): expected about 1 + n dt <s v>/2)"}
 
