@@ -176,10 +176,10 @@ __global__ void __launch_bounds__(256) k_scan_reduce(const int32_t* __restrict__
                                                      const int32_t* __restrict__ count_g, int64_t C,
                                                      int64_t* __restrict__ block_sums, int64_t n_tiles)
 {
-    const int64_t c0 = (int64_t)blockIdx.x * kScanTile + threadIdx.x * 8;
+    const int64_t c0 = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanPer;
     Tri v{0, 0, 0};
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < kScanPer; ++j) {
         const int64_t c = c0 + j;
         if (c < C) {
             const int64_t a = count_e[c], b = count_g[c];
@@ -265,11 +265,11 @@ __device__ __forceinline__ void write_sort_tiles(int32_t* stile, int64_t nb, int
 
 __global__ void __launch_bounds__(256) k_scan_final(ScanFinalArgs a)
 {
-    const int64_t c0 = (int64_t)blockIdx.x * kScanTile + threadIdx.x * 8;
-    int32_t ne[8], ng[8];
+    const int64_t c0 = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+    int32_t ne[kScanPer], ng[kScanPer];
     Tri v{0, 0, 0};
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < kScanPer; ++j) {
         const int64_t c = c0 + j;
         ne[j] = c < a.C ? a.count_e[c] : 0;
         ng[j] = c < a.C ? a.count_g[c] : 0;
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(256) k_scan_final(ScanFinalArgs a)
     const int64_t np_total = *a.n_pairs;
     const int64_t n_pair_tiles = (np_total + kPairsPerTile - 1) / kPairsPerTile;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < kScanPer; ++j) {
         const int64_t c = c0 + j;
         if (c >= a.C) break;
         const int64_t m = ne[j] < ng[j] ? ne[j] : ng[j];
