@@ -92,3 +92,26 @@ def test_ntc_rate_matches_pairing():
     # higher by about n dt <s v> / 2 (~2.5 % here)
     ratio = n_ntc / n_pair
     assert 0.995 <= ratio < 1.06, ratio
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_ntc_long_cells(seed):
+    """Cells of 32 and more candidates take the warp-cooperative path (32
+    candidates evaluated at once, the batch cut at the first candidate an
+    earlier accepted one could have changed).  Cells of few particles and many
+    candidates repeat particles within a batch all the time, so the cut is
+    exercised; the results must still be those of the in-order sequence."""
+    rng = wl.rng_for(40 + seed)
+    sizes = [(4, 5), (1, 1), (30, 40), (12, 3), (0, 5), (8, 9), (3, 2), (2, 60)]
+    ce = np.concatenate([np.full(ne, c) for c, (ne, _) in enumerate(sizes)])
+    cg_ = np.concatenate([np.full(ng, c) for c, (_, ng) in enumerate(sizes)])
+    e = wl._species(3.0 * wl.isotropic(rng, ce.size), ce)
+    g = wl._species(0.3 * wl.isotropic(rng, cg_.size), cg_)
+    # 2 n dt N_e N_g candidates per cell with w/V = 20, dt = 0.05: 2 N_e N_g
+    w = wl.Workload("long cells", len(sizes), 20.0, 0.05, 50 + seed, 1, e, g)
+    st, o = _compare(w, seed)
+    counts = np.asarray(o["n_cand"]) if "n_cand" in o else None
+    assert st["pairs_tested"] >= 2 * (30 * 40)
+    assert o["n_coll"].sum() > 100
+    if counts is not None:
+        assert (counts >= 32).sum() >= 4
