@@ -36,9 +36,9 @@ L2_NOTE = "inputs larger than L2 (particle state ~1.3 GB resident, 129 MB L2)"
 # is now, scaled to a launch by its units; the profile file gives the command.
 # A kernel changed since its capture must be taken out of this table.
 MEASURED_TRAFFIC = {
-    "k_sort_gather": ((134.694144e6 + 111.26272e6) / 8372876, "particle",
+    "k_sort_gather": ((134.677504e6 + 111.480576e6) / 8372876, "particle",
                       "profiles/k_sort_gather_in_place_256x256.md"),
-    "k_count": (34.025984e6 / 8372876, "particle", "profiles/k_count_256x256.md"),
+    "k_count": (34.025472e6 / 8372876, "particle", "profiles/k_count_256x256.md"),
     "k_pair_prob": ((97.137152e6 + 4.566784e6) / 4186438, "pair", "profiles/k_pair_prob_256x256.md"),
 }
 
