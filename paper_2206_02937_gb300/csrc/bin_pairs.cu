@@ -38,7 +38,8 @@ __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 // unsorted[s] is set if a cell index descends or lies outside [0, C): only
 // then does the placement run.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int4 load_cells4(const int32_t* __restrict__ cell, int64_t i, int64_t n, bool vec)
+template <typename Idx>
+__device__ __forceinline__ int4 load_cells4(const int32_t* __restrict__ cell, Idx i, Idx n, bool vec)
 {
     if (vec && i + 3 < n) return *reinterpret_cast<const int4*>(cell + i);  // 16-byte aligned: i % 4 == 0
     int4 v = make_int4(-1, -1, -1, -1);
@@ -49,29 +50,32 @@ __device__ __forceinline__ int4 load_cells4(const int32_t* __restrict__ cell, in
     return v;
 }
 
+// Positions in Idx: 32-bit when every position the grid visits fits (the
+// launch checks), else 64-bit.
+template <typename Idx>
 __global__ void k_count(const int32_t* __restrict__ cell_e, int64_t n_e, const int32_t* __restrict__ cell_g,
                         int64_t n_g, int64_t C, int32_t* __restrict__ count_e, int32_t* __restrict__ count_g,
                         int32_t* __restrict__ unsorted, DeviceStats* stats)
 {
     const int s = blockIdx.y;
     const int32_t* __restrict__ cell = s == 0 ? cell_e : cell_g;
-    const int64_t n = s == 0 ? n_e : n_g;
+    const Idx n = (Idx)(s == 0 ? n_e : n_g);
     int32_t* __restrict__ count = s == 0 ? count_e : count_g;
     const unsigned lane = lane_id();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
-    const int64_t n_round = (n + 127) / 128 * 128;  // whole warps in every iteration
+    const Idx stride = (Idx)gridDim.x * (Idx)blockDim.x * 4;
+    const Idx n_round = (n + 127) / 128 * 128;  // whole warps in every iteration
     const bool vec = (reinterpret_cast<uintptr_t>(cell) & 15u) == 0;
     // cell indices are int32, so C above 2^31 admits every non-negative one
     const uint32_t C32 = C > 0x80000000ll ? 0x80000000u : (uint32_t)C;
     bool disorder = false, bad = false;
     // the next group's loads are issued before this group is processed, so
     // two groups per thread are in flight
-    auto edge = [&](int64_t j0) -> int32_t {
+    auto edge = [&](Idx j0) -> int32_t {
         if (lane == 0) return (j0 > 0 && j0 - 1 < n) ? cell[j0 - 1] : -1;
         if (lane == 31) return j0 + 4 < n ? cell[j0 + 4] : -1;
         return -1;
     };
-    int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    Idx i0 = ((Idx)blockIdx.x * (Idx)blockDim.x + (Idx)threadIdx.x) * 4;
     int4 q = make_int4(-1, -1, -1, -1);
     int32_t e = -1;
     if (i0 < n_round) {
@@ -112,7 +116,7 @@ __global__ void k_count(const int32_t* __restrict__ cell_e, int64_t n_e, const i
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int64_t i = i0 + j;
+            const Idx i = i0 + j;
             if (i >= n) break;
             const int32_t c = v[j];
             const int32_t pc = j == 0 ? prev : v[j - 1];
@@ -793,8 +797,14 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
     const dim3 cgrid(grid_for((nmax + 3) / 4, 256, ctx->n_sm * kCountCtasPerSm), 2);  // four particles per thread
     {
         TimedScope ts_(ctx, COMPTON_K_COUNT, stream);
-        k_count<<<cgrid, 256, 0, stream>>>(e_in->cell_dev, ne, g_in->cell_dev, ng, C, ctx->count[0], ctx->count[1],
-                                           ctx->unsorted, ctx->stats);
+        // 32-bit positions when the grid's last visited position fits
+        const int64_t span = (nmax + 127) / 128 * 128 + (int64_t)cgrid.x * 256 * 4;
+        if (span < ((int64_t)1 << 31))
+            k_count<int32_t><<<cgrid, 256, 0, stream>>>(e_in->cell_dev, ne, g_in->cell_dev, ng, C, ctx->count[0],
+                                                        ctx->count[1], ctx->unsorted, ctx->stats);
+        else
+            k_count<int64_t><<<cgrid, 256, 0, stream>>>(e_in->cell_dev, ne, g_in->cell_dev, ng, C, ctx->count[0],
+                                                        ctx->count[1], ctx->unsorted, ctx->stats);
     }
     COMPTON_LAUNCH_CHECK(ctx, "k_count");
     TimedScope scan_scope(ctx, COMPTON_K_SCAN, stream);
