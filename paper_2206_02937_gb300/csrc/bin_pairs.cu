@@ -24,6 +24,7 @@ namespace compton {
 namespace {
 
 constexpr int kSortThreads = 128;
+constexpr int kPlaceThreads = 1024;  // threads per placement CTA
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
@@ -359,7 +360,7 @@ __device__ __forceinline__ void store_rec(SortRec* r, uint32_t key, uint32_t pid
 // The weight a record carries (its first padding word).
 __device__ __forceinline__ float rec_weight(const SortRec* r) { return __uint_as_float(r->pad[0]); }
 
-__global__ void k_place(PlaceArgs a)
+__global__ void __launch_bounds__(kPlaceThreads) k_place(PlaceArgs a)
 {
     const int s = blockIdx.y;
     if (a.unsorted[s] == 0) return;
@@ -766,7 +767,7 @@ __global__ void __launch_bounds__(kSortThreads, 10) k_sort_gather(SortGatherArgs
 }
 
 constexpr int kCountCtasPerSm = 16;
-constexpr int kPlaceCtasPerSm = 16;
+constexpr int kPlaceCtasPerSm = 4;
 
 int grid_for(int64_t n, int threads, int max_blocks)
 {
@@ -791,9 +792,10 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
 
     const int64_t nmax = ne > ng ? ne : ng;
     // grid-stride kernels: CTAs per SM of the histogram and the placement
-    // (four waves of 256-thread CTAs; one wave made the placement's early
-    // exit for input in cell order 2 us shorter but the placement of
-    // shuffled input 0.3 ms longer)
+    // (the placement in 1024-thread CTAs: as many threads as sixteen
+    // 256-thread CTAs per SM, whose placement of shuffled input one wave of
+    // fewer threads made 0.3 ms longer, in a quarter of the CTAs, so its
+    // early exit for input in cell order is shorter)
     const dim3 cgrid(grid_for((nmax + 3) / 4, 256, ctx->n_sm * kCountCtasPerSm), 2);  // four particles per thread
     {
         TimedScope ts_(ctx, COMPTON_K_COUNT, stream);
@@ -841,7 +843,7 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
     scan_scope.end();
     COMPTON_LAUNCH_CHECK(ctx, "k_scan_final");
 
-    const dim3 pgrid(grid_for(nmax, 256, ctx->n_sm * kPlaceCtasPerSm), 2);
+    const dim3 pgrid(grid_for(nmax, kPlaceThreads, ctx->n_sm * kPlaceCtasPerSm), 2);
     PlaceArgs pa;
     const compton_species* ins[2] = {e_in, g_in};
     compton_species* outs[2] = {e_out, g_out};
@@ -863,7 +865,7 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
     pa.step = step;
     {
         TimedScope ts_(ctx, COMPTON_K_PLACE, stream);
-        k_place<<<pgrid, 256, 0, stream>>>(pa);
+        k_place<<<pgrid, kPlaceThreads, 0, stream>>>(pa);
     }
     COMPTON_LAUNCH_CHECK(ctx, "k_place");
 
