@@ -25,6 +25,7 @@ namespace {
 
 constexpr int kSortThreads = 128;
 constexpr int kPlaceThreads = 1024;  // threads per placement CTA
+constexpr int kCountThreads = 1024;  // threads per histogram CTA (256, 512: 1 us slower)
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
@@ -54,9 +55,10 @@ __device__ __forceinline__ int4 load_cells4(const int32_t* __restrict__ cell, Id
 // Positions in Idx: 32-bit when every position the grid visits fits (the
 // launch checks), else 64-bit.
 template <typename Idx>
-__global__ void k_count(const int32_t* __restrict__ cell_e, int64_t n_e, const int32_t* __restrict__ cell_g,
-                        int64_t n_g, int64_t C, int32_t* __restrict__ count_e, int32_t* __restrict__ count_g,
-                        int32_t* __restrict__ unsorted, DeviceStats* stats)
+__global__ void __launch_bounds__(kCountThreads) k_count(const int32_t* __restrict__ cell_e, int64_t n_e,
+                                                        const int32_t* __restrict__ cell_g, int64_t n_g, int64_t C,
+                                                        int32_t* __restrict__ count_e, int32_t* __restrict__ count_g,
+                                                        int32_t* __restrict__ unsorted, DeviceStats* stats)
 {
     const int s = blockIdx.y;
     const int32_t* __restrict__ cell = s == 0 ? cell_e : cell_g;
@@ -766,7 +768,7 @@ __global__ void __launch_bounds__(kSortThreads, 10) k_sort_gather(SortGatherArgs
     }
 }
 
-constexpr int kCountCtasPerSm = 16;
+constexpr int kCountCtasPerSm = 4;
 constexpr int kPlaceCtasPerSm = 4;
 
 int grid_for(int64_t n, int threads, int max_blocks)
@@ -791,22 +793,24 @@ compton_status launch_bin_pairs(compton_ctx* ctx, const compton_species* e_in, c
                                           stream));
 
     const int64_t nmax = ne > ng ? ne : ng;
-    // grid-stride kernels: CTAs per SM of the histogram and the placement
-    // (the placement in 1024-thread CTAs: as many threads as sixteen
+    // grid-stride kernels: CTAs per SM of the histogram and the placement,
+    // both in 1024-thread CTAs (the placement: as many threads as sixteen
     // 256-thread CTAs per SM, whose placement of shuffled input one wave of
     // fewer threads made 0.3 ms longer, in a quarter of the CTAs, so its
     // early exit for input in cell order is shorter)
-    const dim3 cgrid(grid_for((nmax + 3) / 4, 256, ctx->n_sm * kCountCtasPerSm), 2);  // four particles per thread
+    const dim3 cgrid(grid_for((nmax + 3) / 4, kCountThreads, ctx->n_sm * kCountCtasPerSm), 2);  // four per thread
     {
         TimedScope ts_(ctx, COMPTON_K_COUNT, stream);
         // 32-bit positions when the grid's last visited position fits
-        const int64_t span = (nmax + 127) / 128 * 128 + (int64_t)cgrid.x * 256 * 4;
+        const int64_t span = (nmax + 127) / 128 * 128 + (int64_t)cgrid.x * kCountThreads * 4;
         if (span < ((int64_t)1 << 31))
-            k_count<int32_t><<<cgrid, 256, 0, stream>>>(e_in->cell_dev, ne, g_in->cell_dev, ng, C, ctx->count[0],
-                                                        ctx->count[1], ctx->unsorted, ctx->stats);
+            k_count<int32_t><<<cgrid, kCountThreads, 0, stream>>>(e_in->cell_dev, ne, g_in->cell_dev, ng, C,
+                                                                  ctx->count[0], ctx->count[1], ctx->unsorted,
+                                                                  ctx->stats);
         else
-            k_count<int64_t><<<cgrid, 256, 0, stream>>>(e_in->cell_dev, ne, g_in->cell_dev, ng, C, ctx->count[0],
-                                                        ctx->count[1], ctx->unsorted, ctx->stats);
+            k_count<int64_t><<<cgrid, kCountThreads, 0, stream>>>(e_in->cell_dev, ne, g_in->cell_dev, ng, C,
+                                                                  ctx->count[0], ctx->count[1], ctx->unsorted,
+                                                                  ctx->stats);
     }
     COMPTON_LAUNCH_CHECK(ctx, "k_count");
     TimedScope scan_scope(ctx, COMPTON_K_SCAN, stream);
