@@ -104,7 +104,9 @@ __device__ __forceinline__ void resolve(const ScatterArgs& a, const AcceptedPair
         x = inv.x;
         if (inv.gamma > a.gamma64) invariants_f64(ux, uy, uz, kx, ky, kz, &x, &v);
     }
-    const float F2 = kn_F2(x);
+    // sigma_KN's integral, as the probability kernel computed it (kept in the
+    // entry's first spare word; zero from the other producers)
+    const float F2 = e.pad[0] ? __uint_as_float(e.pad[0]) : kn_F2(x);
     const Philox4 rnd = draw(a.seed, a.step, kStreamAngle, e.p);
     const Angle ang = kn_sample_angle(x, rnd.r0 >> 8, F2);
     collide_pair(ux, uy, uz, kx, ky, kz, x, ang, u24_closed0(rnd.r1), a.collide64_sq);
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
     // warp's last chunk, so that the FP64 invariants stay out of the loop
     auto evaluate = [&](const Batch& b) {
         bool hit = false, rare = false;
-        float x = -1.0f;
+        float x = -1.0f, F2 = 0.0f;
         int32_t ie = 0, ig = 0;
         uint32_t p = 0;
         float dens = 0.0f, u0 = 1.0f;
@@ -269,7 +271,8 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
             rare = inv.gamma > a.gamma64;
             if (!rare) {
                 // sigma_KN from its series below x = 1, the closed form above
-                const float Pr = one_minus_exp_neg(dens * a.dt * 0.375f * kn_F2(inv.x) * inv.v);
+                F2 = kn_F2(inv.x);
+                const float Pr = one_minus_exp_neg(dens * a.dt * 0.375f * F2 * inv.v);
                 const float P = inv.eps > 0.0f ? Pr : 0.0f;
                 hit = u0 < P;
                 if (a.prob_out) a.prob_out[p] = P;
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit)
             a.accepted[acc_base + n_acc + __popc(m & lt_mask)] =
-                AcceptedPair{ie, ig, x, p, {b.u[0], b.u[1], b.u[2]}, {b.k[0], b.k[1], b.k[2]}, {0u, 0u}};
+                AcceptedPair{ie, ig, x, p, {b.u[0], b.u[1], b.u[2]}, {b.k[0], b.k[1], b.k[2]}, {__float_as_uint(F2), 0u}};
         n_acc += __popc(m);
     };
 
@@ -454,10 +457,10 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
 // The collisions of the accepted pairs of k_pair_prob: the list has
 // prob_warps regions (region w from pair index chunk_begin(w) * 128 on,
 // warp_acc[w] entries); kCollideWarps warps share a region, taking its
-// entries 32 at a time in turn (one, two and four warps per region: 0.083,
-// 0.072 and 0.066 ms on the 512^2 step; the regions' lengths vary, and with
-// one warp each the longest set the kernel's time).
-constexpr int kCollideWarps = 4;
+// entries 32 at a time in turn (one, two, four and eight warps per region:
+// 0.083, 0.072, 0.066 and 0.065 ms on the 512^2 step; the regions' lengths
+// vary, and with one warp each the longest set the kernel's time).
+constexpr int kCollideWarps = 8;
 __global__ void __launch_bounds__(128) k_collide_regions(ScatterArgs a, int prob_warps)
 {
     const int64_t total = a.n_pairs ? *a.n_pairs : a.p_end;
