@@ -42,7 +42,9 @@ struct __align__(32) SortRec {
 // electron and photon index, rest-frame photon energy (negative when the
 // probability came from the network), pair index (counter of its draws), and
 // both momenta as they were read (so the collision kernel reads the list
-// sequentially instead of the particle arrays at random).
+// sequentially instead of the particle arrays at random); pad[0] holds the
+// bits of F(x, 2) (sigma_KN's integral, which the angle sampler needs) when
+// the producer computed it, else 0.
 struct __align__(16) AcceptedPair {
     int32_t ie, ig;
     float x;
