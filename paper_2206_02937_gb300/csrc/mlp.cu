@@ -68,6 +68,8 @@ constexpr uint64_t kWaitNs = 2000000000ull;             // 2 s bound on every wa
 // Measured (16.8M samples, BF16): 0, 1, 2 and 4 pairs of 16: 1.217, 1.163,
 // 1.170 and 1.265 ms; FP8 was fastest with none.
 constexpr int kSiluFmaPairs = 1;
+// BF16 on k_mlp_ta (the A operand in tensor memory) instead of k_mlp_tc<false>.
+constexpr bool kBf16TmemA = true;
 
 __device__ __forceinline__ float silu_exact(float z) { return z / (1.0f + expf(-z)); }
 __device__ __forceinline__ float sigmoid_exact(float z) { return 1.0f / (1.0f + expf(-z)); }
@@ -541,6 +543,176 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpMinCtas) k_mlp_tc(MlpArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// BF16 forward with the A operand in tensor memory.  Each row group keeps its
+// accumulator (64 columns) and its next layer's input (32 columns, two BF16
+// values per column) in TMEM, so an epilogue writes a row's 64 activations
+// with four tcgen05.st instead of shared-memory stores and a proxy fence;
+// 96 columns per group fit five groups in the 512 columns.  Otherwise as
+// k_mlp_tc<false>: half weights in shared memory, the half bias as one more
+// K step against a block of ones, h = z / 2 in the accumulator.
+// ---------------------------------------------------------------------------
+constexpr int kTaGroups = 5;
+constexpr int kTaThreads = 128 * kTaGroups;
+constexpr uint32_t kTaOffW = 0;                                     // 4 half-weight tiles
+constexpr uint32_t kTaOffRaw = kTaOffW + 4 * kWTileBytes;           // staged momenta per group
+constexpr uint32_t kTaOffBB = kTaOffRaw + 6 * kTileM * 4 * kTaGroups;  // half-bias blocks (256-aligned)
+constexpr uint32_t kTaOffOnes = kTaOffBB + 3 * 2048;                // ones block of the bias step
+constexpr uint32_t kTaOffW4 = kTaOffOnes + 4096;                    // 64 floats
+constexpr uint32_t kTaOffBar = kTaOffW4 + 256;                      // one mbarrier per group
+constexpr uint32_t kTaOffSlot = kTaOffBar + 8 * 8;                  // TMEM address
+constexpr uint32_t kTaSmem = kTaOffSlot + 16 + 1024;                // + alignment slack
+// requested at launch: more than half an SM's shared memory, so that one CTA
+// (which allocates all 512 TMEM columns) is resident per SM
+constexpr uint32_t kTaSmemLaunch = 120 * 1024;
+static_assert(kTaSmem <= kTaSmemLaunch, "layout exceeds the launch size");
+static_assert(kTaOffBB % 256 == 0 && kTaOffOnes % 256 == 0, "32-byte swizzled blocks need 256-byte alignment");
+
+__global__ void __launch_bounds__(kTaThreads, 1) k_mlp_ta(MlpArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x;
+    const int g = tid >> 7;
+    const int lt = tid & 127;
+    const int warp = tid >> 5;
+    float* st = reinterpret_cast<float*>(sm + kTaOffRaw) + g * 6 * kTileM + lt;
+    float* w4 = reinterpret_cast<float*>(sm + kTaOffW4);
+    uint64_t* bar0 = reinterpret_cast<uint64_t*>(sm + kTaOffBar);
+    uint64_t* bar = bar0 + g;
+    uint32_t* slot = reinterpret_cast<uint32_t*>(sm + kTaOffSlot);
+    const MlpDev& m = a.m;
+    const uint4* wsrc = reinterpret_cast<const uint4*>(m.whalf);
+    for (int i = tid; i < (int)(4 * kWTileBytes / 16); i += kTaThreads)
+        reinterpret_cast<uint4*>(sm + kTaOffW)[i] = wsrc[i];
+    for (int i = tid; i < 3 * 2048 / 16; i += kTaThreads)
+        reinterpret_cast<uint4*>(sm + kTaOffBB)[i] = wsrc[4 * kWTileBytes / 16 + i];
+    for (int r = tid; r < kTileM; r += kTaThreads) {
+        *reinterpret_cast<uint4*>(sm + kTaOffOnes + tc::sw32_offset(r, 0)) = make_uint4(0x3F803F80u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(sm + kTaOffOnes + tc::sw32_offset(r, 1)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid < 64) w4[tid] = m.w4[tid];
+    const float b4 = m.b4[0];
+    if (tid == 0) {
+        for (int q = 0; q < kTaGroups; ++q) tc::mbar_init(bar0 + q, 1);
+        tc::fence_barrier_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(slot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t dcol = *slot + 96u * (uint32_t)g;  // accumulator: 64 columns
+    const uint32_t acol = dcol + 64u;                 // next layer's input: 32 columns
+    const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+    const uint32_t trow = dcol + lanes, arow = acol + lanes;
+    constexpr uint32_t idesc = tc::make_idesc(1, 1, 128, 64);
+    const uint32_t sW = tc::smem_u32(sm + kTaOffW);
+    uint32_t phase = 0;
+    bool failed = false;
+    const int64_t n_rows = a.cand ? (int64_t)*a.n_cand : (a.cinfo ? *a.n_pairs : a.n);
+    const int64_t n_tiles = (n_rows + kTileM - 1) / kTileM;
+    const int64_t tile0 = (int64_t)blockIdx.x * kTaGroups + g;
+    const int64_t tstride = (int64_t)gridDim.x * kTaGroups;
+    if (tile0 < n_tiles) stage_pair_raw(a, tile0 * kTileM + lt, n_rows, st);
+    for (int64_t tile = tile0; tile < n_tiles && !failed; tile += tstride) {
+        const int64_t row = tile * kTileM + lt;
+        float f[6] = {0, 0, 0, 0, 0, 0};
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        if (row < n_rows)
+            features<true>(m, st[0], st[kTileM], st[2 * kTileM], st[3 * kTileM], st[4 * kTileM], st[5 * kTileM], f);
+        if (tile + tstride < n_tiles) stage_pair_raw(a, (tile + tstride) * kTileM + lt, n_rows, st);
+        {
+            // layer 0's input: 6 features and 1, 1 (K 6, 7: the half bias' hi, lo rows of W)
+            const uint32_t x0[8] = {pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
+                                    0x3F803F80u, 0u, 0u, 0u, 0u};
+            tc::tmem_st8(arow, x0);
+            tc::tmem_wait_st();
+        }
+        tc::fence_before_sync();
+        group_sync(g);
+        tc::fence_after_sync();
+
+        uint64_t acc2 = act::pk2(0.0f, 0.0f);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            if (lt == 0) {
+                const uint64_t bd = tc::sw128_kmajor_desc(sW + l * kWTileBytes);
+                const int n_ks = l == 0 ? 1 : 4;
+                for (int ks = 0; ks < n_ks; ++ks) tc::mma_bf16_ta(dcol, acol + 8 * ks, bd + 2 * ks, idesc, ks > 0);
+                if (l > 0)
+                    tc::mma_bf16(dcol, tc::sw32_kmajor_desc(sW + kTaOffOnes),
+                                 tc::sw32_kmajor_desc(sW + kTaOffBB + (l - 1) * 2048), idesc, 1u);
+                tc::mma_commit(bar);
+            }
+            const bool ok = tc::mbar_wait(bar, phase, kWaitNs);
+            phase ^= 1u;
+            tc::fence_after_sync();
+            if (ok) {
+                auto quarter = [&](int qc, uint32_t (&r)[16]) {
+                    uint32_t pk[8];
+                    float y[16];
+#pragma unroll
+                    for (int c = 0; c < 16; c += 2) {
+                        const uint64_t h2 = act::pk2(__uint_as_float(r[c]), __uint_as_float(r[c + 1]));
+                        const uint64_t y2 =
+                            ((8 * qc + c / 2) % 16 < kSiluFmaPairs) ? act::silu2_fma(h2) : act::silu2_mufu(h2);
+                        act::upk2(y2, y[c], y[c + 1]);
+                    }
+                    if (l < 3) {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) pk[c] = pack_bf16x2(y[2 * c], y[2 * c + 1]);
+                        tc::tmem_st8(arow + 8 * qc, pk);  // K 16 qc .. 16 qc + 15 of the next layer
+                    } else {
+                        const float4* w4v = reinterpret_cast<const float4*>(w4 + 16 * qc);
+#pragma unroll
+                        for (int c4 = 0; c4 < 4; ++c4) {
+                            const float4 w = w4v[c4];
+                            acc2 = act::fma2(act::pk2(y[4 * c4], y[4 * c4 + 1]), act::pk2(w.x, w.y), acc2);
+                            acc2 = act::fma2(act::pk2(y[4 * c4 + 2], y[4 * c4 + 3]), act::pk2(w.z, w.w), acc2);
+                        }
+                    }
+                };
+                uint32_t ra[16], rb[16];
+                tc::tmem_ld16(trow + 0, ra);
+                tc::tmem_wait16(ra);
+                tc::tmem_ld16(trow + 16, rb);
+                quarter(0, ra);
+                tc::tmem_wait16(rb);
+                tc::tmem_ld16(trow + 32, ra);
+                quarter(1, rb);
+                tc::tmem_wait16(ra);
+                tc::tmem_ld16(trow + 48, rb);
+                quarter(2, ra);
+                tc::tmem_wait16(rb);
+                quarter(3, rb);
+                if (l < 3) tc::tmem_wait_st();
+            }
+            tc::fence_before_sync();
+            const bool bad = group_sync_or(g, !ok);
+            tc::fence_after_sync();
+            if (bad) {
+                failed = true;
+                break;
+            }
+        }
+        float acc_lo, acc_hi;
+        act::upk2(acc2, acc_lo, acc_hi);
+        const float acc_out = acc_lo + acc_hi;
+        if (a.decide) decide_row(a, row, !failed && row < n_rows, acc_out + b4);
+        else if (!failed && row < n_rows) a.r_out[row] = __fdividef(1.0f, 1.0f + __expf(-(acc_out + b4)));
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (failed && lt == 0) atomicOr(&a.stats->error_flags, (unsigned long long)kErrTimeout);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(*slot, 512);
+}
+
+// ---------------------------------------------------------------------------
 // FP32 forward on the CUDA cores: one sample per thread, activations in shared
 // memory laid out [unit][thread] (conflict-free), transposed weights read as
 // broadcasts, 64 accumulators in registers.
@@ -707,6 +879,17 @@ compton_status launch_mlp_infer(compton_ctx* ctx, const float* ux, const float* 
         return COMPTON_OK;
     }
     const bool fp8 = mode == COMPTON_MODE_MLP_FP8;
+    if (!fp8 && kBf16TmemA) {
+        const void* kt = (const void*)k_mlp_ta;
+        COMPTON_CUDA_TRY(ctx, cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTaSmemLaunch));
+        const int grid_ta = grid_persistent(kt, kTaThreads, (int)kTaSmemLaunch, n, kTileM * kTaGroups);
+        {
+            TimedScope ts_(ctx, COMPTON_K_MLP, stream);
+            k_mlp_ta<<<grid_ta, kTaThreads, kTaSmemLaunch, stream>>>(a);
+        }
+        COMPTON_LAUNCH_CHECK(ctx, "k_mlp_ta");
+        return COMPTON_OK;
+    }
     const void* kern = fp8 ? (const void*)k_mlp_tc<true> : (const void*)k_mlp_tc<false>;
     COMPTON_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTc));
     const int grid = grid_persistent(kern, kMlpThreads, (int)kSmemTc, n, kTileM * kMlpGroups);
