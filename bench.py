@@ -861,7 +861,7 @@ def run_mlp(args, cg, torch, ctx, w, stream, dev, bufs, step0, peaks, with_oracl
             "plain_ms_per_step_same_state": ms_plain_same / args.steps,
             "plain_collisions_same_state": st_plain_same["scatters"], "collisions": st["scatters"],
             "network_kernel_ms": kern, "network_samples": n,
-            "roofline": {"kernel": "k_mlp_tc<bf16>", "bound": "tensor", "achieved": achieved, "peak": peak_bf16,
+            "roofline": {"kernel": "k_mlp_ta (bf16)", "bound": "tensor", "achieved": achieved, "peak": peak_bf16,
                          "unit": "TFLOP/s", "frac": achieved / peak_bf16,
                          "note": "algorithmic FLOPs 2(6*64+3*64*64+64) per sample; peak: measured bf16 burst"},
             "error_vs_plain": err, "error_vs_oracle": vs_oracle, "train": train, "invariant_features": invariant,
