@@ -199,7 +199,10 @@ struct Batch {
     float u[3], k[3];
 };
 
-template <bool kBinned, bool kWeighted>
+// kCandOut (the surrogate modes' first kernel): the same filter, but each
+// batch of candidates goes with its momenta to the context's candidate list
+// (one atomic per batch) instead of being evaluated.
+template <bool kBinned, bool kWeighted, bool kCandOut = false>
 __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
 {
     __shared__ WarpWindow s_win[kProbWarps];
@@ -253,6 +256,18 @@ __global__ void __launch_bounds__(kProbThreads, 4) k_pair_prob(ScatterArgs a)
     // aside in the warp's region of the candidate list and decided after the
     // warp's last chunk, so that the FP64 invariants stay out of the loop
     auto evaluate = [&](const Batch& b) {
+        if (kCandOut) {
+            uint32_t base = 0;
+            if (lane == 0 && b.n > 0) base = atomicAdd(a.n_cand, (uint32_t)b.n);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if ((int)lane < b.n) {
+                int slot = b.first + (int)lane;
+                if (slot >= kQueueCap) slot -= kQueueCap;
+                a.cand[base + lane] = CandPair{Q.ie[slot], Q.ig[slot], Q.dens[slot], Q.u0[slot], Q.p[slot],
+                                               {b.u[0], b.u[1], b.u[2]}, {b.k[0], b.k[1], b.k[2]}, 0u};
+            }
+            return;
+        }
         bool hit = false, rare = false;
         float x = -1.0f, F2 = 0.0f;
         int32_t ie = 0, ig = 0;
@@ -476,140 +491,6 @@ __global__ void __launch_bounds__(128) k_collide_regions(ScatterArgs a, int prob
         for (uint32_t i = lane + 32u * (uint32_t)(v % kCollideWarps); i < n; i += 32u * kCollideWarps)
             resolve(a, a.accepted[base + i]);
     }
-}
-
-// Surrogate modes, first kernel: phase A of k_pair_prob (locate, Bernoulli
-// uniform, bound test); the candidates, with their momenta, go to the
-// context's candidate list for the network.
-template <bool kBinned, bool kWeighted>
-__global__ void __launch_bounds__(kProbThreads, 4) k_cand(ScatterArgs a)
-{
-    __shared__ CellInfo win[kCellWindow];
-    __shared__ float wbound[kCellWindow];  // each staged cell's candidate bound
-    __shared__ unsigned red_pairs;
-    __shared__ int warp_cnt[kProbThreads / 32];
-    __shared__ uint32_t cta_base;
-    const int tid = threadIdx.x;
-    const unsigned lane = tid & 31u;
-    const int64_t total = kBinned ? *a.n_pairs : a.p_end;
-    const int64_t tile = blockIdx.x;
-    const int64_t p0 = (kBinned ? 0 : a.p_begin) + tile * kPairsPerTile;
-    if (p0 >= total) return;
-    if (tid == 0) red_pairs = 0;
-    int c_first = 0, nwin = 0;
-    if (kBinned) {
-        c_first = a.tile_cell[tile];
-        nwin = a.tile_cell[tile + 1] - c_first + 1;
-        if (nwin <= kCellWindow)
-            for (int i = tid; i < nwin; i += kProbThreads) {
-                const CellInfo c = a.cinfo[c_first + i];
-                win[i] = c;
-                if (!kWeighted) wbound[i] = one_minus_exp_neg(2.0002f * c.dens * a.dt);
-            }
-    }
-    __syncthreads();
-    const int64_t pb = p0 + (int64_t)tid * kPairsPerThread;
-    const Philox4 rnd4 = draw(a.seed, a.step, kStreamScatter, (uint32_t)(pb >> 2));
-    const uint32_t words[4] = {rnd4.r0, rnd4.r1, rnd4.r2, rnd4.r3};
-    const bool all = a.prob_out != nullptr;
-    const CellInfo* cw = nwin <= kCellWindow ? win : a.cinfo + c_first;
-    int ci = (kBinned && pb < total) ? find_cell(cw, nwin, pb) : 0;
-    unsigned n_pairs = 0;
-    int ie[kPairsPerThread], ig[kPairsPerThread];
-    float dens[kPairsPerThread], u0[kPairsPerThread];
-    bool is_cand[kPairsPerThread];
-#pragma unroll
-    for (int r = 0; r < kPairsPerThread; ++r) {
-        const int64_t p = pb + r;
-        const bool valid = p < total;
-        ie[r] = 0;
-        ig[r] = 0;
-        dens[r] = 0.0f;
-        float bound = 0.0f;
-        if (valid) {
-            if (kBinned) {
-                while (ci + 1 < nwin && (int64_t)cw[ci + 1].pair_off <= p) ++ci;
-                const CellInfo c = cw[ci];
-                const int j = (int)(p - c.pair_off);
-                ie[r] = c.e_start + j;
-                ig[r] = c.g_start + j;
-                dens[r] = pair_density<kWeighted>(a, c.dens, ie[r], ig[r]);
-                bound = (!kWeighted && nwin <= kCellWindow) ? wbound[ci]
-                                                            : one_minus_exp_neg(2.0002f * dens[r] * a.dt);
-            } else {
-                ie[r] = (int)p;
-                ig[r] = (int)p;
-                dens[r] = a.n_dens[p];
-                bound = one_minus_exp_neg(2.0002f * dens[r] * a.dt);
-            }
-            ++n_pairs;
-        }
-        u0[r] = u24_closed0(words[r]);
-        is_cand[r] = valid && (all || u0[r] < bound);
-        if (valid && !is_cand[r] && a.flag_out) a.flag_out[p] = 0;
-    }
-    // the candidates' momenta: all loads in flight before the first use
-    float mom[kPairsPerThread][6];
-#pragma unroll
-    for (int r = 0; r < kPairsPerThread; ++r) {
-        if (is_cand[r]) {
-            mom[r][0] = a.u[0][ie[r]];
-            mom[r][1] = a.u[1][ie[r]];
-            mom[r][2] = a.u[2][ie[r]];
-            mom[r][3] = a.k[0][ig[r]];
-            mom[r][4] = a.k[1][ig[r]];
-            mom[r][5] = a.k[2][ig[r]];
-        }
-    }
-    // the CTA's candidates take one contiguous range of the list (one atomic
-    // per CTA): lane prefix within the warp, warp prefix within the CTA
-    int mine = 0;
-#pragma unroll
-    for (int r = 0; r < kPairsPerThread; ++r) mine += is_cand[r] ? 1 : 0;
-    int incl = mine;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int o = __shfl_up_sync(0xffffffffu, incl, d);
-        if ((int)lane >= d) incl += o;
-    }
-    const int w = tid >> 5;
-    if (lane == 31) warp_cnt[w] = incl;
-    __syncthreads();
-    if (tid == 0) {
-        int run = 0;
-        for (int i = 0; i < kProbThreads / 32; ++i) {
-            const int c = warp_cnt[i];
-            warp_cnt[i] = run;
-            run += c;
-        }
-        cta_base = run ? atomicAdd(a.n_cand, (uint32_t)run) : 0u;
-    }
-    __syncthreads();
-    uint32_t at = cta_base + (uint32_t)(warp_cnt[w] + incl - mine);
-#pragma unroll
-    for (int r = 0; r < kPairsPerThread; ++r) {
-        if (is_cand[r]) {
-            CandPair c;
-            c.ie = ie[r];
-            c.ig = ig[r];
-            c.dens = dens[r];
-            c.u0 = u0[r];
-            c.p = (uint32_t)(pb + r);
-            c.u[0] = mom[r][0];
-            c.u[1] = mom[r][1];
-            c.u[2] = mom[r][2];
-            c.k[0] = mom[r][3];
-            c.k[1] = mom[r][4];
-            c.k[2] = mom[r][5];
-            c.pad = 0u;
-            a.cand[at++] = c;
-        }
-    }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) n_pairs += __shfl_xor_sync(0xffffffffu, n_pairs, d);
-    if (lane == 0) atomicAdd(&red_pairs, n_pairs);
-    __syncthreads();
-    if (tid == 0) atomicAdd(&a.stats->pairs_tested, (unsigned long long)red_pairs);
 }
 
 // Surrogate modes, third kernel: every candidate's probability from its
@@ -1006,9 +887,10 @@ compton_status launch_step(compton_ctx* ctx, ScatterArgs& a, compton_mode mode, 
         COMPTON_CUDA_TRY(ctx, cudaMemsetAsync(ctx->n_cand, 0, sizeof(uint32_t), stream));
         {
             TimedScope ts_(ctx, COMPTON_K_PROB, stream);
-            k_cand<kBinned, kWeighted><<<tiles, kProbThreads, 0, stream>>>(a);
+            // the candidate filter of the plain kernel, candidates to the list
+            k_pair_prob<kBinned, kWeighted, true><<<prob_grid(tiles), kProbThreads, 0, stream>>>(a);
         }
-        COMPTON_LAUNCH_CHECK(ctx, "k_cand");
+        COMPTON_LAUNCH_CHECK(ctx, "k_pair_prob<cand>");
         // tensor-core modes and the paper's network decide inside the network
         // kernel; the FP32 network writes r and k_decide decides
         const MlpDecide dec{a.dt, a.gamma64, a.prob_out, a.flag_out};
