@@ -258,7 +258,8 @@ def test_two_chained_steps():
 
 def test_unaligned_input_arrays():
     # species arrays that start 4 bytes past an aligned address (views at
-    # offset 1): the histogram takes its scalar loads; the order must match
+    # offset 1): the histogram and the sort's staging take their scalar
+    # loads; order and momenta must match
     import paper_2206_02937_gb300 as cgl
     from tests.gpu_util import species_np, torch_cuda
     torch = torch_cuda()
@@ -286,7 +287,9 @@ def test_unaligned_input_arrays():
         cgl.compton_destroy(ctx)
     assert np.array_equal(be["id"], w.e["id"][o["e_perm"]])
     assert np.array_equal(bg["id"], w.g["id"][o["g_perm"]])
-    assert np.array_equal(be["ux"], w.e["ux"][o["e_perm"]])
+    for c in ("ux", "uy", "uz"):
+        assert np.array_equal(be[c], w.e[c][o["e_perm"]])
+        assert np.array_equal(bg[c], w.g[c][o["g_perm"]])
 
 
 @pytest.mark.parametrize("case", ["c1", "ragged", "gamma_fp64", "gamma_fp32"])
