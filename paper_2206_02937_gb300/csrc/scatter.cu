@@ -814,13 +814,17 @@ unsigned prob_grid(unsigned tiles)
     return tiles < 1u ? 1u : (tiles < cap ? tiles : cap);
 }
 
+// CTAs of 256 threads over a list of up to max_accepted entries: up to 32
+// per SM, so that a 512^2 step's accepted pairs (about a million) take at
+// most one entry per thread (with 8 per SM each thread resolved two or three
+// in turn: 0.119 against 0.106 ms for the BF16-network step's collisions).
 int collide_grid(int64_t max_accepted)
 {
     int dev = 0, n_sm = 1;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm < 1) n_sm = 1;
     const int64_t want = (max_accepted + 255) / 256;
-    const int64_t cap = (int64_t)n_sm * 8;
+    const int64_t cap = (int64_t)n_sm * 32;
     return (int)(want < 1 ? 1 : (want < cap ? want : cap));
 }
 
