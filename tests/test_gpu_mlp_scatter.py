@@ -86,18 +86,23 @@ def test_surrogate_scatter_matches_network_and_oracle(mode_name):
         assert np.linalg.norm(ka - ko) <= 1e-5 * scale[q]
 
 
-def test_surrogate_filtered_equals_full_evaluation():
+@pytest.mark.parametrize("mode_name", ["MODE_MLP_BF16", "MODE_MLP_FP32", "MODE_PNET"])
+def test_surrogate_filtered_equals_full_evaluation(mode_name):
     # the surrogate step without prob_out runs the network on the candidates
-    # only; flags and momenta equal those of the full evaluation
+    # of the probability kernel's filter only; flags and momenta equal those
+    # of the full evaluation (every pair a candidate)
     import paper_2206_02937_gb300 as cg
+    from oracle import pnet as opn
     torch = torch_cuda()
     cg.build()
+    mode = getattr(cg, mode_name)
     w = _workload(seed=4)
     out = {}
     for want_p in (True, False):
         ctx = cg.compton_init(w.n_cells, max(w.n_e, w.n_g), w.w_over_v, w.dt, w.seed)
         try:
             cg.compton_mlp_set_params(ctx, omlp.init_params(11).astype(np.float32))
+            cg.compton_pnet_set_params(ctx, opn.init_params(12).astype(np.float32))
             e_in, g_in = to_species(torch, w.e), to_species(torch, w.g)
             e_out, g_out = cg.Species.empty_like(e_in), cg.Species.empty_like(g_in)
             pairs = cg.compton_bin_pairs(ctx, e_in, g_in, e_out, g_out, 2)
@@ -105,7 +110,7 @@ def test_surrogate_filtered_equals_full_evaluation():
             P = torch.zeros(n, device="cuda") if want_p else None
             F = torch.zeros(n, dtype=torch.uint8, device="cuda")
             cg.compton_get_stats(ctx, reset=True)
-            cg.compton_scatter_step(ctx, e_out, g_out, pairs, cg.MODE_MLP_BF16, 2, P, F)
+            cg.compton_scatter_step(ctx, e_out, g_out, pairs, mode, 2, P, F)
             st = cg.compton_get_stats(ctx, reset=True)
             out[want_p] = (F.cpu().numpy(), species_np(e_out), species_np(g_out), st)
         finally:
